@@ -1,0 +1,229 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only builds inputs (A, b and the factors they were built from).  It
+holds none of LSRN's arithmetic: no sketch, no SVD of the sketch, no LSQR or
+Chebyshev step, and not the Philox/Box-Muller generator of the sketching
+matrix.  Its random numbers come from numpy's PCG64 streams, which are the same
+on every platform.  Both the oracle and the CUDA path consume the bytes made
+here, so a test always compares the two on identical inputs.
+
+Workload families (the paper's experiments use random matrices with a prescribed
+condition number and rank, section 6.2 and 6.4, and sprandn-like sparse
+matrices, section 6.5):
+
+* ``dense_haar``        -- A = U diag(sigma) V^T with Haar-distributed U, V
+                           (QR of a Gaussian matrix, signs fixed by diag(R) > 0),
+                           sigma log-spaced from 1 to 1/cond on the first `rank`
+                           entries, zeros after; b = A x0 + noise * N(0, 1).
+* ``dense_householder`` -- same spectrum, but U = H_1..H_k [I_r; 0] and
+                           V = H'_1..H'_k [I_r; 0] from k seeded Householder
+                           reflectors, so that a 10^6 x 2000 matrix can be built
+                           in one pass (compact WY form, rank-k update).
+* ``csr_uniform_rows``  -- CSR with a fixed number of distinct, uniformly drawn,
+                           sorted columns per row and N(0, 1) values.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Optional
+
+import numpy as np
+
+
+def log_spaced_sigma(rank: int, cond: float) -> np.ndarray:
+    """sigma_i = cond^(-(i-1)/(rank-1)), i = 1..rank (1 -> 1/cond)."""
+    if rank <= 0:
+        return np.zeros(0)
+    if rank == 1:
+        return np.ones(1)
+    return np.power(10.0, -np.log10(cond) * np.arange(rank) / (rank - 1))
+
+
+@dataclasses.dataclass
+class DenseProblem:
+    A: object                       # numpy (m, n) float64 C-contiguous, or a torch tensor
+    b: object                       # (m,)
+    x0: np.ndarray                  # (n,)
+    sigma: np.ndarray               # (rank,) planted singular values
+    apply_Ut: Callable[[np.ndarray], np.ndarray]   # b (m,) -> U^T b (rank,)
+    apply_V: Callable[[np.ndarray], np.ndarray]    # c (rank,) -> V c (n,)
+    meta: dict
+
+
+def _haar(rng: np.random.Generator, n: int, k: int) -> np.ndarray:
+    q, r = np.linalg.qr(rng.standard_normal((n, k)))
+    return q * np.sign(np.diag(r))
+
+
+def dense_haar(m: int, n: int, rank: int, cond: float, noise: float, seed: int) -> DenseProblem:
+    """Dense A = U diag(sigma) V^T with Haar factors (the 2000 x 100 recipe)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    U = _haar(rng, m, rank)
+    V = _haar(rng, n, rank)
+    sigma = log_spaced_sigma(rank, cond)
+    A = np.ascontiguousarray((U * sigma) @ V.T)
+    x0 = rng.standard_normal(n)
+    b = A @ x0 + noise * rng.standard_normal(m)
+    return DenseProblem(A=A, b=b, x0=x0, sigma=sigma,
+                        apply_Ut=lambda v: U.T @ v, apply_V=lambda c: V @ c,
+                        meta=dict(kind="haar", m=m, n=n, rank=rank, cond=cond,
+                                  noise=noise, seed=seed, U=U, V=V))
+
+
+class _Reflectors:
+    """Q = H_1 ... H_k = I - Y T Y^T with H_i = I - tau_i y_i y_i^T (compact WY)."""
+
+    def __init__(self, Y: np.ndarray):
+        self.Y = Y
+        k = Y.shape[1]
+        tau = 2.0 / np.einsum("ij,ij->j", Y, Y)
+        T = np.zeros((k, k))
+        gram = Y.T @ Y
+        for i in range(k):
+            T[i, i] = tau[i]
+            if i:
+                T[:i, i] = -tau[i] * (T[:i, :i] @ gram[:i, i])
+        self.T = T
+
+    def apply(self, X: np.ndarray) -> np.ndarray:     # Q X
+        return X - self.Y @ (self.T @ (self.Y.T @ X))
+
+    def apply_t(self, X: np.ndarray) -> np.ndarray:   # Q^T X
+        return X - self.Y @ (self.T.T @ (self.Y.T @ X))
+
+
+def dense_householder(m: int, n: int, rank: int, cond: float, noise: float, seed: int,
+                      n_reflectors: int = 8, device: Optional[str] = None,
+                      row_block: int = 65536) -> DenseProblem:
+    """Dense A = U diag(sigma) V^T with U, V products of seeded Householder reflectors.
+
+    A = Q [W; 0] with W = diag(sigma) V^T (rank x n) and Q = I - Y T Y^T, so
+    A = [W; 0] - Y (T Y[:rank]^T W): a rank-k update written row block by row
+    block.  With ``device`` set (a torch device string) A and b are built there
+    with torch, otherwise with numpy on the host.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = n_reflectors
+    QU = _Reflectors(rng.standard_normal((m, k)))
+    QV = _Reflectors(rng.standard_normal((n, k)))
+    sigma = log_spaced_sigma(rank, cond)
+    eye = np.zeros((n, rank))
+    eye[:rank, :rank] = np.eye(rank)
+    V = QV.apply(eye)                                   # n x rank
+    W = sigma[:, None] * V.T                            # rank x n
+    Z = QU.T @ (QU.Y[:rank].T @ W)                      # k x n
+    x0 = rng.standard_normal(n)
+    e = rng.standard_normal(m)
+    if device is None:
+        A = np.empty((m, n))
+        for r0 in range(0, m, row_block):
+            r1 = min(m, r0 + row_block)
+            blk = -(QU.Y[r0:r1] @ Z)
+            if r0 < rank:
+                t = min(r1, rank)
+                blk[: t - r0] += W[r0:t]
+            A[r0:r1] = blk
+        b = A @ x0 + noise * e
+    else:
+        import torch
+        dev = torch.device(device)
+        A = torch.empty((m, n), dtype=torch.float64, device=dev)
+        Zt = torch.from_numpy(Z).to(dev)
+        Wt = torch.from_numpy(W).to(dev)
+        Yt = torch.from_numpy(QU.Y).to(dev)
+        for r0 in range(0, m, row_block):
+            r1 = min(m, r0 + row_block)
+            blk = -(Yt[r0:r1] @ Zt)
+            if r0 < rank:
+                t = min(r1, rank)
+                blk[: t - r0] += Wt[r0:t]
+            A[r0:r1] = blk
+        b = A @ torch.from_numpy(x0).to(dev) + noise * torch.from_numpy(e).to(dev)
+
+    def apply_Ut(v: np.ndarray) -> np.ndarray:
+        return QU.apply_t(np.asarray(v, dtype=np.float64).reshape(m, 1))[:rank, 0]
+
+    def apply_V(c: np.ndarray) -> np.ndarray:
+        return V @ np.asarray(c, dtype=np.float64)
+
+    return DenseProblem(A=A, b=b, x0=x0, sigma=sigma, apply_Ut=apply_Ut, apply_V=apply_V,
+                        meta=dict(kind="householder", m=m, n=n, rank=rank, cond=cond,
+                                  noise=noise, seed=seed, n_reflectors=k, V=V))
+
+
+@dataclasses.dataclass
+class CsrMatrix:
+    m: int
+    n: int
+    row_ptr: np.ndarray      # int64 (m + 1,)
+    col_idx: np.ndarray      # int32 (nnz,)
+    values: np.ndarray       # float64 or float32 (nnz,)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        D = np.zeros((self.m, self.n), dtype=np.float64)
+        rows = np.repeat(np.arange(self.m), np.diff(self.row_ptr))
+        D[rows, self.col_idx] = self.values.astype(np.float64)
+        return D
+
+
+def csr_uniform_rows(m: int, n: int, nnz_per_row: int, seed: int,
+                     dtype=np.float64) -> CsrMatrix:
+    """Each row: `nnz_per_row` distinct columns drawn uniformly, sorted; N(0,1) values.
+
+    With dtype float32 the values are the float64 draws rounded to float32.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = min(nnz_per_row, n)
+    cols = np.empty((m, k), dtype=np.int32)
+    for i in range(m):
+        cols[i] = np.sort(rng.choice(n, size=k, replace=False, shuffle=False))
+    vals = rng.standard_normal(m * k).astype(dtype)
+    row_ptr = np.arange(0, (m + 1) * k, k, dtype=np.int64)
+    return CsrMatrix(m=m, n=n, row_ptr=row_ptr, col_idx=cols.reshape(-1), values=vals)
+
+
+def csr_random_density(m: int, n: int, density: float, seed: int,
+                       dtype=np.float64) -> CsrMatrix:
+    """sprandn-like CSR: each entry present independently with probability `density`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    counts = rng.binomial(n, density, size=m)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(counts)
+    cols = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    for i in range(m):
+        c = counts[i]
+        if c:
+            cols[row_ptr[i]:row_ptr[i + 1]] = np.sort(rng.choice(n, size=c, replace=False,
+                                                                 shuffle=False))
+    vals = rng.standard_normal(int(row_ptr[-1])).astype(dtype)
+    return CsrMatrix(m=m, n=n, row_ptr=row_ptr, col_idx=cols, values=vals)
+
+
+def gaussian_vector(n: int, seed: int) -> np.ndarray:
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(n)
+
+
+# Named recipes: the small parity case and the full-size benchmark case.
+def c1_problem(seed: int = 0) -> DenseProblem:
+    """2000 x 100, rank 80, sigma 1 -> 1e-6, Haar factors, noise 1e-3."""
+    return dense_haar(2000, 100, 80, 1e6, 1e-3, seed)
+
+
+def c2_problem(seed: int = 0, device: Optional[str] = None, m: int = 1_000_000,
+               n: int = 2000, rank: int = 1800) -> DenseProblem:
+    """10^6 x 2000, rank 1800, sigma 1 -> 1e-6, 8 Householder reflectors, noise 1e-4."""
+    return dense_householder(m, n, rank, 1e6, 1e-4, seed, device=device)
+
+
+def c3_problem(seed: int = 0, m: int = 10_000, n: int = 1_000_000, nnz_per_row: int = 2000,
+               dtype=np.float64):
+    """10^4 x 10^6 CSR, 2000 uniform columns per row, N(0,1) values; b ~ N(0,1)."""
+    A = csr_uniform_rows(m, n, nnz_per_row, seed, dtype)
+    b = gaussian_vector(m, seed + 7919)
+    return A, b
+
