@@ -1,0 +1,215 @@
+/*
+ * lsrn.h -- C ABI of the GB300 (sm_103a) LSRN solver.
+ *
+ * LSRN (Meng, Saunders, Mahoney, "LSRN: A Parallel Iterative Solver for
+ * Strongly Over- or Under-Determined Systems") computes the min-length
+ * solution x* = argmin ||x||_2 subject to x in argmin_z ||A z - b||_2
+ * (section 1, eqs. (ls) and (ls_min_length)) of a dense or sparse A that is
+ * strongly over- (m >> n) or under-determined (m << n) and possibly
+ * rank-deficient, optionally with Tikhonov regularisation W = lambda I
+ * (section 5, eqs. (l2_reg), (l2_reg_eq), (l2_reg_eq_under)).
+ *
+ * A solve runs the steps of Algorithm 1 (m >= n) or Algorithm 2 (m < n):
+ *   lsrn_plan        orientation, s = ceil(gamma * min(m, n)), workspace
+ *   lsrn_sketch      steps 2-3: A~ = G A (or A G), G Gaussian, drawn on the fly
+ *   lsrn_precond     steps 4-5: SVD of A~, rank r, N = V~ Sigma~^-1 (M = U~ Sigma~^-1)
+ *   lsrn_solve_lsqr  step 6-7 with LSQR
+ *   lsrn_solve_cs    step 6-7 with the Chebyshev semi-iterative method (Algorithm 3)
+ *
+ * Conventions (apply to every entry point):
+ *   - All functions return an lsrn_status; none throws or aborts.  A negative
+ *     status means the call failed; the plan (if any) is left in the state it
+ *     had before the call unless stated otherwise.
+ *   - Pointers to matrix and vector data may be host or device pointers; the
+ *     library asks the CUDA runtime which one it is.  Host data is copied to
+ *     the device inside the call (so host inputs may be freed on return); device
+ *     data must stay valid and unmodified until the call that uses it returns.
+ *   - Arithmetic is FP64 unless an option says otherwise.  All work runs on the
+ *     CUDA stream given to lsrn_plan, on the device that was current then; a
+ *     call that returns results to the caller synchronises that stream.
+ *   - A plan is not thread-safe: calls on one plan must not overlap.  Different
+ *     plans are independent.
+ *   - The library never falls back to CPU arithmetic: without a usable GPU the
+ *     calls return LSRN_ERR_CUDA.
+ */
+#ifndef LSRN_H
+#define LSRN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSRN_OK = 0,
+  LSRN_PENDING = 1,             /* lsrn_poll: the request is still running */
+  LSRN_ERR_INVALID_ARG = -1,    /* bad size, pointer, option or CSR structure */
+  LSRN_ERR_OOM = -2,            /* device allocation failed */
+  LSRN_ERR_CUDA = -3,           /* CUDA runtime error or no usable device */
+  LSRN_ERR_NOT_CONVERGED = -4,  /* LSQR hit max_iter; x holds the last iterate */
+  LSRN_ERR_DIVERGED = -5,       /* CS residual grew: the Theorem 4.5 bounds failed */
+  LSRN_ERR_TIMEOUT = -6,        /* a bounded device wait gave up */
+  LSRN_ERR_QUEUE_FULL = -7,     /* server: no slot or memory budget for the request */
+  LSRN_ERR_STATE = -8,          /* calls out of order (e.g. precond before sketch) */
+  LSRN_ERR_UNSUPPORTED = -9     /* valid request this build does not implement */
+} lsrn_status;
+
+typedef enum {
+  LSRN_DENSE_ROWMAJOR = 0,      /* A[i*ld + j], ld >= n */
+  LSRN_DENSE_COLMAJOR = 1,      /* A[i + j*ld], ld >= m */
+  LSRN_CSR = 2                  /* row_ptr[m+1] (int64), col_idx[nnz] (int32), values[nnz] */
+} lsrn_format;
+
+typedef enum { LSRN_F64 = 0, LSRN_F32 = 1 } lsrn_dtype;
+
+typedef enum {
+  LSRN_SKETCH_F64 = 0,          /* FP64 FMA arithmetic */
+  LSRN_SKETCH_TC_SLICED = 1     /* tensor cores on exact bf16 slices of G and A,
+                                   FP64-accurate (dense A only) */
+} lsrn_sketch_mode;
+
+/* The matrix A (m x n).  For LSRN_CSR, columns within a row need not be
+ * sorted but must be in [0, n) and row_ptr must be non-decreasing with
+ * row_ptr[0] = 0 and row_ptr[m] = nnz. */
+typedef struct {
+  int64_t m, n;
+  int64_t ld;                   /* dense leading dimension in elements */
+  int64_t nnz;                  /* CSR stored entries */
+  int32_t format;               /* lsrn_format */
+  int32_t dtype;                /* lsrn_dtype of values (F32 values are widened to FP64) */
+  const void* values;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+} lsrn_matrix;
+
+typedef struct {
+  double gamma;        /* oversampling factor, > 1; s = ceil(gamma*min(m,n)) (default 2.0) */
+  double tol;          /* epsilon: LSQR atol = btol, CS tolerance (default 1e-14) */
+  double lambda;       /* Tikhonov lambda >= 0, W = lambda I (default 0) */
+  double rcond;        /* rank cut: keep sigma_i > rcond*sigma_1; < 0: max(s, n')*2^-53 */
+  double cs_alpha;     /* alpha of Theorem 4.5 used for the CS bounds; < 0: 1/sqrt(s) */
+  double refine_tol;   /* relative tolerance of each refinement correction (default 1e-3) */
+  int32_t max_iter;    /* LSQR iteration cap; < 0: ceil(1.5 * Theorem 4.6 bound) */
+  int32_t refine_max;  /* refinement steps after the iteration (default 1; 0 = paper only) */
+  uint64_t seed;       /* key of the counter-based generator of G (default 0) */
+  int32_t sketch_mode; /* lsrn_sketch_mode (default LSRN_SKETCH_F64) */
+  int32_t reserved;
+} lsrn_options;
+
+typedef struct {
+  int64_t m, n, s, rank;          /* problem size, sketch size, numerical rank r */
+  int32_t iterations;             /* LSQR iterations / CS steps of the main sweep */
+  int32_t refine_steps;           /* refinement steps taken */
+  int32_t refine_iterations;      /* inner steps spent in refinement */
+  int32_t tall;                   /* 1: Algorithm 1, 0: Algorithm 2 */
+  int32_t istop;                  /* LSQR: 1 = rule S1, 2 = rule S2, 3 = exact, 0 = cap/none */
+  int32_t status;                 /* lsrn_status of the solve */
+  double sigma_max_sketch;        /* sigma_1 of A~ */
+  double sigma_min_sketch;        /* sigma_r of A~ */
+  double sigma_L, sigma_U;        /* CS bounds used (Theorem 4.5), 0 for LSQR */
+  double rnorm_est, arnorm_est;   /* LSQR estimates of ||r||, ||(AN)^T r|| at exit */
+  double anorm_est;               /* LSQR estimate of ||AN||_F */
+  float t_sketch_ms, t_precond_ms, t_iter_ms, t_refine_ms;  /* device time per phase */
+} lsrn_info;
+
+typedef struct lsrn_plan_s* lsrn_plan_t;
+typedef struct lsrn_server_s* lsrn_server_t;
+
+/* Human-readable name of a status code (static storage). */
+const char* lsrn_status_string(lsrn_status s);
+
+/* Fill *opt with the defaults listed in lsrn_options.  INVALID_ARG if opt is NULL. */
+lsrn_status lsrn_default_options(lsrn_options* opt);
+
+/* Create a plan for A (Algorithm 1 step 1 / Algorithm 2 step 1; section 5's
+ * augmentation [A; lambda I] for m >= n or [A/lambda, I_m] for m < n).
+ *   A       matrix descriptor; data host or device.  Dense A whose layout is not
+ *           the one the iteration streams (row-major for m >= n, column-major for
+ *           m < n) and host A are copied into plan-owned device memory; otherwise
+ *           the plan keeps the caller's device pointer, which must outlive it.
+ *   opt     options, or NULL for defaults.
+ *   stream  cudaStream_t to run on (NULL = legacy default stream).
+ *   out     receives the plan.  Ownership passes to the caller, who frees it
+ *           with lsrn_plan_destroy.
+ * INVALID_ARG: m or n < 1, gamma <= 1, lambda < 0, tol <= 0, NULL data, bad ld,
+ * CSR indices out of range or row_ptr not monotone (checked on the device).
+ * OOM when the workspace does not fit.  Nothing is allocated on failure. */
+lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
+                      lsrn_plan_t* out);
+
+/* Algorithm 1 steps 2-3 (A~ = G A, s x n) or Algorithm 2 steps 2-3 (A~ = A G,
+ * m x s).  G has i.i.d. N(0,1) entries (rounded to the grid 2^-12) produced by
+ * Philox4x32-10 + Box-Muller from (seed, row, column); it is never stored.
+ * Asynchronous on the plan's stream. */
+lsrn_status lsrn_sketch(lsrn_plan_t p);
+
+/* Algorithm 1 steps 4-5 / Algorithm 2 steps 4-5: SVD of A~ on the device
+ * (Householder QR, then one-sided Jacobi), numerical rank r, and N = V~
+ * Sigma~^-1 (n x r) or M = U~ Sigma~^-1 (m x r).  Requires lsrn_sketch first
+ * (LSRN_ERR_STATE otherwise).  Synchronises; writes r to *rank_out if non-NULL. */
+lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out);
+
+/* Algorithm 1 steps 6-7 / Algorithm 2 steps 6-7 with LSQR (Paige and Saunders
+ * 1982; stopping rules S1/S2 with atol = btol = tol on the preconditioned
+ * problem), followed by opt.refine_max refinement steps.  Runs lsrn_sketch and
+ * lsrn_precond first if they have not run.  The plan may be solved for many b.
+ *   b     length m (host or device, FP64).
+ *   x     length n (host or device, FP64), written with the solution.
+ *   info  optional (NULL allowed), filled on return.
+ * Returns OK, NOT_CONVERGED (cap reached, x = last iterate) or an error.
+ * Rank 0 (A = 0) returns OK with x = 0.  Synchronises. */
+lsrn_status lsrn_solve_lsqr(lsrn_plan_t p, const double* b, double* x, lsrn_info* info);
+
+/* As lsrn_solve_lsqr, with Algorithm 3 (Chebyshev semi-iterative method):
+ * sigma_L, sigma_U from Theorem 4.5 with alpha = opt.cs_alpha, K + 1 steps with
+ * K = ceil((log tol - log 2) / log((sU - sL)/(sU + sL))), no inner products in
+ * the loop.  Returns DIVERGED if the final residual exceeds the initial one
+ * (the bounds did not hold); x then holds the last iterate.  INVALID_ARG if
+ * (1 - alpha) sqrt(s) <= sqrt(r) (no valid upper bound). */
+lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* info);
+
+/* Release everything the plan owns.  NULL is accepted.  Synchronises. */
+lsrn_status lsrn_plan_destroy(lsrn_plan_t p);
+
+/* Copy the sketch to `out` (host or device, FP64): for m >= n A~ (s x n,
+ * row-major); for m < n A~^T (s x m, row-major).  *rows/*cols receive the
+ * shape.  STATE before lsrn_sketch.  Synchronises. */
+lsrn_status lsrn_plan_get_sketch(lsrn_plan_t p, double* out, int64_t* rows, int64_t* cols);
+
+/* Copy the preconditioner N (n' x r, row-major; n' = n for m >= n) or M
+ * (m x r) to `out` and the r kept singular values of A~ (descending) to
+ * `sigma` (either may be NULL).  STATE before lsrn_precond.  Synchronises. */
+lsrn_status lsrn_plan_get_precond(lsrn_plan_t p, double* out, double* sigma, int64_t* rank);
+
+/* Entries G[i0:i0+rows, j0:j0+cols] of the drawing array of the sketching
+ * matrix (the draw for long-side index i and sketch index j; section 4.1
+ * step 2), row-major, FP64, into device or host memory `g`; optionally the
+ * unrounded binary32 normals into `z` (may be NULL).  Used to check the
+ * generator bit for bit.  Synchronises. */
+lsrn_status lsrn_generate_sketch_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t j0,
+                                       int64_t rows, int64_t cols, double* g, float* z,
+                                       void* stream);
+
+/* ---- serving: a request queue with admission by device-memory budget ----
+ * lsrn_submit copies the request (A, b, options) and returns a ticket at once;
+ * worker threads plan and solve admitted requests on their own streams while
+ * later requests keep arriving; lsrn_poll returns PENDING until the result is
+ * ready, then OK/error, copies x (length n) and info, and retires the ticket.
+ *   hbm_budget_bytes  device bytes that admitted requests may hold at once.
+ *   max_slots         requests that may run concurrently (>= 1).
+ *   solver            0 = LSQR, 1 = CS.
+ * QUEUE_FULL when a single request alone exceeds the budget.  The server is
+ * thread-safe.  lsrn_server_destroy waits for running requests. */
+lsrn_status lsrn_server_create(size_t hbm_budget_bytes, int32_t max_slots, lsrn_server_t* out);
+lsrn_status lsrn_submit(lsrn_server_t s, const lsrn_matrix* A, const double* b,
+                        const lsrn_options* opt, int32_t solver, uint64_t* ticket);
+lsrn_status lsrn_poll(lsrn_server_t s, uint64_t ticket, double* x_out, lsrn_info* info);
+lsrn_status lsrn_server_destroy(lsrn_server_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSRN_H */

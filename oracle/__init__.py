@@ -38,7 +38,8 @@ Readings of the paper that the oracle takes (each also listed in the design doc):
     Chebyshev iterations of Table 3.
   * r = rank(A~) is the numerical rank #{sigma_i > rcond * sigma_1}, rcond
     defaulting to max(s, n) * 2^-53 (max(m, n) * 2^-53 for x*).
-  * G's entries are the Box-Muller normals rounded to the grid 2^-12.
+  * G's entries are the Box-Muller normals rounded to the grid 2^-12, drawn as
+    Gamma[long-side index, sketch index]; G = Gamma^T (m >= n) or Gamma (m < n).
 """
 from __future__ import annotations
 
@@ -149,7 +150,11 @@ def normals(seed: int, tag: int, i0: int, j0: int, rows: int, cols: int) -> np.n
 
 def sketch_block(seed: int, i0: int, j0: int, rows: int, cols: int,
                  tag: int = TAG_SKETCH) -> np.ndarray:
-    """Entries G[i0:i0+rows, j0:j0+cols] of the sketching matrix (float64)."""
+    """Entries [i0:i0+rows, j0:j0+cols] of the drawing array Gamma of the
+    sketching matrix (float64): Gamma[l, i] is the draw for long-side index l
+    (row of A for m >= n, column of A for m < n) and sketch index i < s, so one
+    Philox call covers four consecutive sketch indices.  Algorithm 1 uses
+    G = Gamma^T (s x m), Algorithm 2 uses G = Gamma (n x s)."""
     g = np.empty((rows, cols), dtype=np.float64)
     _lib().orc_gauss_block(seed, tag, i0, j0, rows, cols, None, g.ctypes.data)
     return g
@@ -511,7 +516,7 @@ def lsrn(A, b, gamma: float = 2.0, seed: int = 0, solver: str = "lsqr", tol: flo
         B = np.vstack([A, lam * np.eye(n)]) if lam > 0 else A
         rhs = np.concatenate([b, np.zeros(n)]) if lam > 0 else b
         s = int(math.ceil(gamma * n))
-        G = sketch_block(seed, 0, 0, s, B.shape[0])            # s x (m or m+n)
+        G = sketch_block(seed, 0, 0, B.shape[0], s).T          # s x (m or m+n)
         At = G @ B                                              # s x n
         U_, sig, V_ = jacobi_svd(At)
         rc = default_rcond(s, n) if rcond is None else rcond

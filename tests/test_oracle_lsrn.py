@@ -146,7 +146,7 @@ def test_lemma43_spectrum_of_AN():
     x, info = O.lsrn(A, P.b, gamma=2.0, seed=3)
     s, r = info["s"], info["rank"]
     assert r == 20
-    G = O.sketch_block(3, 0, 0, s, 400)
+    G = O.sketch_block(3, 0, 0, 400, s).T
     sig_gu = np.linalg.svd(G @ P.meta["U"], compute_uv=False)
     sig_an = np.linalg.svd(A @ info["N"], compute_uv=False)
     assert np.allclose(np.sort(sig_an), np.sort(1.0 / sig_gu), rtol=1e-9)
