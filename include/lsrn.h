@@ -120,6 +120,10 @@ typedef struct lsrn_server_s* lsrn_server_t;
 /* Human-readable name of a status code (static storage). */
 const char* lsrn_status_string(lsrn_status s);
 
+/* Text describing the last CUDA error seen by this thread inside the library
+ * (file, line, call, CUDA message); empty if none.  Static thread-local storage. */
+const char* lsrn_last_error_message(void);
+
 /* Fill *opt with the defaults listed in lsrn_options.  INVALID_ARG if opt is NULL. */
 lsrn_status lsrn_default_options(lsrn_options* opt);
 

@@ -1,0 +1,393 @@
+"""Python binding of the LSRN C ABI (include/lsrn.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/liblsrn.so`` built from ``csrc/``.  Arrays may be numpy arrays (host)
+or torch tensors (host or CUDA); their data pointers are handed to the library
+unchanged.  If the library is missing or the GPU is unusable, the calls raise
+-- there is no CPU fallback.
+
+The names follow the C ABI: ``lsrn_plan``, ``lsrn_sketch``, ``lsrn_precond``,
+``lsrn_solve_lsqr``, ``lsrn_solve_cs``, ``lsrn_plan_destroy``,
+``lsrn_server_create``, ``lsrn_submit``, ``lsrn_poll``, ``lsrn_server_destroy``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblsrn.so")
+
+LSRN_OK = 0
+LSRN_PENDING = 1
+LSRN_ERR_INVALID_ARG = -1
+LSRN_ERR_OOM = -2
+LSRN_ERR_CUDA = -3
+LSRN_ERR_NOT_CONVERGED = -4
+LSRN_ERR_DIVERGED = -5
+LSRN_ERR_TIMEOUT = -6
+LSRN_ERR_QUEUE_FULL = -7
+LSRN_ERR_STATE = -8
+LSRN_ERR_UNSUPPORTED = -9
+
+LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
+LSRN_F64, LSRN_F32 = 0, 1
+LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED = 0, 1
+
+
+class lsrn_matrix(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("format", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("values", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p)]
+
+
+class lsrn_options(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("tol", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("rcond", ctypes.c_double), ("cs_alpha", ctypes.c_double),
+                ("refine_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("refine_max", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("sketch_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class lsrn_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("s", ctypes.c_int64),
+                ("rank", ctypes.c_int64), ("iterations", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("refine_iterations", ctypes.c_int32),
+                ("tall", ctypes.c_int32), ("istop", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("sigma_max_sketch", ctypes.c_double), ("sigma_min_sketch", ctypes.c_double),
+                ("sigma_L", ctypes.c_double), ("sigma_U", ctypes.c_double),
+                ("rnorm_est", ctypes.c_double), ("arnorm_est", ctypes.c_double),
+                ("anorm_est", ctypes.c_double), ("t_sketch_ms", ctypes.c_float),
+                ("t_precond_ms", ctypes.c_float), ("t_iter_ms", ctypes.c_float),
+                ("t_refine_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class LsrnError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {status_string(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lib = None
+
+_SIGS = {
+    "lsrn_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "lsrn_last_error_message": ([], ctypes.c_char_p),
+    "lsrn_default_options": ([ctypes.POINTER(lsrn_options)], ctypes.c_int),
+    "lsrn_plan": ([ctypes.POINTER(lsrn_matrix), ctypes.POINTER(lsrn_options), ctypes.c_void_p,
+                   ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "lsrn_sketch": ([ctypes.c_void_p], ctypes.c_int),
+    "lsrn_precond": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "lsrn_solve_lsqr": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.POINTER(lsrn_info)], ctypes.c_int),
+    "lsrn_solve_cs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.POINTER(lsrn_info)], ctypes.c_int),
+    "lsrn_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "lsrn_plan_get_sketch": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "lsrn_plan_get_precond": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "lsrn_generate_sketch_block": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                                   ctypes.c_int),
+    "lsrn_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+                           ctypes.c_int),
+    "lsrn_submit": ([ctypes.c_void_p, ctypes.POINTER(lsrn_matrix), ctypes.c_void_p,
+                     ctypes.POINTER(lsrn_options), ctypes.c_int32,
+                     ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "lsrn_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(lsrn_info)],
+                  ctypes.c_int),
+    "lsrn_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load_library():
+    """Load _build/liblsrn.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"LSRN CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_1109_5981_gb300.build.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().lsrn_status_string(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(status: int, where: str, allowed=(LSRN_OK,)) -> int:
+    if status not in allowed:
+        detail = load_library().lsrn_last_error_message().decode()
+        raise LsrnError(status, where, detail)
+    return status
+
+
+def default_options(**kw) -> lsrn_options:
+    o = lsrn_options()
+    load_library().lsrn_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k in ("lam", "lambda"):
+            k = "lambda_"
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+# --------------------------------------------------------------------------- #
+# array marshalling                                                            #
+# --------------------------------------------------------------------------- #
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return int(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_code(a) -> int:
+    dt = str(a.dtype)
+    if dt in ("float64", "torch.float64"):
+        return LSRN_F64
+    if dt in ("float32", "torch.float32"):
+        return LSRN_F32
+    raise TypeError(f"values must be float64 or float32, got {dt}")
+
+
+def dense_matrix(A, layout: str = "row") -> lsrn_matrix:
+    """Descriptor of a dense 2-D array (numpy or torch, host or device).
+    layout 'row': A[i, j] at i*ld + j (C order); 'col': A is given as its
+    transpose in C order (A^T[j, i]), i.e. A in column-major storage."""
+    mat = lsrn_matrix()
+    if layout == "row":
+        m, n = A.shape
+        ld = A.stride(0) if hasattr(A, "stride") and callable(A.stride) else A.strides[0] // A.itemsize
+        inner = A.stride(1) if hasattr(A, "stride") and callable(A.stride) else A.strides[1] // A.itemsize
+        fmt = LSRN_DENSE_ROWMAJOR
+    else:
+        n, m = A.shape
+        ld = A.stride(0) if hasattr(A, "stride") and callable(A.stride) else A.strides[0] // A.itemsize
+        inner = A.stride(1) if hasattr(A, "stride") and callable(A.stride) else A.strides[1] // A.itemsize
+        fmt = LSRN_DENSE_COLMAJOR
+    if inner != 1:
+        raise ValueError("the fastest dimension must be contiguous")
+    mat.m, mat.n, mat.ld, mat.nnz = m, n, ld, 0
+    mat.format = fmt
+    mat.dtype = _dtype_code(A)
+    mat.values = _ptr(A)
+    return mat
+
+
+def csr_matrix(m: int, n: int, row_ptr, col_idx, values) -> lsrn_matrix:
+    mat = lsrn_matrix()
+    mat.m, mat.n, mat.ld = m, n, 0
+    mat.nnz = int(values.shape[0])
+    mat.format = LSRN_CSR
+    mat.dtype = _dtype_code(values)
+    mat.values = _ptr(values)
+    mat.row_ptr = _ptr(row_ptr)
+    mat.col_idx = _ptr(col_idx)
+    return mat
+
+
+class Plan:
+    """Owns an lsrn_plan_t; keeps the arrays it was built from alive."""
+
+    def __init__(self, handle: int, keep: tuple, m: int, n: int):
+        self.handle = handle
+        self._keep = keep
+        self.m, self.n = m, n
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            load_library().lsrn_plan_destroy(self.handle)
+            self.handle = 0
+
+
+def lsrn_plan(A, opt: Optional[lsrn_options] = None, stream: int = 0, layout: str = "row",
+              csr: Optional[tuple] = None) -> Plan:
+    """lsrn_plan(): A is a dense array, or csr=(m, n, row_ptr, col_idx, values)."""
+    lib = load_library()
+    if csr is not None:
+        m, n, rp, ci, vals = csr
+        mat = csr_matrix(m, n, rp, ci, vals)
+        keep = (rp, ci, vals)
+    else:
+        mat = dense_matrix(A, layout)
+        keep = (A,)
+    h = ctypes.c_void_p()
+    o = opt if opt is not None else default_options()
+    _check(lib.lsrn_plan(ctypes.byref(mat), ctypes.byref(o), ctypes.c_void_p(stream),
+                         ctypes.byref(h)), "lsrn_plan")
+    return Plan(h.value, keep, mat.m, mat.n)
+
+
+def lsrn_sketch(plan: Plan) -> None:
+    _check(load_library().lsrn_sketch(plan.handle), "lsrn_sketch")
+
+
+def lsrn_precond(plan: Plan) -> int:
+    r = ctypes.c_int64()
+    _check(load_library().lsrn_precond(plan.handle, ctypes.byref(r)), "lsrn_precond")
+    return r.value
+
+
+def _solve(fn_name: str, plan: Plan, b, x=None, allow=(LSRN_OK,)):
+    lib = load_library()
+    if x is None:
+        x = np.empty(plan.n, dtype=np.float64) if isinstance(b, np.ndarray) else b.new_empty(plan.n)
+    info = lsrn_info()
+    st = getattr(lib, fn_name)(plan.handle, _ptr(b), _ptr(x), ctypes.byref(info))
+    _check(st, fn_name, allow)
+    d = info.as_dict()
+    d["status"] = st
+    return x, d
+
+
+def lsrn_solve_lsqr(plan: Plan, b, x=None, allow=(LSRN_OK,)):
+    """Returns (x, info dict)."""
+    return _solve("lsrn_solve_lsqr", plan, b, x, allow)
+
+
+def lsrn_solve_cs(plan: Plan, b, x=None, allow=(LSRN_OK,)):
+    return _solve("lsrn_solve_cs", plan, b, x, allow)
+
+
+def lsrn_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def lsrn_plan_get_sketch(plan: Plan) -> np.ndarray:
+    lib = load_library()
+    rows, cols = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.lsrn_plan_get_sketch(plan.handle, None, ctypes.byref(rows), ctypes.byref(cols)),
+           "lsrn_plan_get_sketch")
+    out = np.empty((rows.value, cols.value), dtype=np.float64)
+    _check(lib.lsrn_plan_get_sketch(plan.handle, out.ctypes.data, None, None),
+           "lsrn_plan_get_sketch")
+    return out
+
+
+def lsrn_plan_get_precond(plan: Plan):
+    """Returns (N or M as (q, r) array, sigma (r,))."""
+    lib = load_library()
+    r = ctypes.c_int64()
+    _check(lib.lsrn_plan_get_precond(plan.handle, None, None, ctypes.byref(r)),
+           "lsrn_plan_get_precond")
+    rank = r.value
+    rows, cols = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.lsrn_plan_get_sketch(plan.handle, None, ctypes.byref(rows), ctypes.byref(cols)),
+           "lsrn_plan_get_sketch")
+    N = np.empty((cols.value, rank), dtype=np.float64)
+    sig = np.empty(rank, dtype=np.float64)
+    _check(lib.lsrn_plan_get_precond(plan.handle, N.ctypes.data if rank else None,
+                                     sig.ctypes.data if rank else None, None),
+           "lsrn_plan_get_precond")
+    return N, sig
+
+
+def lsrn_generate_sketch_block(seed: int, tag: int, i0: int, j0: int, rows: int, cols: int,
+                               with_normals: bool = False):
+    """Entries of the drawing array of G (and the raw normals) from the GPU."""
+    lib = load_library()
+    g = np.empty((rows, cols), dtype=np.float64)
+    z = np.empty((rows, cols), dtype=np.float32) if with_normals else None
+    _check(lib.lsrn_generate_sketch_block(seed, tag, i0, j0, rows, cols, g.ctypes.data,
+                                          z.ctypes.data if z is not None else None, None),
+           "lsrn_generate_sketch_block")
+    return (g, z) if with_normals else g
+
+
+def solve(A, b, solver: str = "lsqr", layout: str = "row", csr=None, stream: int = 0,
+          x=None, allow=(LSRN_OK,), **options):
+    """Plan + sketch + precond + solve in one call; returns (x, info)."""
+    plan = lsrn_plan(A, default_options(**options), stream, layout, csr)
+    try:
+        if solver == "lsqr":
+            return lsrn_solve_lsqr(plan, b, x, allow)
+        if solver == "cs":
+            return lsrn_solve_cs(plan, b, x, allow)
+        raise ValueError(solver)
+    finally:
+        plan.close()
+
+
+# ---- serving ---------------------------------------------------------------
+class Server:
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(load_library().lsrn_server_create(hbm_budget_bytes, max_slots, ctypes.byref(h)),
+               "lsrn_server_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            load_library().lsrn_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lsrn_server_create(hbm_budget_bytes: int, max_slots: int = 4) -> Server:
+    return Server(hbm_budget_bytes, max_slots)
+
+
+def lsrn_submit(server: Server, A, b, opt: Optional[lsrn_options] = None, solver: int = 0,
+                layout: str = "row", csr=None) -> int:
+    if csr is not None:
+        m, n, rp, ci, vals = csr
+        mat = csr_matrix(m, n, rp, ci, vals)
+    else:
+        mat = dense_matrix(A, layout)
+    o = opt if opt is not None else default_options()
+    t = ctypes.c_uint64()
+    _check(load_library().lsrn_submit(server.handle, ctypes.byref(mat), _ptr(b), ctypes.byref(o),
+                                      solver, ctypes.byref(t)), "lsrn_submit")
+    return t.value
+
+
+def lsrn_poll(server: Server, ticket: int, x_out):
+    info = lsrn_info()
+    st = load_library().lsrn_poll(server.handle, ticket, _ptr(x_out), ctypes.byref(info))
+    return st, info.as_dict()
+
+
+def lsrn_server_destroy(server: Server) -> None:
+    server.close()

@@ -1,0 +1,522 @@
+// Iteration kernels (Algorithm 1/2 step 6 with LSQR or Algorithm 3).
+//
+// The fused pass streams the row-major matrix X (A for m >= n, A^T for m < n)
+// once and, per row i, forms the dot product d_i = X_i . vin, turns it into a
+// row coefficient t_i (the row mode: an LSQR or Chebyshev update of the state
+// held for that row), and accumulates sum_i t_i X_i.  One HBM pass therefore
+// applies both X and X^T: for m >= n it computes A(Nv) and A^T u in one go,
+// for m < n A^T(Mu) and A t.  Per-CTA partial vectors are summed in a fixed
+// order by a second kernel, so results do not depend on scheduling.
+#include <algorithm>
+#include <cmath>
+
+#include "lsrn_device.cuh"
+#include "lsrn_internal.h"
+
+namespace lsrn {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Coef {
+  double c0, c1;
+};
+
+__device__ __forceinline__ double row_coef(const RowArgs& a, const Coef& k, int64_t i, double d,
+                                           bool writer, double& ss) {
+  double t = 0.0;
+  switch (a.mode) {
+    case RM_ACC_STATE:
+      t = a.st0[i];
+      return t;
+    case RM_LSQR_TALL:
+      t = d - k.c0 * a.st0[i];
+      if (writer) a.st0[i] = t;
+      ss = fma(t, t, ss);
+      return t;
+    case RM_CS_TALL:
+      t = a.st0[i] - k.c0 * d;
+      if (writer) a.st0[i] = t;
+      ss = fma(t, t, ss);
+      return t;
+    case RM_APPLY:
+      return d;
+    case RM_FAT_INIT:
+      t = a.sx * d;
+      if (writer) a.st0[i] = t;
+      ss = fma(t, t, ss);
+      return a.sx * t;
+    case RM_FAT_LSQR:
+      t = a.sx * d - k.c0 * a.st0[i];
+      if (writer) a.st0[i] = t;
+      ss = fma(t, t, ss);
+      return a.sx * t;
+    case RM_FAT_CS:
+      t = k.c0 * a.st0[i] + a.sx * d;
+      if (writer) {
+        a.st0[i] = t;
+        a.st1[i] = fma(k.c1, t, a.st1[i]);
+      }
+      return a.sx * t;
+  }
+  return 0.0;
+}
+
+// TPR threads cover one row (2 * TPR * SLOTS columns max); R rows per step per group.
+template <int TPR, int SLOTS, int R>
+__global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __restrict__ X, int64_t rows,
+                                                            int C, int64_t ldx,
+                                                            const double* __restrict__ vin,
+                                                            RowArgs args, double* __restrict__ pvec,
+                                                            double* __restrict__ pscal,
+                                                            const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  constexpr int GPC = kThreads / TPR;
+  constexpr int WPG = TPR / 32 > 0 ? TPR / 32 : 1;   // warps per group (TPR >= 32)
+  __shared__ double red[2][kThreads / 32][R];
+  __shared__ double cta_acc[(GPC > 1) ? GPC : 1][(GPC > 1) ? 2 * TPR * SLOTS : 1];
+  __shared__ double sred[kThreads / 32];
+  const int tid = threadIdx.x, gid = tid / TPR, gl = tid % TPR;
+  const bool need_dot = args.mode != RM_ACC_STATE;
+  Coef k{0.0, 0.0};
+  if (args.coef) {
+    k.c0 = args.coef[0];
+    k.c1 = args.coef[1];
+  }
+  double w[SLOTS][2], acc[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int c = 2 * gl + 2 * TPR * s;
+    w[s][0] = (need_dot && c < C) ? vin[c] : 0.0;
+    w[s][1] = (need_dot && c + 1 < C) ? vin[c + 1] : 0.0;
+    acc[s][0] = acc[s][1] = 0.0;
+  }
+  double ss = 0.0;
+  const int64_t step = (int64_t)gridDim.x * GPC * R;
+  int buf = 0;
+  for (int64_t base = (int64_t)blockIdx.x * GPC * R; base < rows; base += step) {
+    double a[R][SLOTS][2];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = base + gid * R + r;
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int c = 2 * gl + 2 * TPR * s;
+        if (i < rows && c + 1 < C) {
+          const double2 v = *reinterpret_cast<const double2*>(X + i * ldx + c);
+          a[r][s][0] = v.x;
+          a[r][s][1] = v.y;
+        } else if (i < rows && c < C) {
+          a[r][s][0] = X[i * ldx + c];
+          a[r][s][1] = 0.0;
+        } else {
+          a[r][s][0] = a[r][s][1] = 0.0;
+        }
+      }
+    }
+    double d[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double t = 0.0;
+      if (need_dot) {
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) t = fma(a[r][s][0], w[s][0], fma(a[r][s][1], w[s][1], t));
+      }
+      d[r] = t;
+    }
+    if (need_dot) {
+      if (TPR <= 32) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[r] = group_sum<(TPR < 32 ? TPR : 32)>(d[r]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[r] = group_sum<32>(d[r]);
+        if ((tid & 31) == 0) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) red[buf][tid >> 5][r] = d[r];
+        }
+        __syncthreads();
+        const int w0 = gid * WPG;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          double t = 0.0;
+          for (int q = 0; q < WPG; ++q) t += red[buf][w0 + q][r];
+          d[r] = t;
+        }
+        buf ^= 1;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = base + gid * R + r;
+      double tacc = 0.0;
+      if (i < rows) {
+        double ss_dummy = 0.0;
+        tacc = row_coef(args, k, i, d[r], gl == 0, gl == 0 ? ss : ss_dummy);
+      }
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        acc[s][0] = fma(tacc, a[r][s][0], acc[s][0]);
+        acc[s][1] = fma(tacc, a[r][s][1], acc[s][1]);
+      }
+    }
+  }
+  // combine the groups of this CTA and write the CTA's partial vector
+  double* out = pvec + (int64_t)blockIdx.x * C;
+  if (GPC > 1) {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int c = 2 * gl + 2 * TPR * s;
+      cta_acc[gid][2 * TPR * s + 2 * gl] = acc[s][0];
+      cta_acc[gid][2 * TPR * s + 2 * gl + 1] = acc[s][1];
+      (void)c;
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += kThreads) {
+      double t = 0.0;
+      for (int g = 0; g < GPC; ++g) t += cta_acc[g][c];
+      out[c] = t;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int c = 2 * gl + 2 * TPR * s;
+      if (c < C) out[c] = acc[s][0];
+      if (c + 1 < C) out[c + 1] = acc[s][1];
+    }
+  }
+  ss = group_sum<32>(ss);
+  if ((tid & 31) == 0) sred[tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += sred[q];
+    pscal[blockIdx.x] = t;
+  }
+}
+
+// Rows appended to X by the Tikhonov augmentation: row (xrows + j) = coef * e_j.
+// Writes one extra partial slot (vector of length C and one scalar).
+__global__ void extra_rows_kernel(int64_t nextra, int64_t xrows, int C, double coef,
+                                  const double* __restrict__ vin, RowArgs args,
+                                  double* __restrict__ pvec_slot, double* __restrict__ pscal_slot,
+                                  const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  __shared__ double sred[32];
+  Coef k{0.0, 0.0};
+  if (args.coef) {
+    k.c0 = args.coef[0];
+    k.c1 = args.coef[1];
+  }
+  RowArgs a1 = args;
+  a1.sx = 1.0;   // appended rows are coef * e_j, never scaled by 1/lambda
+  const bool need_dot = args.mode != RM_ACC_STATE;
+  double ss = 0.0;
+  for (int64_t j = threadIdx.x; j < C; j += blockDim.x) {
+    double v = 0.0;
+    if (j < nextra) {
+      const double d = need_dot ? coef * vin[j] : 0.0;
+      const double t = row_coef(a1, k, xrows + j, d, true, ss);
+      v = coef * t;
+    }
+    pvec_slot[j] = v;
+  }
+  ss = group_sum<32>(ss);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += sred[q];
+    *pscal_slot = t;
+  }
+}
+
+// Double-double pass: m >= n: r_i = b_i - X_i . vin (dd), acc += r_i X_i (dd);
+// m < n (bvec == nullptr): acc += (sx * vin_row[i]) X_i (dd), no dot.
+template <int TPR, int SLOTS>
+__global__ void __launch_bounds__(kThreads) dd_pass_kernel(const double* __restrict__ X, int64_t rows,
+                                                           int C, int64_t ldx,
+                                                           const double* __restrict__ vin,
+                                                           const double* __restrict__ bvec,
+                                                           double* __restrict__ rout, double sx,
+                                                           double* __restrict__ phi,
+                                                           double* __restrict__ plo) {
+  constexpr int GPC = kThreads / TPR;
+  constexpr int WPG = TPR / 32 > 0 ? TPR / 32 : 1;
+  __shared__ double redh[2][kThreads / 32], redl[2][kThreads / 32];
+  __shared__ double cta_h[(GPC > 1) ? GPC : 1][(GPC > 1) ? 2 * TPR * SLOTS : 1];
+  __shared__ double cta_l[(GPC > 1) ? GPC : 1][(GPC > 1) ? 2 * TPR * SLOTS : 1];
+  const int tid = threadIdx.x, gid = tid / TPR, gl = tid % TPR;
+  const bool tall = bvec != nullptr;
+  double w[SLOTS][2], ah[SLOTS][2], al[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int c = 2 * gl + 2 * TPR * s;
+    w[s][0] = (tall && c < C) ? vin[c] : 0.0;
+    w[s][1] = (tall && c + 1 < C) ? vin[c + 1] : 0.0;
+    ah[s][0] = ah[s][1] = al[s][0] = al[s][1] = 0.0;
+  }
+  const int64_t step = (int64_t)gridDim.x * GPC;
+  int buf = 0;
+  for (int64_t base = (int64_t)blockIdx.x * GPC; base < rows; base += step) {
+    const int64_t i = base + gid;
+    double a[SLOTS][2];
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int c = 2 * gl + 2 * TPR * s;
+      a[s][0] = (i < rows && c < C) ? X[i * ldx + c] : 0.0;
+      a[s][1] = (i < rows && c + 1 < C) ? X[i * ldx + c + 1] : 0.0;
+    }
+    double t = 0.0;
+    if (tall) {
+      double hi = 0.0, lo = 0.0;
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        dd_add_prod(hi, lo, -a[s][0], w[s][0]);
+        dd_add_prod(hi, lo, -a[s][1], w[s][1]);
+      }
+      if (TPR <= 32) {
+        group_sum_dd<(TPR < 32 ? TPR : 32)>(hi, lo);
+      } else {
+        group_sum_dd<32>(hi, lo);
+        if ((tid & 31) == 0) {
+          redh[buf][tid >> 5] = hi;
+          redl[buf][tid >> 5] = lo;
+        }
+        __syncthreads();
+        hi = 0.0;
+        lo = 0.0;
+        for (int q = 0; q < WPG; ++q) dd_add(hi, lo, redh[buf][gid * WPG + q], redl[buf][gid * WPG + q]);
+        buf ^= 1;
+      }
+      if (i < rows) {
+        dd_add(hi, lo, bvec[i], 0.0);
+        t = hi + lo;
+        if (gl == 0) rout[i] = t;
+      }
+    } else if (i < rows) {
+      t = sx * vin[i];
+    }
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      dd_add_prod(ah[s][0], al[s][0], t, a[s][0]);
+      dd_add_prod(ah[s][1], al[s][1], t, a[s][1]);
+    }
+  }
+  double* oh = phi + (int64_t)blockIdx.x * C;
+  double* ol = plo + (int64_t)blockIdx.x * C;
+  if (GPC > 1) {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      cta_h[gid][2 * TPR * s + 2 * gl] = ah[s][0];
+      cta_h[gid][2 * TPR * s + 2 * gl + 1] = ah[s][1];
+      cta_l[gid][2 * TPR * s + 2 * gl] = al[s][0];
+      cta_l[gid][2 * TPR * s + 2 * gl + 1] = al[s][1];
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += kThreads) {
+      double h = 0.0, l = 0.0;
+      for (int g = 0; g < GPC; ++g) dd_add(h, l, cta_h[g][c], cta_l[g][c]);
+      oh[c] = h;
+      ol[c] = l;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int c = 2 * gl + 2 * TPR * s;
+      if (c < C) {
+        oh[c] = ah[s][0];
+        ol[c] = al[s][0];
+      }
+      if (c + 1 < C) {
+        oh[c + 1] = ah[s][1];
+        ol[c + 1] = al[s][1];
+      }
+    }
+  }
+}
+
+// Extra (ridge) rows of the double-double pass, written as one more partial slot.
+//  m >= n: row xrows+j = coef e_j: r = 0 - coef x_j, acc_j += coef * r
+//  m <  n: row xrows+i = e_i:      acc_i += vin_row[xrows + i]
+__global__ void dd_extra_kernel(int64_t nextra, int64_t xrows, int C, double coef,
+                                const double* __restrict__ vin, bool tall,
+                                double* __restrict__ rout, double* __restrict__ ph,
+                                double* __restrict__ pl) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < C;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double h = 0.0, l = 0.0;
+    if (j < nextra) {
+      if (tall) {
+        double rh = 0.0, rl = 0.0;
+        dd_add_prod(rh, rl, -coef, vin[j]);
+        const double r = rh + rl;
+        rout[xrows + j] = r;
+        dd_add_prod(h, l, coef, r);
+      } else {
+        h = vin[xrows + j];
+      }
+    }
+    ph[j] = h;
+    pl[j] = l;
+  }
+}
+
+__global__ void reduce_kernel(const double* __restrict__ pvec, int nslots, int64_t C,
+                              double* __restrict__ out, const double* __restrict__ pscal,
+                              double* __restrict__ scal_out, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C) {
+    double t = 0.0;
+    for (int s = 0; s < nslots; ++s) t += pvec[(int64_t)s * C + c];
+    out[c] = t;
+  }
+  if (scal_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int s = 0; s < nslots; ++s) t += pscal[s];
+    *scal_out = t;
+  }
+}
+
+__global__ void reduce_dd_kernel(const double* __restrict__ ph, const double* __restrict__ pl,
+                                 int nslots, int64_t C, double* __restrict__ oh,
+                                 double* __restrict__ ol) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double h = 0.0, l = 0.0;
+  for (int s = 0; s < nslots; ++s) dd_add(h, l, ph[(int64_t)s * C + c], pl[(int64_t)s * C + c]);
+  oh[c] = h;
+  if (ol) ol[c] = l;
+}
+
+// Warp per row: out[i] = c0 * (M_i . v) + c1 * y[i]; y2[i] += c2 * out[i].
+__global__ void __launch_bounds__(256) gemv_kernel(const double* __restrict__ M, int64_t R, int64_t C,
+                                                   const double* __restrict__ v, double* out,
+                                                   const double* y, double* y2,
+                                                   const double* __restrict__ c,
+                                                   const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= R) return;
+  const double* m = M + row * C;
+  double acc = 0.0;
+  for (int64_t j = lane; j < C; j += 32) acc = fma(m[j], v[j], acc);
+  acc = group_sum<32>(acc);
+  if (lane == 0) {
+    double o = c[0] * acc;
+    if (y) o = fma(c[1], y[row], o);
+    out[row] = o;
+    if (y2) y2[row] = fma(c[2], o, y2[row]);
+  }
+}
+
+}  // namespace
+
+static int pick_layout(int64_t C, int* tpr, int* slots) {
+  if (C <= 64) { *tpr = 32; *slots = 1; }
+  else if (C <= 128) { *tpr = 32; *slots = 2; }
+  else if (C <= 256) { *tpr = 64; *slots = 2; }
+  else if (C <= 512) { *tpr = 128; *slots = 2; }
+  else if (C <= 1024) { *tpr = 256; *slots = 2; }
+  else if (C <= 2048) { *tpr = 256; *slots = 4; }
+  else if (C <= 4096) { *tpr = 256; *slots = 8; }
+  else return -1;
+  return 0;
+}
+
+int pass_blocks(int64_t rows, int64_t C) {
+  int tpr, slots;
+  if (pick_layout(C, &tpr, &slots) != 0) return 0;
+  const int64_t gpc = kThreads / tpr;
+  const int64_t per = gpc * 2;
+  const int64_t want = (rows + per - 1) / per;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * num_sms()));
+}
+
+lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
+                            double* pscal, const int* done) {
+  int tpr, slots;
+  if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
+  const int C = (int)p->xcols;
+  dim3 grid(p->nblk);
+#define LSRN_ROWPASS(T, S, R)                                                                   \
+  row_pass_kernel<T, S, R><<<grid, kThreads, 0, p->stream>>>(p->X, p->xrows, C, p->ldx, vin, a, \
+                                                             pvec, pscal, done)
+  if (tpr == 32 && slots == 1) LSRN_ROWPASS(32, 1, 4);
+  else if (tpr == 32) LSRN_ROWPASS(32, 2, 4);
+  else if (tpr == 64) LSRN_ROWPASS(64, 2, 4);
+  else if (tpr == 128) LSRN_ROWPASS(128, 2, 4);
+  else if (slots == 2) LSRN_ROWPASS(256, 2, 4);
+  else if (slots == 4) LSRN_ROWPASS(256, 4, 2);
+  else LSRN_ROWPASS(256, 8, 1);
+#undef LSRN_ROWPASS
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status launch_extra_rows(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
+                              double* pscal, const int* done) {
+  if (p->extra_rows == 0) return LSRN_OK;
+  extra_rows_kernel<<<1, 1024, 0, p->stream>>>(p->extra_rows, p->xrows, (int)p->xcols,
+                                               p->extra_coef, vin, a, pvec + (int64_t)p->nblk * p->xcols,
+                                               pscal + p->nblk, done);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
+                           double* pvec_hi, double* pvec_lo, const int* done) {
+  (void)done;
+  int tpr, slots;
+  if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
+  const int C = (int)p->xcols;
+  dim3 grid(p->nblk);
+#define LSRN_DDPASS(T, S)                                                                       \
+  dd_pass_kernel<T, S><<<grid, kThreads, 0, p->stream>>>(p->X, p->xrows, C, p->ldx, vin, bvec,   \
+                                                         rout, p->xscale, pvec_hi, pvec_lo)
+  if (tpr == 32 && slots == 1) LSRN_DDPASS(32, 1);
+  else if (tpr == 32) LSRN_DDPASS(32, 2);
+  else if (tpr == 64) LSRN_DDPASS(64, 2);
+  else if (tpr == 128) LSRN_DDPASS(128, 2);
+  else if (slots == 2) LSRN_DDPASS(256, 2);
+  else if (slots == 4) LSRN_DDPASS(256, 4);
+  else LSRN_DDPASS(256, 8);
+#undef LSRN_DDPASS
+  if (p->extra_rows > 0) {
+    dd_extra_kernel<<<(unsigned)((p->xcols + 255) / 256), 256, 0, p->stream>>>(
+        p->extra_rows, p->xrows, C, p->extra_coef, vin, bvec != nullptr, rout,
+        pvec_hi + (int64_t)p->nblk * C, pvec_lo + (int64_t)p->nblk * C);
+  }
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status launch_reduce(const double* pvec, int nslots, int64_t C, double* out,
+                          const double* pscal, double* scal_out, const int* done, cudaStream_t st) {
+  reduce_kernel<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(pvec, nslots, C, out, pscal, scal_out,
+                                                             done);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status launch_reduce_dd(const double* phi, const double* plo, int nslots, int64_t C,
+                             double* out_hi, double* out_lo, cudaStream_t st) {
+  reduce_dd_kernel<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(phi, plo, nslots, C, out_hi,
+                                                                out_lo);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, double* out,
+                        const double* y, double* y2, const double* c, const int* done,
+                        cudaStream_t st) {
+  if (R == 0) return LSRN_OK;
+  gemv_kernel<<<(unsigned)((R * 32 + 255) / 256), 256, 0, st>>>(M, R, C, v, out, y, y2, c, done);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+}  // namespace lsrn

@@ -1,0 +1,325 @@
+// Preconditioner (Algorithm 1 steps 4-5, Algorithm 2 steps 4-5) on the device.
+//
+// Input: the sketch Xs (S x Q, row-major, S > Q): A~ for m >= n, A~^T for m < n.
+// 1. Householder QR of Xs -> R (Q x Q upper triangular); Q is not formed.
+// 2. One-sided (Hestenes) Jacobi on Y = R^T: rotate pairs of columns of Y
+//    (= rows of R, contiguous in memory) until all pairs are orthogonal to
+//    |y_a . y_b| <= tol ||y_a|| ||y_b||; parallel round-robin ordering, one
+//    kernel per round.  With Y J = W (orthogonal columns, norms sigma_j),
+//    R = J Sigma U_W^T, so the right singular vectors of Xs are W Sigma^-1.
+// 3. sigma sorted descending, rank r = #{sigma_j > rcond * sigma_1},
+//    N = V~ Sigma~^-1 = W_r Sigma_r^-2 (Q x r), also stored transposed.
+#include <algorithm>
+#include <cmath>
+
+#include "lsrn_device.cuh"
+#include "lsrn_internal.h"
+
+namespace lsrn {
+
+namespace {
+
+// Reflector for column k: H = I - tau v v^T, v_k = 1, annihilates X[k+1:, k].
+__global__ void __launch_bounds__(256) hh_reflector_kernel(double* __restrict__ X, int64_t S,
+                                                           int64_t Q, int64_t k,
+                                                           double* __restrict__ tau) {
+  __shared__ double red[8];
+  __shared__ double s_scal;
+  const int tid = threadIdx.x;
+  double ss = 0.0;
+  for (int64_t i = k + 1 + tid; i < S; i += 256) {
+    const double x = X[i * Q + k];
+    ss = fma(x, x, ss);
+  }
+  ss = group_sum<32>(ss);
+  if ((tid & 31) == 0) red[tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    const double alpha = X[k * Q + k];
+    double tk = 0.0, scal = 0.0;
+    if (t > 0.0) {
+      const double nrm = sqrt(alpha * alpha + t);
+      const double beta = alpha >= 0.0 ? -nrm : nrm;
+      tk = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+      X[k * Q + k] = beta;
+    }
+    tau[k] = tk;
+    s_scal = scal;
+  }
+  __syncthreads();
+  const double scal = s_scal;
+  if (scal != 0.0)
+    for (int64_t i = k + 1 + tid; i < S; i += 256) X[i * Q + k] *= scal;
+}
+
+// wpart[rb][c] = sum_{i in row block rb, i >= k} v_i X[i, c] for c in (k, Q)
+__global__ void __launch_bounds__(128) hh_w_kernel(const double* __restrict__ X, int64_t S,
+                                                   int64_t Q, int64_t k, int64_t rpb,
+                                                   double* __restrict__ wpart,
+                                                   const double* __restrict__ tau) {
+  if (tau[k] == 0.0) return;
+  const int64_t c = k + 1 + (int64_t)blockIdx.x * 128 + threadIdx.x;
+  const int64_t r0 = k + (int64_t)blockIdx.y * rpb;
+  const int64_t r1 = min(S, r0 + rpb);
+  double acc = 0.0;
+  if (c < Q) {
+    for (int64_t i = r0; i < r1; ++i) {
+      const double v = (i == k) ? 1.0 : X[i * Q + k];
+      acc = fma(v, X[i * Q + c], acc);
+    }
+    wpart[(int64_t)blockIdx.y * Q + c] = acc;
+  }
+}
+
+// X[i, c] -= tau v_i w_c with w_c = sum_rb wpart[rb][c]
+__global__ void __launch_bounds__(128) hh_update_kernel(double* __restrict__ X, int64_t S, int64_t Q,
+                                                        int64_t k, int64_t rpb, int nrb,
+                                                        const double* __restrict__ wpart,
+                                                        const double* __restrict__ tau) {
+  const double tk = tau[k];
+  if (tk == 0.0) return;
+  const int64_t c = k + 1 + (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (c >= Q) return;
+  double w = 0.0;
+  for (int b = 0; b < nrb; ++b) w += wpart[(int64_t)b * Q + c];
+  const double t = tk * w;
+  const int64_t r0 = k + (int64_t)blockIdx.y * rpb;
+  const int64_t r1 = min(S, r0 + rpb);
+  for (int64_t i = r0; i < r1; ++i) {
+    const double v = (i == k) ? 1.0 : X[i * Q + k];
+    X[i * Q + c] = fma(-v, t, X[i * Q + c]);
+  }
+}
+
+// W[j][c] = R[j][c] (upper triangle of X), zero below the diagonal
+__global__ void extract_r_kernel(const double* __restrict__ X, int64_t Q, double* __restrict__ W) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Q * Q) return;
+  const int64_t j = idx / Q, c = idx % Q;
+  W[idx] = (c >= j) ? X[j * Q + c] : 0.0;
+}
+
+// One round of the parallel one-sided Jacobi sweep: warp per pair of rows of W.
+// Round-robin (circle) schedule over P (even) players: pair 0 = (P-1, t),
+// pair k >= 1 = ((t + k) mod (P-1), (t - k + P - 1) mod (P-1)).
+__global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ W, int64_t Q, int P,
+                                                           int t, double tol,
+                                                           int* __restrict__ rot_count) {
+  const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= P / 2) return;
+  int a, b;
+  if (warp == 0) {
+    a = P - 1;
+    b = t;
+  } else {
+    a = (t + warp) % (P - 1);
+    b = (t - warp + P - 1) % (P - 1);
+  }
+  if (a >= Q || b >= Q) return;
+  if (a > b) {
+    const int tmp = a;
+    a = b;
+    b = tmp;
+  }
+  double* wa = W + (int64_t)a * Q;
+  double* wb = W + (int64_t)b * Q;
+  double aa = 0.0, bb = 0.0, ab = 0.0;
+  for (int64_t c = lane; c < Q; c += 32) {
+    const double x = wa[c], y = wb[c];
+    aa = fma(x, x, aa);
+    bb = fma(y, y, bb);
+    ab = fma(x, y, ab);
+  }
+  aa = group_sum<32>(aa);
+  bb = group_sum<32>(bb);
+  ab = group_sum<32>(ab);
+  if (aa == 0.0 || bb == 0.0) return;
+  if (fabs(ab) <= tol * sqrt(aa) * sqrt(bb)) return;
+  const double zeta = (bb - aa) / (2.0 * ab);
+  double tt;
+  if (fabs(zeta) > 1e150) {
+    tt = 0.5 / zeta;
+  } else {
+    tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  }
+  const double cs = 1.0 / sqrt(1.0 + tt * tt);
+  const double sn = cs * tt;
+  for (int64_t c = lane; c < Q; c += 32) {
+    const double x = wa[c], y = wb[c];
+    wa[c] = cs * x - sn * y;
+    wb[c] = sn * x + cs * y;
+  }
+  if (lane == 0) atomicAdd(rot_count, 1);
+}
+
+__global__ void row_norms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= Q) return;
+  double acc = 0.0;
+  for (int64_t c = lane; c < Q; c += 32) {
+    const double x = W[row * Q + c];
+    acc = fma(x, x, acc);
+  }
+  acc = group_sum<32>(acc);
+  if (lane == 0) nrm[row] = sqrt(acc);
+}
+
+// Stable descending order of the norms, rank count, sigma extremes.
+__global__ void __launch_bounds__(1024) sort_rank_kernel(const double* __restrict__ nrm, int64_t Q,
+                                                         double rcond, int* __restrict__ perm,
+                                                         double* __restrict__ sig,
+                                                         int* __restrict__ rank_out) {
+  __shared__ double smax[32];
+  __shared__ int scount[32];
+  const int tid = threadIdx.x;
+  double mx = 0.0;
+  for (int64_t j = tid; j < Q; j += 1024) mx = fmax(mx, nrm[j]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) smax[tid >> 5] = mx;
+  __syncthreads();
+  if (tid < 32) {
+    double v = smax[tid];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (tid == 0) smax[0] = v;
+  }
+  __syncthreads();
+  const double sigmax = smax[0];
+  int cnt = 0;
+  for (int64_t j = tid; j < Q; j += 1024) {
+    const double sj = nrm[j];
+    int64_t pos = 0;
+    for (int64_t k = 0; k < Q; ++k) {
+      const double sk = nrm[k];
+      pos += (sk > sj) || (sk == sj && k < j);
+    }
+    perm[pos] = (int)j;
+    sig[pos] = sj;
+    cnt += (sigmax > 0.0 && sj > rcond * sigmax) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  __syncthreads();
+  if ((tid & 31) == 0) scount[tid >> 5] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int w = 0; w < 32; ++w) t += scount[w];
+    *rank_out = t;
+  }
+}
+
+// N[i][k] = W[perm[k]][i] / sig[k]^2 ; NT[k][i] = same  (i < Q, k < r)
+__global__ void form_n_kernel(const double* __restrict__ W, int64_t Q, const int* __restrict__ perm,
+                              const double* __restrict__ sig, int64_t r, double* __restrict__ N,
+                              double* __restrict__ NT) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Q * r) return;
+  const int64_t k = idx / Q, i = idx % Q;
+  const double s = sig[k];
+  const double v = W[(int64_t)perm[k] * Q + i] / (s * s);
+  NT[k * Q + i] = v;
+  N[i * r + k] = v;
+}
+
+}  // namespace
+
+lsrn_status run_precond(Plan* p) {
+  cudaStream_t st = p->stream;
+  const int64_t S = p->s, Q = p->q;
+  double* X = p->Xs;
+  // 1. Householder QR (one column at a time).
+  double* wpart = p->pvec;   // reuse pass partial buffer: needs nrb * Q doubles
+  const int64_t cap_rows = std::max<int64_t>(1, (int64_t)(p->nblk + 1) * p->xcols / std::max<int64_t>(Q, 1));
+  for (int64_t k = 0; k < Q; ++k) {
+    hh_reflector_kernel<<<1, 256, 0, st>>>(X, S, Q, k, p->tau);
+    const int64_t ncols = Q - k - 1;
+    if (ncols <= 0) continue;
+    const int64_t cblk = (ncols + 127) / 128;
+    const int64_t rows = S - k;
+    int64_t nrb = std::max<int64_t>(1, (2 * num_sms() + cblk - 1) / cblk);
+    nrb = std::min<int64_t>(nrb, (rows + 63) / 64);
+    nrb = std::min<int64_t>(nrb, cap_rows);
+    const int64_t rpb = (rows + nrb - 1) / nrb;
+    nrb = (rows + rpb - 1) / rpb;
+    dim3 grid((unsigned)cblk, (unsigned)nrb);
+    hh_w_kernel<<<grid, 128, 0, st>>>(X, S, Q, k, rpb, wpart, p->tau);
+    hh_update_kernel<<<grid, 128, 0, st>>>(X, S, Q, k, rpb, (int)nrb, wpart, p->tau);
+  }
+  LSRN_CUDA_TRY(cudaGetLastError());
+  // 2. One-sided Jacobi on the rows of R.
+  const int64_t QQ = Q * Q;
+  extract_r_kernel<<<(unsigned)((QQ + 255) / 256), 256, 0, st>>>(X, Q, p->Wj);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  const int P = (int)(Q + (Q & 1));
+  const double tol = (double)std::max(S, Q) * 0x1p-53;
+  const int warps_per_round = P / 2;
+  const unsigned rblocks = (unsigned)((warps_per_round * 32 + 255) / 256);
+  int* rot = p->iscal + IC_ROT;
+  int host_rot = 0;
+  int sweeps = 0;
+  const int max_sweeps = 40;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  if (P > 1) {
+    LSRN_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < P - 1; ++t)
+      jacobi_round_kernel<<<rblocks, 256, 0, st>>>(p->Wj, Q, P, t, tol, rot);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess) {
+      record_cuda_error(ce, "capture jacobi sweep", __FILE__, __LINE__);
+      return LSRN_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      record_cuda_error(ce, "instantiate jacobi sweep", __FILE__, __LINE__);
+      return LSRN_ERR_CUDA;
+    }
+    do {
+      cudaMemsetAsync(rot, 0, sizeof(int), st);
+      cudaGraphLaunch(gexec, st);
+      cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaError_t se = cudaStreamSynchronize(st);
+      if (se != cudaSuccess) {
+        cudaGraphExecDestroy(gexec);
+        cudaGraphDestroy(graph);
+        record_cuda_error(se, "jacobi sweep", __FILE__, __LINE__);
+        return LSRN_ERR_CUDA;
+      }
+      ++sweeps;
+    } while (host_rot > 0 && sweeps < max_sweeps);
+    cudaGraphExecDestroy(gexec);
+    cudaGraphDestroy(graph);
+  }
+  p->sweeps = sweeps;
+  if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;
+  // 3. sigma, order, rank, N.
+  row_norms_kernel<<<(unsigned)((Q * 32 + 255) / 256), 256, 0, st>>>(p->Wj, Q, p->tmpq);
+  const double rcond = p->opt.rcond >= 0.0 ? p->opt.rcond : (double)std::max(S, Q) * 0x1p-53;
+  sort_rank_kernel<<<1, 1024, 0, st>>>(p->tmpq, Q, rcond, p->perm, p->sig, p->iscal + IC_CAP);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  int r = 0;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(&r, p->iscal + IC_CAP, sizeof(int), cudaMemcpyDeviceToHost, st));
+  double smax = 0.0;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(&smax, p->sig, sizeof(double), cudaMemcpyDeviceToHost, st));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+  p->rank = r;
+  p->sigma_max = smax;
+  p->sigma_min = 0.0;
+  if (r > 0) {
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&p->sigma_min, p->sig + (r - 1), sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+    const int64_t tot = Q * (int64_t)r;
+    form_n_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p->Wj, Q, p->perm, p->sig, r,
+                                                                   p->Nm, p->NT);
+    LSRN_CUDA_TRY(cudaGetLastError());
+    LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return LSRN_OK;
+}
+
+}  // namespace lsrn

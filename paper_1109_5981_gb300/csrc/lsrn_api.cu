@@ -1,0 +1,495 @@
+// C ABI of the LSRN library: plan management and the solve entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "lsrn_device.cuh"
+#include "lsrn_internal.h"
+
+namespace lsrn {
+
+lsrn_status run_lsqr(Plan* p, int* iters, int* istop);
+lsrn_status run_cs(Plan* p, int* iters, double* sL, double* sU, bool* diverged);
+lsrn_status run_refine(Plan* p, int nsteps, int* inner);
+lsrn_status finish_x(Plan* p, double* xout);
+int pass_blocks(int64_t rows, int64_t C);
+lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host);
+
+static thread_local char g_last_error[512];
+
+void record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s -> %s", file, line, what,
+           cudaGetErrorString(e));
+  if (getenv("LSRN_VERBOSE")) fprintf(stderr, "lsrn: %s\n", g_last_error);
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+bool is_device_pointer(const void* ptr) {
+  if (ptr == nullptr) return false;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+
+// out (rows x cols, ld_out, FP64) = transpose or copy of a (FP64/FP32) matrix.
+// src element (i, j) of the logical rows_src x cols_src matrix is at
+// src[i*ld_row + j*ld_col].
+__global__ void gather_matrix_kernel(const void* __restrict__ src, int dtype, int64_t ld_row,
+                                     int64_t ld_col, int64_t rows, int64_t cols,
+                                     double* __restrict__ out, int64_t ld_out) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  // read with the stride-1 index fastest (coalesced for either source layout)
+  const bool src_rows_fast = ld_col == 1;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = src_rows_fast ? r0 + k : r0 + threadIdx.x;
+    const int64_t j = src_rows_fast ? c0 + threadIdx.x : c0 + k;
+    double v = 0.0;
+    if (i < rows && j < cols) {
+      const int64_t off = i * ld_row + j * ld_col;
+      v = dtype == LSRN_F32 ? (double)((const float*)src)[off] : ((const double*)src)[off];
+    }
+    if (src_rows_fast) tile[k][threadIdx.x] = v;
+    else tile[threadIdx.x][k] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = r0 + k, j = c0 + threadIdx.x;
+    if (i < rows && j < cols) out[i * ld_out + j] = tile[k][threadIdx.x];
+  }
+}
+
+}  // namespace
+
+lsrn_status gather_matrix(const void* src, int dtype, int64_t ld_row, int64_t ld_col, int64_t rows,
+                          int64_t cols, double* out, int64_t ld_out, cudaStream_t st) {
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  gather_matrix_kernel<<<grid, dim3(32, 8), 0, st>>>(src, dtype, ld_row, ld_col, rows, cols, out,
+                                                      ld_out);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+static lsrn_status dalloc(Plan* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(ptr, bytes, p->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    record_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+    return e == cudaErrorMemoryAllocation ? LSRN_ERR_OOM : LSRN_ERR_CUDA;
+  }
+  p->owned.push_back(*ptr);
+  return LSRN_OK;
+}
+
+template <class T>
+static lsrn_status dalloc_n(Plan* p, T** ptr, int64_t n) {
+  return dalloc(p, (void**)ptr, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+}
+
+static void release(Plan* p) {
+  if (p == nullptr) return;
+  if (p->stream) {
+    for (void* ptr : p->owned) cudaFreeAsync(ptr, p->stream);
+    if (p->coefs) cudaFreeAsync(p->coefs, p->stream);
+    cudaStreamSynchronize(p->stream);
+  }
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+static lsrn_status validate_options(const lsrn_options& o) {
+  if (!(o.gamma > 1.0) || !std::isfinite(o.gamma)) return LSRN_ERR_INVALID_ARG;
+  if (!(o.tol > 0.0) || !(o.tol < 1.0)) return LSRN_ERR_INVALID_ARG;
+  if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda)) return LSRN_ERR_INVALID_ARG;
+  if (o.refine_max < 0 || o.refine_max > 16) return LSRN_ERR_INVALID_ARG;
+  if (!(o.refine_tol > 0.0) || !(o.refine_tol < 1.0)) return LSRN_ERR_INVALID_ARG;
+  if (o.sketch_mode != LSRN_SKETCH_F64 && o.sketch_mode != LSRN_SKETCH_TC_SLICED)
+    return LSRN_ERR_INVALID_ARG;
+  return LSRN_OK;
+}
+
+static lsrn_status plan_workspace(Plan* p) {
+  const int64_t q = p->q, s = p->s;
+  p->nblk = pass_blocks(p->xrows, p->xcols);
+  if (p->nblk <= 0) return LSRN_ERR_UNSUPPORTED;
+  LSRN_TRY(dalloc_n(p, &p->Xs, s * q));
+  LSRN_TRY(dalloc_n(p, &p->Wj, q * q));
+  LSRN_TRY(dalloc_n(p, &p->tau, q));
+  LSRN_TRY(dalloc_n(p, &p->sig, q));
+  LSRN_TRY(dalloc_n(p, &p->perm, q));
+  LSRN_TRY(dalloc_n(p, &p->Nm, q * q));
+  LSRN_TRY(dalloc_n(p, &p->NT, q * q));
+  LSRN_TRY(dalloc_n(p, &p->scal, (int64_t)SC_COUNT));
+  LSRN_TRY(dalloc_n(p, &p->iscal, (int64_t)IC_COUNT));
+  LSRN_TRY(dalloc_n(p, &p->st0, p->nstate));
+  LSRN_TRY(dalloc_n(p, &p->st1, p->nstate));
+  LSRN_TRY(dalloc_n(p, &p->vq, q));
+  LSRN_TRY(dalloc_n(p, &p->vq2, q));
+  LSRN_TRY(dalloc_n(p, &p->tmpq, q));
+  for (auto& v : p->vr) LSRN_TRY(dalloc_n(p, &v, q));
+  LSRN_TRY(dalloc_n(p, &p->xfull, std::max(q, p->nstate)));
+  LSRN_TRY(dalloc_n(p, &p->bdev, std::max<int64_t>(p->m, 1)));
+  LSRN_TRY(dalloc_n(p, &p->pvec, (int64_t)(p->nblk + 1) * p->xcols));
+  LSRN_TRY(dalloc_n(p, &p->pvec2, (int64_t)(p->nblk + 1) * p->xcols));
+  LSRN_TRY(dalloc_n(p, &p->pscal, std::max<int64_t>(p->nblk + 1, 4 * (int64_t)num_sms())));
+  LSRN_CUDA_TRY(cudaMemsetAsync(p->scal, 0, SC_COUNT * sizeof(double), p->stream));
+  LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal, 0, IC_COUNT * sizeof(int), p->stream));
+  const double one = 1.0;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(p->scal + SC_ONE, &one, sizeof(double), cudaMemcpyHostToDevice,
+                                p->stream));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return LSRN_OK;
+}
+
+static lsrn_status dense_setup(Plan* p, const lsrn_matrix* A, bool host) {
+  const int64_t m = A->m, n = A->n;
+  const bool rowmajor = A->format == LSRN_DENSE_ROWMAJOR;
+  if (A->ld < (rowmajor ? n : m)) return LSRN_ERR_INVALID_ARG;
+  // X = A (row-major) for m >= n, X = A^T (row-major, i.e. A column-major) for m < n.
+  const bool layout_ok = (p->tall && rowmajor) || (!p->tall && !rowmajor);
+  const bool aligned = ((uintptr_t)A->values % 16 == 0) && (A->ld % 2 == 0);
+  if (!host && layout_ok && aligned && A->dtype == LSRN_F64) {
+    p->X = (const double*)A->values;
+    p->ldx = A->ld;
+    return LSRN_OK;
+  }
+  const int64_t xr = p->xrows, xc = p->xcols;
+  const int64_t ldx = xc + (xc & 1);
+  double* Xo = nullptr;
+  LSRN_TRY(dalloc_n(p, &Xo, xr * ldx));
+  const void* src = A->values;
+  void* staged = nullptr;
+  const size_t esz = A->dtype == LSRN_F32 ? 4 : 8;
+  const int64_t src_elems = rowmajor ? (m - 1) * A->ld + n : (n - 1) * A->ld + m;
+  if (host) {
+    LSRN_TRY(dalloc(p, &staged, (size_t)src_elems * esz));
+    LSRN_CUDA_TRY(cudaMemcpyAsync(staged, A->values, (size_t)src_elems * esz,
+                                  cudaMemcpyHostToDevice, p->stream));
+    src = staged;
+  }
+  // element (i, j) of A sits at i*ld + j (row-major) or i + j*ld (column-major);
+  // X(i', j') = A(i', j') for m >= n and A(j', i') for m < n.
+  int64_t ld_row, ld_col;
+  if (p->tall) {
+    ld_row = rowmajor ? A->ld : 1;
+    ld_col = rowmajor ? 1 : A->ld;
+  } else {
+    ld_row = rowmajor ? 1 : A->ld;
+    ld_col = rowmajor ? A->ld : 1;
+  }
+  LSRN_TRY(gather_matrix(src, A->dtype, ld_row, ld_col, xr, xc, Xo, ldx, p->stream));
+  if (staged) {
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    cudaFreeAsync(staged, p->stream);
+    p->owned.erase(std::find(p->owned.begin(), p->owned.end(), staged));
+  }
+  p->X = Xo;
+  p->owned_X = Xo;
+  p->ldx = ldx;
+  return LSRN_OK;
+}
+
+}  // namespace lsrn
+
+using namespace lsrn;
+
+struct lsrn_plan_s : Plan {};
+
+extern "C" {
+
+const char* lsrn_status_string(lsrn_status s) {
+  switch (s) {
+    case LSRN_OK: return "LSRN_OK";
+    case LSRN_PENDING: return "LSRN_PENDING";
+    case LSRN_ERR_INVALID_ARG: return "LSRN_ERR_INVALID_ARG";
+    case LSRN_ERR_OOM: return "LSRN_ERR_OOM";
+    case LSRN_ERR_CUDA: return "LSRN_ERR_CUDA";
+    case LSRN_ERR_NOT_CONVERGED: return "LSRN_ERR_NOT_CONVERGED";
+    case LSRN_ERR_DIVERGED: return "LSRN_ERR_DIVERGED";
+    case LSRN_ERR_TIMEOUT: return "LSRN_ERR_TIMEOUT";
+    case LSRN_ERR_QUEUE_FULL: return "LSRN_ERR_QUEUE_FULL";
+    case LSRN_ERR_STATE: return "LSRN_ERR_STATE";
+    case LSRN_ERR_UNSUPPORTED: return "LSRN_ERR_UNSUPPORTED";
+  }
+  return "LSRN_UNKNOWN_STATUS";
+}
+
+const char* lsrn_last_error_message(void) { return g_last_error; }
+
+lsrn_status lsrn_default_options(lsrn_options* opt) {
+  if (opt == nullptr) return LSRN_ERR_INVALID_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->gamma = 2.0;
+  opt->tol = 1e-14;
+  opt->lambda = 0.0;
+  opt->rcond = -1.0;
+  opt->cs_alpha = -1.0;
+  opt->refine_tol = 1e-3;
+  opt->max_iter = -1;
+  opt->refine_max = 1;
+  opt->seed = 0;
+  opt->sketch_mode = LSRN_SKETCH_F64;
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
+                      lsrn_plan_t* out) {
+  if (out == nullptr || A == nullptr) return LSRN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (A->m < 1 || A->n < 1 || A->values == nullptr) return LSRN_ERR_INVALID_ARG;
+  if (A->format != LSRN_DENSE_ROWMAJOR && A->format != LSRN_DENSE_COLMAJOR && A->format != LSRN_CSR)
+    return LSRN_ERR_INVALID_ARG;
+  if (A->dtype != LSRN_F64 && A->dtype != LSRN_F32) return LSRN_ERR_INVALID_ARG;
+  lsrn_options o;
+  if (opt) o = *opt;
+  else lsrn_default_options(&o);
+  LSRN_TRY(validate_options(o));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return LSRN_ERR_CUDA;
+  }
+  lsrn_plan_s* p = new (std::nothrow) lsrn_plan_s();
+  if (p == nullptr) return LSRN_ERR_OOM;
+  cudaGetDevice(&p->device);
+  if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    p->stream = nullptr;
+    release(p);
+    return LSRN_ERR_CUDA;
+  }
+  for (auto& e : p->ev) cudaEventCreate(&e);
+  if (stream) {  // order after the caller's prior work on its stream
+    cudaEventRecord(p->ev[7], (cudaStream_t)stream);
+    cudaStreamWaitEvent(p->stream, p->ev[7], 0);
+  }
+  p->opt = o;
+  p->m = A->m;
+  p->n = A->n;
+  p->tall = A->m >= A->n;
+  p->lam = o.lambda;
+  p->ridge = o.lambda > 0.0;
+  p->csr = A->format == LSRN_CSR;
+  p->xrows = p->tall ? A->m : A->n;
+  p->xcols = p->tall ? A->n : A->m;
+  p->q = p->xcols;
+  p->s = (int64_t)std::ceil(o.gamma * (double)p->q);
+  if (p->s <= p->q) p->s = p->q + 1;
+  if (p->ridge) {
+    p->extra_rows = p->tall ? A->n : A->m;
+    p->extra_coef = p->tall ? o.lambda : 1.0;
+    p->xscale = p->tall ? 1.0 : 1.0 / o.lambda;
+  }
+  p->nstate = p->xrows + p->extra_rows;
+  const bool host = !is_device_pointer(A->values);
+  lsrn_status st;
+  if (p->csr) st = csr_plan_setup(p, A, host);
+  else st = dense_setup(p, A, host);
+  if (st == LSRN_OK) st = plan_workspace(p);
+  if (st == LSRN_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LSRN_ERR_CUDA;
+  if (st != LSRN_OK) {
+    release(p);
+    return st;
+  }
+  *out = p;
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_sketch(lsrn_plan_t p) {
+  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
+  cudaSetDevice(p->device);
+  cudaEventRecord(p->ev[0], p->stream);
+  const uint32_t tag = 0;
+  if (p->csr) {
+    LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, p->xscale, p->s,
+                               p->opt.seed, tag, p->Xs, p->q, p->stream));
+  } else {
+    const size_t scratch = sketch_f64_scratch_bytes(p->xrows, p->q, p->s);
+    double* buf = nullptr;
+    if (scratch) LSRN_CUDA_TRY(cudaMallocAsync((void**)&buf, scratch, p->stream));
+    lsrn_status st = launch_sketch_f64(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
+                                       tag, p->Xs, p->q, buf, scratch, p->stream);
+    if (buf) cudaFreeAsync(buf, p->stream);
+    LSRN_TRY(st);
+  }
+  if (p->ridge)
+    LSRN_TRY(launch_sketch_add_gamma(p->Xs, p->q, p->s, p->q, p->opt.seed, tag, p->xrows,
+                                     p->extra_coef, p->stream));
+  cudaEventRecord(p->ev[1], p->stream);
+  p->state = 1;   // a new sketch invalidates an earlier preconditioner
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
+  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
+  if (p->state < 1) return LSRN_ERR_STATE;
+  cudaSetDevice(p->device);
+  cudaEventRecord(p->ev[2], p->stream);
+  LSRN_TRY(run_precond(p));
+  cudaEventRecord(p->ev[3], p->stream);
+  LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[3]));
+  cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
+  cudaEventElapsedTime(&p->t_precond_ms, p->ev[2], p->ev[3]);
+  p->state = 2;
+  if (rank_out) *rank_out = p->rank;
+  return LSRN_OK;
+}
+
+static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_info* info,
+                                bool use_cs) {
+  if (p == nullptr || b == nullptr || x == nullptr) return LSRN_ERR_INVALID_ARG;
+  cudaSetDevice(p->device);
+  LSRN_CUDA_TRY(cudaMemcpyAsync(p->bdev, b, p->m * sizeof(double), cudaMemcpyDefault, p->stream));
+  if (p->state < 1) LSRN_TRY(lsrn_sketch(p));
+  if (p->state < 2) LSRN_TRY(lsrn_precond(p, nullptr));
+  lsrn_info inf;
+  memset(&inf, 0, sizeof(inf));
+  inf.m = p->m;
+  inf.n = p->n;
+  inf.s = p->s;
+  inf.rank = p->rank;
+  inf.tall = p->tall ? 1 : 0;
+  inf.sigma_max_sketch = p->sigma_max;
+  inf.sigma_min_sketch = p->sigma_min;
+  inf.t_sketch_ms = p->t_sketch_ms;
+  inf.t_precond_ms = p->t_precond_ms;
+  lsrn_status result = LSRN_OK;
+  const bool xdev = is_device_pointer(x);
+  double* xout = xdev ? x : p->xfull;
+  if (p->rank == 0) {
+    LSRN_TRY(finish_x(p, xout));
+  } else {
+    cudaEventRecord(p->ev[4], p->stream);
+    if (use_cs) {
+      bool diverged = false;
+      LSRN_TRY(run_cs(p, &inf.iterations, &inf.sigma_L, &inf.sigma_U, &diverged));
+      if (diverged) result = LSRN_ERR_DIVERGED;
+    } else {
+      LSRN_TRY(run_lsqr(p, &inf.iterations, &inf.istop));
+      if (inf.istop == 0) result = LSRN_ERR_NOT_CONVERGED;
+      double sc[SC_COUNT];
+      LSRN_CUDA_TRY(cudaMemcpyAsync(sc, p->scal, sizeof(sc), cudaMemcpyDeviceToHost, p->stream));
+      LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+      inf.rnorm_est = sc[SC_RNORM];
+      inf.arnorm_est = sc[SC_ARNORM];
+      inf.anorm_est = sc[SC_ANORM];
+    }
+    cudaEventRecord(p->ev[5], p->stream);
+    if (result == LSRN_OK) {
+      LSRN_TRY(run_refine(p, p->opt.refine_max, &inf.refine_iterations));
+      inf.refine_steps = inf.refine_iterations > 0 ? p->opt.refine_max : 0;
+    }
+    cudaEventRecord(p->ev[6], p->stream);
+    LSRN_TRY(finish_x(p, xout));
+    LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[6]));
+    cudaEventElapsedTime(&inf.t_iter_ms, p->ev[4], p->ev[5]);
+    cudaEventElapsedTime(&inf.t_refine_ms, p->ev[5], p->ev[6]);
+  }
+  if (!xdev)
+    LSRN_CUDA_TRY(cudaMemcpyAsync(x, xout, p->n * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  inf.status = result;
+  if (info) *info = inf;
+  return result;
+}
+
+lsrn_status lsrn_solve_lsqr(lsrn_plan_t p, const double* b, double* x, lsrn_info* info) {
+  return solve_common(p, b, x, info, false);
+}
+
+lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* info) {
+  if (p != nullptr && p->state >= 2 && p->rank > 0) {
+    double sL, sU;
+    if (thm45_bounds(p, &sL, &sU) != LSRN_OK) return LSRN_ERR_INVALID_ARG;
+  }
+  return solve_common(p, b, x, info, true);
+}
+
+lsrn_status lsrn_plan_destroy(lsrn_plan_t p) {
+  if (p == nullptr) return LSRN_OK;
+  cudaSetDevice(p->device);
+  release(p);
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_plan_get_sketch(lsrn_plan_t p, double* out, int64_t* rows, int64_t* cols) {
+  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
+  if (p->state < 1) return LSRN_ERR_STATE;
+  if (rows) *rows = p->s;
+  if (cols) *cols = p->q;
+  if (out) {
+    LSRN_CUDA_TRY(cudaMemcpyAsync(out, p->Xs, p->s * p->q * sizeof(double), cudaMemcpyDefault,
+                                  p->stream));
+  }
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_plan_get_precond(lsrn_plan_t p, double* out, double* sigma, int64_t* rank) {
+  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
+  if (p->state < 2) return LSRN_ERR_STATE;
+  if (rank) *rank = p->rank;
+  if (out && p->rank > 0)
+    LSRN_CUDA_TRY(cudaMemcpyAsync(out, p->Nm, p->q * p->rank * sizeof(double), cudaMemcpyDefault,
+                                  p->stream));
+  if (sigma && p->rank > 0)
+    LSRN_CUDA_TRY(cudaMemcpyAsync(sigma, p->sig, p->rank * sizeof(double), cudaMemcpyDefault,
+                                  p->stream));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_generate_sketch_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t j0,
+                                       int64_t rows, int64_t cols, double* g, float* z,
+                                       void* stream) {
+  if (rows < 0 || cols < 0 || i0 < 0 || j0 < 0) return LSRN_ERR_INVALID_ARG;
+  if (i0 + rows > (int64_t)0xFFFFFFFFll) return LSRN_ERR_INVALID_ARG;
+  if (rows * cols == 0) return LSRN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool gdev = g == nullptr || is_device_pointer(g);
+  const bool zdev = z == nullptr || is_device_pointer(z);
+  double* gd = g;
+  float* zd = z;
+  const size_t tot = (size_t)(rows * cols);
+  if (g && !gdev) LSRN_CUDA_TRY(cudaMallocAsync((void**)&gd, tot * sizeof(double), st));
+  if (z && !zdev) LSRN_CUDA_TRY(cudaMallocAsync((void**)&zd, tot * sizeof(float), st));
+  lsrn_status res = launch_gamma_block(seed, tag, i0, j0, rows, cols, gd, zd, st);
+  if (g && !gdev) {
+    cudaMemcpyAsync(g, gd, tot * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(gd, st);
+  }
+  if (z && !zdev) {
+    cudaMemcpyAsync(z, zd, tot * sizeof(float), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(zd, st);
+  }
+  LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+  return res;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Internal declarations shared by the LSRN translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "lsrn.h"
+
+namespace lsrn {
+
+#define LSRN_CUDA_TRY(expr)                              \
+  do {                                                   \
+    cudaError_t lsrn_err__ = (expr);                     \
+    if (lsrn_err__ != cudaSuccess) {                     \
+      record_cuda_error(lsrn_err__, #expr, __FILE__, __LINE__); \
+      return lsrn_err__ == cudaErrorMemoryAllocation ? LSRN_ERR_OOM : LSRN_ERR_CUDA; \
+    }                                                    \
+  } while (0)
+
+#define LSRN_TRY(expr)                 \
+  do {                                 \
+    lsrn_status lsrn_st__ = (expr);    \
+    if (lsrn_st__ != LSRN_OK) return lsrn_st__; \
+  } while (0)
+
+void record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+int num_sms();
+
+// ---- device scalar block (one per plan) -----------------------------------
+enum ScalarSlot : int {
+  SC_BNORM = 0,   // ||b|| (LSQR: beta_1)
+  SC_ALPHA,       // alpha_k
+  SC_BETA,        // beta_k
+  SC_SU,          // tall: 1/beta (scale of stored u); fat: 1/alpha (scale of stored v)
+  SC_CU,          // coefficient handed to the fused pass
+  SC_RHOBAR,
+  SC_PHIBAR,
+  SC_ANORM2,
+  SC_RNORM,
+  SC_ARNORM,
+  SC_ANORM,
+  SC_XNORM,
+  SC_CX,          // phi/rho   (fat vector update)
+  SC_CW,          // theta/rho (fat vector update)
+  SC_SS,          // sum of squares from the last pass
+  SC_SS0,         // initial sum of squares (CS divergence test)
+  SC_ONE,         // constant 1
+  SC_ZERO,        // constant 0
+  SC_TMP0,
+  SC_TMP1,
+  SC_ALPHA_NEW,
+  SC_SV_NEW,
+  SC_COUNT = 32
+};
+
+enum IntSlot : int { IC_DONE = 0, IC_ITN, IC_ISTOP, IC_CAP, IC_ROT, IC_COUNT = 8 };
+
+// Row modes of the fused pass over the rows of X (see k_iter.cu).
+enum RowMode : int {
+  RM_ACC_STATE = 0,  // t = st0[i]                                  (no dot)
+  RM_LSQR_TALL = 1,  // t = d - c0*st0[i]; st0[i] = t; ss += t^2
+  RM_CS_TALL = 2,    // t = st0[i] - c0*d; st0[i] = t; ss += t^2
+  RM_APPLY = 3,      // t = d
+  RM_FAT_INIT = 4,   // t = sx*d; st0[i] = t; ss += t^2;             acc with sx*t
+  RM_FAT_LSQR = 5,   // t = sx*d - c0*st0[i]; st0[i] = t; ss += t^2; acc with sx*t
+  RM_FAT_CS = 6,     // t = c0*st0[i] + sx*d; st0[i] = t; st1[i] += c1*t; acc with sx*t
+};
+
+struct RowArgs {
+  int mode;
+  double* st0;
+  double* st1;
+  const double* coef;   // device pointer to c0, c1 (read at kernel start)
+  double sx;            // constant scale of every X row
+};
+
+// ---- the plan -----------------------------------------------------------
+struct Plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  lsrn_options opt{};
+  int64_t m = 0, n = 0;
+  bool tall = true;
+  bool ridge = false;
+  double lam = 0.0;
+  bool csr = false;
+
+  // X: the matrix the fused passes stream, row-major: A (m >= n) or A^T (m < n)
+  const double* X = nullptr;
+  int64_t ldx = 0;
+  int64_t xrows = 0, xcols = 0;     // rows, columns of X
+  double xscale = 1.0;              // 1/lambda for the fat ridge operator [A/lambda, I]
+  int64_t extra_rows = 0;           // ridge rows appended to X (coef extra_coef * e_j)
+  double extra_coef = 0.0;
+  int64_t nstate = 0;               // xrows + extra_rows
+  double* owned_X = nullptr;        // plan-owned copy of X, if any
+
+  // CSR (m >= n: A; m < n: A^T) in both orientations for deterministic passes
+  const int64_t* rp = nullptr;  const int32_t* ci = nullptr;  const double* cv = nullptr;   // rows of X
+  const int64_t* rpT = nullptr; const int32_t* ciT = nullptr; const double* cvT = nullptr;  // columns of X
+  int64_t nnz = 0;
+  std::vector<void*> owned;         // device buffers freed at destroy
+
+  // sketch and preconditioner
+  int64_t s = 0;                    // sketch size
+  int64_t q = 0;                    // xcols: n (tall) or m (fat)
+  double* Xs = nullptr;             // s x q sketch (A~ or A~^T), row-major; QR in place
+  double* Wj = nullptr;             // q x q Jacobi workspace (rows = columns of R^T)
+  double* tau = nullptr;
+  double* sig = nullptr;            // q singular values, sorted descending
+  int* perm = nullptr;
+  double* Nm = nullptr;             // q x r row-major (N or M)
+  double* NT = nullptr;             // r x q row-major
+  int64_t rank = 0;
+  double sigma_max = 0.0, sigma_min = 0.0;
+  int sweeps = 0;
+  int state = 0;                    // 0 planned, 1 sketched, 2 preconditioned
+
+  // iteration workspace
+  double* scal = nullptr;           // SC_COUNT doubles
+  int* iscal = nullptr;             // IC_COUNT ints
+  double* coefs = nullptr;          // CS coefficient table (2 per step), capacity ncoef
+  int64_t ncoef = 0;
+  double* st0 = nullptr;            // nstate
+  double* st1 = nullptr;            // nstate
+  double* vq = nullptr;             // q (g / q vectors, reduced)
+  double* vq2 = nullptr;            // q
+  double* tmpq = nullptr;           // q
+  double* vr[6] = {nullptr};        // r-length vectors
+  double* xfull = nullptr;          // nstate (fat) or q (tall x)
+  double* bdev = nullptr;           // m (+ ridge) right-hand side staging
+  double* pvec = nullptr;           // (nblk + 1) * xcols pass partials
+  double* pvec2 = nullptr;          // second partial buffer (double-double low parts)
+  double* pscal = nullptr;          // (nblk + 1) scalar partials
+  int nblk = 0;                     // CTAs of the fused pass
+  cudaEvent_t ev[8] = {nullptr};
+  float t_sketch_ms = 0, t_precond_ms = 0;
+};
+
+// ---- kernels (launchers) -------------------------------------------------
+// sketch: C (S x Q, ldc) = xscale * Gamma[lrow0 : lrow0+L]^T X   (X: L x Q row-major)
+lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
+                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
+                              double* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t sketch_f64_scratch_bytes(int64_t L, int64_t Q, int64_t S);
+// C[i, j] = scale_c * C[i, j] + coef * Gamma[lrow0 + j, i], i < S, j < Q
+lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
+                                    uint32_t tag, int64_t lrow0, double coef, cudaStream_t st);
+lsrn_status launch_gamma_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t j0, int64_t rows,
+                               int64_t cols, double* g, float* z, cudaStream_t st);
+// CSR sketch: C (S x Q) = xscale * Gamma^T X with X given by its columns (CSC of X)
+lsrn_status launch_sketch_csr(const int64_t* colptr, const int32_t* rowidx, const double* vals,
+                              int64_t L, int64_t Q, double xscale, int64_t S, uint64_t seed,
+                              uint32_t tag, double* C, int64_t ldc, cudaStream_t st);
+
+// Theorem 4.5 bounds (sigma_L, sigma_U) for the plan's r and s and alpha option
+lsrn_status thm45_bounds(const Plan* p, double* sL, double* sU);
+bool is_device_pointer(const void* ptr);
+
+// SVD / preconditioner: Xs (S x Q) -> N (Q x r), NT, sig; returns rank
+lsrn_status run_precond(Plan* p);
+
+// fused passes
+lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
+                            double* pscal, const int* done);
+lsrn_status launch_extra_rows(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
+                              double* pscal, const int* done);
+lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
+                           double* pvec_hi, double* pvec_lo, const int* done);
+lsrn_status launch_reduce(const double* pvec, int nslots, int64_t C, double* out,
+                          const double* pscal, double* scal_out, const int* done, cudaStream_t st);
+lsrn_status launch_reduce_dd(const double* phi, const double* plo, int nslots, int64_t C,
+                             double* out_hi, double* out_lo, cudaStream_t st);
+// out[i] = c[0]*dot(M_i, v) + c[1]*y[i]; if y2: y2[i] += c[2]*out[i]    (c: device pointer)
+lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, double* out,
+                        const double* y, double* y2, const double* c, const int* done,
+                        cudaStream_t st);
+// CSR pass: t = Xrow . vin per row, epilogue as RowArgs; then the transpose product
+lsrn_status launch_csr_rowdot(const Plan* p, const double* vin, const RowArgs& a, double* tout,
+                              double* pscal, const int* done);
+lsrn_status launch_csr_coldot(const Plan* p, const double* t, double* out, const int* done);
+
+}  // namespace lsrn
