@@ -23,20 +23,23 @@ struct Coef {
   double c0, c1;
 };
 
+// Row coefficient t_i from the dot d = X_i . vin and the row's state values
+// (s0, s1 read before any thread of the row group writes them).  Returns the
+// multiplier of X_i in the accumulated vector; the writer thread stores the
+// updated state.
 __device__ __forceinline__ double row_coef(const RowArgs& a, const Coef& k, int64_t i, double d,
-                                           bool writer, double& ss) {
+                                           double s0, double s1, bool writer, double& ss) {
   double t = 0.0;
   switch (a.mode) {
     case RM_ACC_STATE:
-      t = a.st0[i];
-      return t;
+      return s0;
     case RM_LSQR_TALL:
-      t = d - k.c0 * a.st0[i];
+      t = d - k.c0 * s0;
       if (writer) a.st0[i] = t;
       ss = fma(t, t, ss);
       return t;
     case RM_CS_TALL:
-      t = a.st0[i] - k.c0 * d;
+      t = s0 - k.c0 * d;
       if (writer) a.st0[i] = t;
       ss = fma(t, t, ss);
       return t;
@@ -48,19 +51,24 @@ __device__ __forceinline__ double row_coef(const RowArgs& a, const Coef& k, int6
       ss = fma(t, t, ss);
       return a.sx * t;
     case RM_FAT_LSQR:
-      t = a.sx * d - k.c0 * a.st0[i];
+      t = a.sx * d - k.c0 * s0;
       if (writer) a.st0[i] = t;
       ss = fma(t, t, ss);
       return a.sx * t;
     case RM_FAT_CS:
-      t = k.c0 * a.st0[i] + a.sx * d;
+      t = k.c0 * s0 + a.sx * d;
       if (writer) {
         a.st0[i] = t;
-        a.st1[i] = fma(k.c1, t, a.st1[i]);
+        a.st1[i] = fma(k.c1, t, s1);
       }
       return a.sx * t;
   }
   return 0.0;
+}
+
+__device__ __forceinline__ bool mode_reads_st0(int mode) {
+  return mode == RM_ACC_STATE || mode == RM_LSQR_TALL || mode == RM_CS_TALL ||
+         mode == RM_FAT_LSQR || mode == RM_FAT_CS;
 }
 
 // TPR threads cover one row (2 * TPR * SLOTS columns max); R rows per step per group.
@@ -79,6 +87,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
   __shared__ double sred[kThreads / 32];
   const int tid = threadIdx.x, gid = tid / TPR, gl = tid % TPR;
   const bool need_dot = args.mode != RM_ACC_STATE;
+  const bool reads0 = mode_reads_st0(args.mode);
+  const bool reads1 = args.mode == RM_FAT_CS;
   Coef k{0.0, 0.0};
   if (args.coef) {
     k.c0 = args.coef[0];
@@ -115,6 +125,15 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
         }
       }
     }
+    // row state, read by every thread of the group before the barrier below;
+    // the group's writer updates it only after that barrier
+    double s0v[R], s1v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = base + gid * R + r;
+      s0v[r] = (i < rows && reads0) ? args.st0[i] : 0.0;
+      s1v[r] = (i < rows && reads1) ? args.st1[i] : 0.0;
+    }
     double d[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -129,6 +148,7 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
       if (TPR <= 32) {
 #pragma unroll
         for (int r = 0; r < R; ++r) d[r] = group_sum<(TPR < 32 ? TPR : 32)>(d[r]);
+        __syncwarp();
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) d[r] = group_sum<32>(d[r]);
@@ -153,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
       double tacc = 0.0;
       if (i < rows) {
         double ss_dummy = 0.0;
-        tacc = row_coef(args, k, i, d[r], gl == 0, gl == 0 ? ss : ss_dummy);
+        tacc = row_coef(args, k, i, d[r], s0v[r], s1v[r], gl == 0, gl == 0 ? ss : ss_dummy);
       }
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
@@ -217,7 +237,10 @@ __global__ void extra_rows_kernel(int64_t nextra, int64_t xrows, int C, double c
     double v = 0.0;
     if (j < nextra) {
       const double d = need_dot ? coef * vin[j] : 0.0;
-      const double t = row_coef(a1, k, xrows + j, d, true, ss);
+      const int64_t i = xrows + j;
+      const double s0 = mode_reads_st0(a1.mode) ? a1.st0[i] : 0.0;
+      const double s1 = a1.mode == RM_FAT_CS ? a1.st1[i] : 0.0;
+      const double t = row_coef(a1, k, i, d, s0, s1, true, ss);
       v = coef * t;
     }
     pvec_slot[j] = v;
@@ -413,7 +436,29 @@ __global__ void __launch_bounds__(256) gemv_kernel(const double* __restrict__ M,
   }
 }
 
+// Warp per row, double-double accumulation: out[i] = round(M_i . v).
+__global__ void __launch_bounds__(256) gemv_dd_kernel(const double* __restrict__ M, int64_t R,
+                                                      int64_t C, const double* __restrict__ v,
+                                                      double* __restrict__ out) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= R) return;
+  const double* m = M + row * C;
+  double hi = 0.0, lo = 0.0;
+  for (int64_t j = lane; j < C; j += 32) dd_add_prod(hi, lo, m[j], v[j]);
+  group_sum_dd<32>(hi, lo);
+  if (lane == 0) out[row] = hi + lo;
+}
+
 }  // namespace
+
+lsrn_status launch_gemv_dd(const double* M, int64_t R, int64_t C, const double* v, double* out,
+                           cudaStream_t st) {
+  if (R == 0) return LSRN_OK;
+  gemv_dd_kernel<<<(unsigned)((R * 32 + 255) / 256), 256, 0, st>>>(M, R, C, v, out);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
 
 static int pick_layout(int64_t C, int* tpr, int* slots) {
   if (C <= 64) { *tpr = 32; *slots = 1; }

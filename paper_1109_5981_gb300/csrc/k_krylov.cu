@@ -597,7 +597,7 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
       double* z = p->vr[4];
       double* v = p->vr[0];
       double* x = p->xfull;
-      LSRN_TRY(launch_gemv(p->Nm, q, r, y, x, nullptr, nullptr, c100(p), nullptr, p->stream));
+      LSRN_TRY(launch_gemv_dd(p->Nm, q, r, y, x, p->stream));
       LSRN_TRY(launch_dd_pass(p, x, p->bdev, p->st1, p->pvec, p->pvec2, nullptr));
       LSRN_TRY(launch_reduce_dd(p->pvec, p->pvec2, nslots, q, p->vq, p->vq2, p->stream));
       // g = hi + lo
@@ -642,7 +642,7 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
 lsrn_status finish_x(Plan* p, double* xout) {
   const int64_t r = p->rank, q = p->q;
   if (r == 0) return fill(p, xout, p->n, 0.0);
-  if (p->tall) return launch_gemv(p->Nm, q, r, p->vr[2], xout, nullptr, nullptr, c100(p), nullptr, p->stream);
+  if (p->tall) return launch_gemv_dd(p->Nm, q, r, p->vr[2], xout, p->stream);
   const double sc = p->ridge ? 1.0 / p->lam : 1.0;
   scale_copy_kernel<<<grid_for(p->n), 256, 0, p->stream>>>(p->st1, p->n, sc, xout);
   LSRN_CUDA_TRY(cudaGetLastError());

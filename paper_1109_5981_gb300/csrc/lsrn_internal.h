@@ -177,6 +177,9 @@ lsrn_status launch_reduce_dd(const double* phi, const double* plo, int nslots, i
 lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, double* out,
                         const double* y, double* y2, const double* c, const int* done,
                         cudaStream_t st);
+// out[i] = M_i . v accumulated in double-double (warp per row)
+lsrn_status launch_gemv_dd(const double* M, int64_t R, int64_t C, const double* v, double* out,
+                           cudaStream_t st);
 // CSR pass: t = Xrow . vin per row, epilogue as RowArgs; then the transpose product
 lsrn_status launch_csr_rowdot(const Plan* p, const double* vin, const RowArgs& a, double* tout,
                               double* pscal, const int* done);
