@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""LSRN benchmark: least-squares solves per second on one GB300.
+
+Workload (N = 1): the dense tall problem A (10^6 x 2000, rank 1800, singular
+values log-spaced 1 -> 1e-6, random orthogonal factors from 8 seeded
+Householder reflectors), b = A x0 + 1e-4 N(0,1), gamma = 2 (s = 4000), LSQR to
+tol 1e-14 plus one refinement step.  One step = one complete solve through the
+C ABI: lsrn_plan + lsrn_sketch + lsrn_precond + lsrn_solve_lsqr (+ destroy),
+i.e. Algorithm 1 steps 1-7, on inputs already resident in HBM.  A (16 GB) is
+larger than L2, so no L2 flush is needed between steps.
+
+Each step's x is checked against the planted-factor closed form
+x* = V Sigma^-1 U^T b computed by the oracle on the host; the line reports the
+worst relative error seen.
+
+Under torchrun (N > 1) every rank solves its own independently seeded problem
+(no collective on the data path; weak scaling) and value = all solves / max
+rank time.
+
+--impl reference times the oracle (plain FP64 CPU LSRN) on bounded samples of
+the same workload on this host's cores and extrapolates to one solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LS solves/s at <=1e-10 rel err (dense 1e6x2000 rank 1800, FP64, LSQR + refinement)"
+UNIT = "solves/s"
+M, N, RANK = 1_000_000, 2000, 1800
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solver", default="lsqr", choices=["lsqr", "cs"])
+    ap.add_argument("--sketch", default="f64", choices=["f64", "tc"])
+    ap.add_argument("--m", type=int, default=M)
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--rank", type=int, default=RANK)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- #
+# clocks during the timed region                                               #
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "power_w_max": float(max(power)) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- #
+# CPU baseline: the oracle on bounded samples                                  #
+# --------------------------------------------------------------------------- #
+def oracle_sampled_solve_seconds(A_host: np.ndarray, b_host: np.ndarray, iters: int,
+                                 refine_passes: int, seed: int = 0) -> dict:
+    """Time the oracle's LSRN stages on samples of the workload and extrapolate
+    to one full solve with the paper's cost model (section 4.3, eq. lsrn_flops):
+    sketch ~ s*m*randn + 2smn (linear in the rows sampled), SVD ~ n^3, each
+    iteration = one application of A and one of A^T."""
+    import oracle as O
+    m, n = A_host.shape
+    s = math.ceil(2.0 * n)
+    out = {}
+    # sketch: G (s x m_s) drawn by the oracle, times A[:m_s]
+    m_s = min(m, 8000)
+    t = time.perf_counter()
+    G = O.sketch_block(seed, 0, 0, m_s, s).T
+    At_part = G @ A_host[:m_s]
+    out["sketch_s"] = (time.perf_counter() - t) * (m / m_s)
+    del G, At_part
+    # SVD of a (2 n_s) x n_s sketch by the oracle's one-sided Jacobi, scaled by n^3
+    n_s = min(n, 160)
+    rng = np.random.Generator(np.random.PCG64(1))
+    X = rng.standard_normal((2 * n_s, n_s)) @ np.diag(np.logspace(0, -6, n_s))
+    t = time.perf_counter()
+    O.jacobi_svd(X)
+    out["svd_s"] = (time.perf_counter() - t) * (n / n_s) ** 3
+    # one oracle LSQR-style application of A and A^T on the full matrix
+    v = rng.standard_normal(n)
+    t = time.perf_counter()
+    u = A_host @ v
+    w = A_host.T @ u
+    per_pass = time.perf_counter() - t
+    out["iter_s"] = per_pass * (iters + refine_passes)
+    out["total_s"] = out["sketch_s"] + out["svd_s"] + out["iter_s"]
+    out["sample"] = (f"sketch on {m_s} of {m} rows (x{m / m_s:.0f}), Jacobi SVD at "
+                     f"{2 * n_s}x{n_s} (x(n/{n_s})^3), one A and A^T product on the full "
+                     f"matrix (x{iters + refine_passes} passes)")
+    del u, w
+    return out
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import workloads as W
+    t0 = time.perf_counter()
+    P = W.c2_problem(seed=0, m=args.m, n=args.n, rank=args.rank)
+    gen_s = time.perf_counter() - t0
+    iters = 83
+    steps = []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sampled_solve_seconds(P.A, P.b, iters, 24)
+        if k >= args.warmup:
+            steps.append(r)
+    tot = float(np.mean([r["total_s"] for r in steps]))
+    value = 1.0 / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, cond 1e6, "
+                               "noise 1e-4, gamma 2, LSQR tol 1e-14",
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": steps[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "stages_s": {k: steps[-1][k] for k in ("sketch_s", "svd_s", "iter_s")},
+        "generator_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# our implementation                                                           #
+# --------------------------------------------------------------------------- #
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import oracle as O
+    import paper_1109_5981_gb300 as L
+    import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl")
+        dist = dist_
+    L.load_library()
+    dev = f"cuda:{local}"
+
+    P = W.c2_problem(seed=rank, device=dev, m=args.m, n=args.n, rank=args.rank)
+    A, b = P.A, P.b
+    x = torch.empty(args.n, dtype=torch.float64, device=dev)
+    xstar = O.minlen_from_factors(P.apply_Ut, P.sigma, P.apply_V, b.cpu().numpy())
+    opts = L.default_options(seed=1234 + rank,
+                             sketch_mode=L.LSRN_SKETCH_TC_SLICED if args.sketch == "tc"
+                             else L.LSRN_SKETCH_F64)
+    solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
+
+    def step():
+        plan = L.lsrn_plan(A, opts)
+        try:
+            _, info = solve_fn(plan, b, x)
+        finally:
+            plan.close()
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = L.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    infos, errs = [], []
+    for _ in range(args.steps):
+        infos.append(step())
+        errs.append(O.rel_err(x.cpu().numpy(), xstar))
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = L.kernel_launches() - launches0
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * args.steps / (elapsed_ms / 1e3)
+    info = infos[-1]
+    s = info["s"]
+    t_sketch = float(np.mean([i["t_sketch_ms"] for i in infos]))
+    sketch_flops = 2.0 * s * args.m * args.n
+    fp64_peak = L.probe_fp64_fma()
+    achieved = sketch_flops / (t_sketch * 1e-3) / 1e12
+    roofline = {"kernel": "sketch_f64_kernel" if args.sketch == "f64" else "sketch_tc_kernel",
+                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA throughput measured in this run (lsrn_probe_fp64_fma)",
+                "work_per_launch": f"2*s*m*n = {sketch_flops:.3e} flop"}
+
+    # end to end through the C ABI with host buffers (pinned A, b in; x out)
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True)
+        A_h.copy_(A)
+        b_h = b.cpu().numpy().copy()
+        x_h = np.empty(args.n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan = L.lsrn_plan(A_h, opts)
+            solve_fn(plan, b_h, x_h)
+            plan.close()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        errs.append(O.rel_err(x_h, xstar))
+        e2e = {"value": world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(args.m * args.n * 8 + args.m * 8),
+               "d2h_bytes_per_step": int(args.n * 8)}
+        del A_h
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        A_np = A.cpu().numpy()
+        r = oracle_sampled_solve_seconds(A_np, b.cpu().numpy(), info["iterations"],
+                                         info["refine_iterations"] + 1)
+        cpu = {"value": 1.0 / r["total_s"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": r["sample"], "stages_s": {k: r[k] for k in ("sketch_s", "svd_s", "iter_s")}}
+        del A_np
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator, no dataset)",
+            "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, cond 1e6, "
+                                   f"noise 1e-4, gamma 2, {args.solver.upper()} tol 1e-14 + 1 "
+                                   f"refinement, sketch {args.sketch}",
+                       "l2": "inputs larger than L2 (A is 16 GB)",
+                       "parallelism": "independent problem per GPU"},
+            "accuracy": {"max_rel_err_vs_planted_xstar": max(errs), "target": 1e-10,
+                         "ok": bool(max(errs) <= 1e-10)},
+            "phases_ms": {"sketch": t_sketch,
+                          "precond": float(np.mean([i["t_precond_ms"] for i in infos])),
+                          "iter": float(np.mean([i["t_iter_ms"] for i in infos])),
+                          "refine": float(np.mean([i["t_refine_ms"] for i in infos]))},
+            "iterations": info["iterations"], "refine_iterations": info["refine_iterations"],
+            "rank": info["rank"], "s": s,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

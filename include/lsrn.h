@@ -124,6 +124,17 @@ const char* lsrn_status_string(lsrn_status s);
  * (file, line, call, CUDA message); empty if none.  Static thread-local storage. */
 const char* lsrn_last_error_message(void);
 
+/* Number of CUDA kernels the library has launched in this process (a
+ * diagnostic for profiling and benchmarking; kernels inside CUDA graphs are
+ * counted when the graph is launched). */
+uint64_t lsrn_kernel_launches(void);
+
+/* Measurement aid with no counterpart in the paper: FP64 fused multiply-add
+ * throughput of the current device in TFLOP/s (best of three launches of a
+ * register-resident FMA loop, ~0.1 s), the peak against which FP64-arithmetic
+ * bound kernels are compared.  Synchronises the device. */
+lsrn_status lsrn_probe_fp64_fma(double* tflops);
+
 /* Fill *opt with the defaults listed in lsrn_options.  INVALID_ARG if opt is NULL. */
 lsrn_status lsrn_default_options(lsrn_options* opt);
 

@@ -83,6 +83,8 @@ _lib = None
 _SIGS = {
     "lsrn_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "lsrn_last_error_message": ([], ctypes.c_char_p),
+    "lsrn_kernel_launches": ([], ctypes.c_uint64),
+    "lsrn_probe_fp64_fma": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lsrn_default_options": ([ctypes.POINTER(lsrn_options)], ctypes.c_int),
     "lsrn_plan": ([ctypes.POINTER(lsrn_matrix), ctypes.POINTER(lsrn_options), ctypes.c_void_p,
                    ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -131,6 +133,18 @@ def load_library():
         fn.restype = res
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load_library().lsrn_kernel_launches())
+
+
+def probe_fp64_fma() -> float:
+    """FP64 FMA throughput of the current device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(load_library().lsrn_probe_fp64_fma(ctypes.byref(v)), "lsrn_probe_fp64_fma")
+    return v.value
 
 
 def status_string(status: int) -> str:

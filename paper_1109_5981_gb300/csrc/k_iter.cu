@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(256) gemv_dd_kernel(const double* __restrict__
 lsrn_status launch_gemv_dd(const double* M, int64_t R, int64_t C, const double* v, double* out,
                            cudaStream_t st) {
   if (R == 0) return LSRN_OK;
-  gemv_dd_kernel<<<(unsigned)((R * 32 + 255) / 256), 256, 0, st>>>(M, R, C, v, out);
+  launch(gemv_dd_kernel, (unsigned)((R * 32 + 255) / 256), 256, 0, st, M, R, C, v, out);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }
@@ -488,7 +488,7 @@ lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, 
   const int C = (int)p->xcols;
   dim3 grid(p->nblk);
 #define LSRN_ROWPASS(T, S, R)                                                                   \
-  row_pass_kernel<T, S, R><<<grid, kThreads, 0, p->stream>>>(p->X, p->xrows, C, p->ldx, vin, a, \
+  launch(row_pass_kernel<T, S, R>, grid, kThreads, 0, p->stream, p->X, p->xrows, C, p->ldx, vin, a, \
                                                              pvec, pscal, done)
   if (tpr == 32 && slots == 1) LSRN_ROWPASS(32, 1, 4);
   else if (tpr == 32) LSRN_ROWPASS(32, 2, 4);
@@ -505,7 +505,7 @@ lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, 
 lsrn_status launch_extra_rows(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
                               double* pscal, const int* done) {
   if (p->extra_rows == 0) return LSRN_OK;
-  extra_rows_kernel<<<1, 1024, 0, p->stream>>>(p->extra_rows, p->xrows, (int)p->xcols,
+  launch(extra_rows_kernel, 1, 1024, 0, p->stream, p->extra_rows, p->xrows, (int)p->xcols,
                                                p->extra_coef, vin, a, pvec + (int64_t)p->nblk * p->xcols,
                                                pscal + p->nblk, done);
   LSRN_CUDA_TRY(cudaGetLastError());
@@ -520,7 +520,7 @@ lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec,
   const int C = (int)p->xcols;
   dim3 grid(p->nblk);
 #define LSRN_DDPASS(T, S)                                                                       \
-  dd_pass_kernel<T, S><<<grid, kThreads, 0, p->stream>>>(p->X, p->xrows, C, p->ldx, vin, bvec,   \
+  launch(dd_pass_kernel<T, S>, grid, kThreads, 0, p->stream, p->X, p->xrows, C, p->ldx, vin, bvec,   \
                                                          rout, p->xscale, pvec_hi, pvec_lo)
   if (tpr == 32 && slots == 1) LSRN_DDPASS(32, 1);
   else if (tpr == 32) LSRN_DDPASS(32, 2);
@@ -531,7 +531,7 @@ lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec,
   else LSRN_DDPASS(256, 8);
 #undef LSRN_DDPASS
   if (p->extra_rows > 0) {
-    dd_extra_kernel<<<(unsigned)((p->xcols + 255) / 256), 256, 0, p->stream>>>(
+    launch(dd_extra_kernel, (unsigned)((p->xcols + 255) / 256), 256, 0, p->stream, 
         p->extra_rows, p->xrows, C, p->extra_coef, vin, bvec != nullptr, rout,
         pvec_hi + (int64_t)p->nblk * C, pvec_lo + (int64_t)p->nblk * C);
   }
@@ -541,7 +541,7 @@ lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec,
 
 lsrn_status launch_reduce(const double* pvec, int nslots, int64_t C, double* out,
                           const double* pscal, double* scal_out, const int* done, cudaStream_t st) {
-  reduce_kernel<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(pvec, nslots, C, out, pscal, scal_out,
+  launch(reduce_kernel, (unsigned)((C + 255) / 256), 256, 0, st, pvec, nslots, C, out, pscal, scal_out,
                                                              done);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
@@ -549,7 +549,7 @@ lsrn_status launch_reduce(const double* pvec, int nslots, int64_t C, double* out
 
 lsrn_status launch_reduce_dd(const double* phi, const double* plo, int nslots, int64_t C,
                              double* out_hi, double* out_lo, cudaStream_t st) {
-  reduce_dd_kernel<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(phi, plo, nslots, C, out_hi,
+  launch(reduce_dd_kernel, (unsigned)((C + 255) / 256), 256, 0, st, phi, plo, nslots, C, out_hi,
                                                                 out_lo);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
@@ -559,7 +559,7 @@ lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, 
                         const double* y, double* y2, const double* c, const int* done,
                         cudaStream_t st) {
   if (R == 0) return LSRN_OK;
-  gemv_kernel<<<(unsigned)((R * 32 + 255) / 256), 256, 0, st>>>(M, R, C, v, out, y, y2, c, done);
+  launch(gemv_kernel, (unsigned)((R * 32 + 255) / 256), 256, 0, st, M, R, C, v, out, y, y2, c, done);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }

@@ -348,15 +348,15 @@ inline unsigned grid_for(int64_t n) {
 // ---- helpers used by the host drivers --------------------------------------
 static lsrn_status sumsq(Plan* p, const double* v, int64_t n, double* out) {
   const int parts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 2 * num_sms());
-  sumsq_kernel<<<parts, 256, 0, p->stream>>>(v, n, p->pscal);
-  sum_parts_kernel<<<1, 32, 0, p->stream>>>(p->pscal, parts, out);
+  launch(sumsq_kernel, parts, 256, 0, p->stream, v, n, p->pscal);
+  launch(sum_parts_kernel, 1, 32, 0, p->stream, p->pscal, parts, out);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }
 
 static lsrn_status fill(Plan* p, double* v, int64_t n, double val) {
   if (n <= 0) return LSRN_OK;
-  fill_kernel<<<grid_for(n), 256, 0, p->stream>>>(v, n, val);
+  launch(fill_kernel, grid_for(n), 256, 0, p->stream, v, n, val);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }
@@ -474,14 +474,14 @@ lsrn_status run_lsqr(Plan* p, int* iters, int* istop) {
     LSRN_TRY(launch_extra_rows(p, nullptr, a0, p->pvec, p->pscal, nullptr));
     LSRN_TRY(launch_reduce(p->pvec, p->nblk + (p->extra_rows ? 1 : 0), q, p->vq, p->pscal, nullptr, nullptr, p->stream));
     LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, tmpr, nullptr, nullptr, c100(p), nullptr, p->stream));
-    lsqr_tall_init_kernel<<<1, kCtl, 0, p->stream>>>(p->scal, p->iscal, tmpr, v, w, y, r);
+    launch(lsqr_tall_init_kernel, 1, kCtl, 0, p->stream, p->scal, p->iscal, tmpr, v, w, y, r);
     LSRN_CUDA_TRY(cudaGetLastError());
     RowArgs a{RM_LSQR_TALL, p->st0, nullptr, p->scal + SC_CU, 1.0};
     LSRN_TRY(iterate(p, cap, [&]() -> lsrn_status {
       LSRN_TRY(launch_gemv(p->Nm, q, r, v, p->tmpq, nullptr, nullptr, c100(p), done, p->stream));
       LSRN_TRY(fused_pass(p, p->tmpq, a, p->vq, done));
       LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, tmpr, nullptr, nullptr, c100(p), done, p->stream));
-      lsqr_tall_update_kernel<<<1, kCtl, 0, p->stream>>>(p->scal, p->iscal, tmpr, v, w, y, r, tol, tol);
+      launch(lsqr_tall_update_kernel, 1, kCtl, 0, p->stream, p->scal, p->iscal, tmpr, v, w, y, r, tol, tol);
       LSRN_CUDA_TRY(cudaGetLastError());
       return LSRN_OK;
     }));
@@ -492,28 +492,28 @@ lsrn_status run_lsqr(Plan* p, int* iters, int* istop) {
     double* wv = p->xfull;
     const int64_t ns = p->nstate;
     LSRN_TRY(launch_gemv(p->NT, r, q, p->bdev, tmpr, nullptr, nullptr, c100(p), nullptr, p->stream));
-    lsqr_fat_init_u_kernel<<<1, kCtl, 0, p->stream>>>(p->scal, p->iscal, tmpr, u, r);
+    launch(lsqr_fat_init_u_kernel, 1, kCtl, 0, p->stream, p->scal, p->iscal, tmpr, u, r);
     LSRN_TRY(launch_gemv(p->Nm, q, r, u, p->vq2, nullptr, nullptr, c100(p), nullptr, p->stream));
     RowArgs a0{RM_FAT_INIT, vhat, nullptr, nullptr, p->xscale};
     LSRN_TRY(fused_pass(p, p->vq2, a0, p->vq, nullptr));
-    lsqr_fat_init_alpha_kernel<<<1, 32, 0, p->stream>>>(p->scal, p->iscal);
+    launch(lsqr_fat_init_alpha_kernel, 1, 32, 0, p->stream, p->scal, p->iscal);
     LSRN_TRY(fill(p, x, ns, 0.0));
     // w = vhat * sv
     double sv_host = 0.0;
     LSRN_CUDA_TRY(cudaMemcpyAsync(&sv_host, p->scal + SC_SU, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    scale_copy_kernel<<<grid_for(ns), 256, 0, p->stream>>>(vhat, ns, sv_host, wv);
+    launch(scale_copy_kernel, grid_for(ns), 256, 0, p->stream, vhat, ns, sv_host, wv);
     LSRN_CUDA_TRY(cudaGetLastError());
     const int nparts = (int)grid_for(ns);
     RowArgs a{RM_FAT_LSQR, vhat, nullptr, p->scal + SC_CU, p->xscale};
     LSRN_TRY(iterate(p, cap, [&]() -> lsrn_status {
       LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, tmpr, nullptr, nullptr, c100(p), done, p->stream));
-      lsqr_fat_u_kernel<<<1, kCtl, 0, p->stream>>>(p->scal, p->iscal, tmpr, u, r);
+      launch(lsqr_fat_u_kernel, 1, kCtl, 0, p->stream, p->scal, p->iscal, tmpr, u, r);
       LSRN_TRY(launch_gemv(p->Nm, q, r, u, p->vq2, nullptr, nullptr, c100(p), done, p->stream));
       LSRN_TRY(fused_pass(p, p->vq2, a, p->vq, done));
-      lsqr_fat_scalar_kernel<<<1, 32, 0, p->stream>>>(p->scal, p->iscal);
-      lsqr_fat_vec_kernel<<<nparts, 256, 0, p->stream>>>(p->scal, p->iscal, x, wv, vhat, ns, p->pscal);
-      lsqr_fat_test_kernel<<<1, 32, 0, p->stream>>>(p->scal, p->iscal, p->pscal, nparts, tol, tol);
+      launch(lsqr_fat_scalar_kernel, 1, 32, 0, p->stream, p->scal, p->iscal);
+      launch(lsqr_fat_vec_kernel, nparts, 256, 0, p->stream, p->scal, p->iscal, x, wv, vhat, ns, p->pscal);
+      launch(lsqr_fat_test_kernel, 1, 32, 0, p->stream, p->scal, p->iscal, p->pscal, nparts, tol, tol);
       LSRN_CUDA_TRY(cudaGetLastError());
       return LSRN_OK;
     }));
@@ -601,19 +601,19 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
       LSRN_TRY(launch_dd_pass(p, x, p->bdev, p->st1, p->pvec, p->pvec2, nullptr));
       LSRN_TRY(launch_reduce_dd(p->pvec, p->pvec2, nslots, q, p->vq, p->vq2, p->stream));
       // g = hi + lo
-      axpy_kernel<<<grid_for(q), 256, 0, p->stream>>>(p->vq, p->vq2, q, 1.0);
+      launch(axpy_kernel, grid_for(q), 256, 0, p->stream, p->vq, p->vq2, q, 1.0);
       LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, h, nullptr, nullptr, c100(p), nullptr, p->stream));
       LSRN_TRY(fill(p, v, r, 0.0));
       LSRN_TRY(fill(p, z, r, 0.0));
       RowArgs a{RM_APPLY, nullptr, nullptr, nullptr, 1.0};
       for (int k = 0; k < steps; ++k) {
         const double* blk = p->coefs + (int64_t)k * 8;
-        cheb_vec_kernel<<<grid_for(r), 256, 0, p->stream>>>(h, v, z, r, blk + 0);
+        launch(cheb_vec_kernel, grid_for(r), 256, 0, p->stream, h, v, z, r, blk + 0);
         LSRN_TRY(launch_gemv(p->Nm, q, r, v, p->tmpq, nullptr, nullptr, c100(p), nullptr, p->stream));
         LSRN_TRY(fused_pass(p, p->tmpq, a, p->vq, nullptr));
         LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, h, h, nullptr, blk + 5, nullptr, p->stream));
       }
-      axpy_kernel<<<grid_for(r), 256, 0, p->stream>>>(y, z, r, 1.0);
+      launch(axpy_kernel, grid_for(r), 256, 0, p->stream, y, z, r, 1.0);
       LSRN_CUDA_TRY(cudaGetLastError());
     } else {
       double* rho = p->vr[5];
@@ -621,7 +621,7 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
       double* x = p->st1;
       LSRN_TRY(launch_dd_pass(p, x, nullptr, nullptr, p->pvec, p->pvec2, nullptr));
       LSRN_TRY(launch_reduce_dd(p->pvec, p->pvec2, nslots, q, p->vq, p->vq2, p->stream));
-      resid_dd_kernel<<<grid_for(q), 256, 0, p->stream>>>(p->bdev, p->vq, p->vq2, q, p->tmpq);
+      launch(resid_dd_kernel, grid_for(q), 256, 0, p->stream, p->bdev, p->vq, p->vq2, q, p->tmpq);
       LSRN_CUDA_TRY(cudaGetLastError());
       LSRN_TRY(launch_gemv(p->NT, r, q, p->tmpq, rho, nullptr, nullptr, c100(p), nullptr, p->stream));
       LSRN_TRY(fill(p, v, p->nstate, 0.0));
@@ -644,7 +644,7 @@ lsrn_status finish_x(Plan* p, double* xout) {
   if (r == 0) return fill(p, xout, p->n, 0.0);
   if (p->tall) return launch_gemv_dd(p->Nm, q, r, p->vr[2], xout, p->stream);
   const double sc = p->ridge ? 1.0 / p->lam : 1.0;
-  scale_copy_kernel<<<grid_for(p->n), 256, 0, p->stream>>>(p->st1, p->n, sc, xout);
+  launch(scale_copy_kernel, grid_for(p->n), 256, 0, p->stream, p->st1, p->n, sc, xout);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }

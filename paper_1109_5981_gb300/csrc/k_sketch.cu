@@ -181,14 +181,14 @@ lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx
   const int64_t nz = (L + lchunk - 1) / lchunk;
   dim3 grid((unsigned)((Q + SK_BN - 1) / SK_BN), (unsigned)((S + SK_BM - 1) / SK_BM), (unsigned)nz);
   if (nz == 1) {
-    sketch_f64_kernel<<<grid, 256, 0, st>>>(X, L, Q, ldx, xscale, S, seed, tag, lchunk, C, ldc, 0);
+    launch(sketch_f64_kernel, grid, 256, 0, st, X, L, Q, ldx, xscale, S, seed, tag, lchunk, C, ldc, 0);
   } else {
     if (scratch == nullptr || scratch_bytes < (size_t)nz * S * Q * sizeof(double))
       return LSRN_ERR_INVALID_ARG;
-    sketch_f64_kernel<<<grid, 256, 0, st>>>(X, L, Q, ldx, xscale, S, seed, tag, lchunk, scratch, Q,
+    launch(sketch_f64_kernel, grid, 256, 0, st, X, L, Q, ldx, xscale, S, seed, tag, lchunk, scratch, Q,
                                             S * Q);
     const int64_t tot = S * Q;
-    splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(scratch, (int)nz, S, Q, C,
+    launch(splitk_reduce_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, scratch, (int)nz, S, Q, C,
                                                                           ldc);
   }
   LSRN_CUDA_TRY(cudaGetLastError());
@@ -199,7 +199,7 @@ lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st) {
   const int64_t tot = ((S + 3) / 4) * Q;
   if (tot == 0) return LSRN_OK;
-  sketch_add_gamma_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, ldc, S, Q, seed, tag,
+  launch(sketch_add_gamma_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, C, ldc, S, Q, seed, tag,
                                                                           lrow0, coef);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
@@ -209,7 +209,7 @@ lsrn_status launch_gamma_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t 
                                int64_t cols, double* g, float* z, cudaStream_t st) {
   const int64_t tot = rows * cols;
   if (tot == 0) return LSRN_OK;
-  gamma_block_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(seed, tag, i0, j0, rows, cols,
+  launch(gamma_block_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, seed, tag, i0, j0, rows, cols,
                                                                       g, z);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
@@ -221,7 +221,7 @@ lsrn_status launch_sketch_csr(const int64_t* colptr, const int32_t* rowidx, cons
   (void)L;
   if (Q == 0 || S == 0) return LSRN_OK;
   dim3 grid((unsigned)Q, (unsigned)((S + 1023) / 1024));
-  sketch_csr_kernel<<<grid, 256, 0, st>>>(colptr, rowidx, vals, Q, xscale, S, seed, tag, C, ldc);
+  launch(sketch_csr_kernel, grid, 256, 0, st, colptr, rowidx, vals, Q, xscale, S, seed, tag, C, ldc);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }

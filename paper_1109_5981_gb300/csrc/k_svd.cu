@@ -235,7 +235,7 @@ lsrn_status run_precond(Plan* p) {
   double* wpart = p->pvec;   // reuse pass partial buffer: needs nrb * Q doubles
   const int64_t cap_rows = std::max<int64_t>(1, (int64_t)(p->nblk + 1) * p->xcols / std::max<int64_t>(Q, 1));
   for (int64_t k = 0; k < Q; ++k) {
-    hh_reflector_kernel<<<1, 256, 0, st>>>(X, S, Q, k, p->tau);
+    launch(hh_reflector_kernel, 1, 256, 0, st, X, S, Q, k, p->tau);
     const int64_t ncols = Q - k - 1;
     if (ncols <= 0) continue;
     const int64_t cblk = (ncols + 127) / 128;
@@ -246,13 +246,13 @@ lsrn_status run_precond(Plan* p) {
     const int64_t rpb = (rows + nrb - 1) / nrb;
     nrb = (rows + rpb - 1) / rpb;
     dim3 grid((unsigned)cblk, (unsigned)nrb);
-    hh_w_kernel<<<grid, 128, 0, st>>>(X, S, Q, k, rpb, wpart, p->tau);
-    hh_update_kernel<<<grid, 128, 0, st>>>(X, S, Q, k, rpb, (int)nrb, wpart, p->tau);
+    launch(hh_w_kernel, grid, 128, 0, st, X, S, Q, k, rpb, wpart, p->tau);
+    launch(hh_update_kernel, grid, 128, 0, st, X, S, Q, k, rpb, (int)nrb, wpart, p->tau);
   }
   LSRN_CUDA_TRY(cudaGetLastError());
   // 2. One-sided Jacobi on the rows of R.
   const int64_t QQ = Q * Q;
-  extract_r_kernel<<<(unsigned)((QQ + 255) / 256), 256, 0, st>>>(X, Q, p->Wj);
+  launch(extract_r_kernel, (unsigned)((QQ + 255) / 256), 256, 0, st, X, Q, p->Wj);
   LSRN_CUDA_TRY(cudaGetLastError());
   const int P = (int)(Q + (Q & 1));
   const double tol = (double)std::max(S, Q) * 0x1p-53;
@@ -267,8 +267,9 @@ lsrn_status run_precond(Plan* p) {
   if (P > 1) {
     LSRN_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (int t = 0; t < P - 1; ++t)
-      jacobi_round_kernel<<<rblocks, 256, 0, st>>>(p->Wj, Q, P, t, tol, rot);
+      launch(jacobi_round_kernel, rblocks, 256, 0, st, p->Wj, Q, P, t, tol, rot);
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    g_kernel_launches.fetch_sub((unsigned long long)(P - 1));   // captured, not run
     if (ce != cudaSuccess) {
       record_cuda_error(ce, "capture jacobi sweep", __FILE__, __LINE__);
       return LSRN_ERR_CUDA;
@@ -282,6 +283,7 @@ lsrn_status run_precond(Plan* p) {
     do {
       cudaMemsetAsync(rot, 0, sizeof(int), st);
       cudaGraphLaunch(gexec, st);
+      g_kernel_launches.fetch_add((unsigned long long)(P - 1));
       cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st);
       cudaError_t se = cudaStreamSynchronize(st);
       if (se != cudaSuccess) {
@@ -298,9 +300,9 @@ lsrn_status run_precond(Plan* p) {
   p->sweeps = sweeps;
   if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;
   // 3. sigma, order, rank, N.
-  row_norms_kernel<<<(unsigned)((Q * 32 + 255) / 256), 256, 0, st>>>(p->Wj, Q, p->tmpq);
+  launch(row_norms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, p->tmpq);
   const double rcond = p->opt.rcond >= 0.0 ? p->opt.rcond : (double)std::max(S, Q) * 0x1p-53;
-  sort_rank_kernel<<<1, 1024, 0, st>>>(p->tmpq, Q, rcond, p->perm, p->sig, p->iscal + IC_CAP);
+  launch(sort_rank_kernel, 1, 1024, 0, st, p->tmpq, Q, rcond, p->perm, p->sig, p->iscal + IC_CAP);
   LSRN_CUDA_TRY(cudaGetLastError());
   int r = 0;
   LSRN_CUDA_TRY(cudaMemcpyAsync(&r, p->iscal + IC_CAP, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -314,7 +316,7 @@ lsrn_status run_precond(Plan* p) {
     LSRN_CUDA_TRY(cudaMemcpyAsync(&p->sigma_min, p->sig + (r - 1), sizeof(double),
                                   cudaMemcpyDeviceToHost, st));
     const int64_t tot = Q * (int64_t)r;
-    form_n_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p->Wj, Q, p->perm, p->sig, r,
+    launch(form_n_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, p->Wj, Q, p->perm, p->sig, r,
                                                                    p->Nm, p->NT);
     LSRN_CUDA_TRY(cudaGetLastError());
     LSRN_CUDA_TRY(cudaStreamSynchronize(st));

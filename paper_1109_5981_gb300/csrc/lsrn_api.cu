@@ -19,6 +19,7 @@ int pass_blocks(int64_t rows, int64_t C);
 lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host);
 
 static thread_local char g_last_error[512];
+std::atomic<unsigned long long> g_kernel_launches{0};
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s -> %s", file, line, what,
@@ -86,7 +87,7 @@ __global__ void gather_matrix_kernel(const void* __restrict__ src, int dtype, in
 lsrn_status gather_matrix(const void* src, int dtype, int64_t ld_row, int64_t ld_col, int64_t rows,
                           int64_t cols, double* out, int64_t ld_out, cudaStream_t st) {
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  gather_matrix_kernel<<<grid, dim3(32, 8), 0, st>>>(src, dtype, ld_row, ld_col, rows, cols, out,
+  launch(gather_matrix_kernel, grid, dim3(32, 8), 0, st, src, dtype, ld_row, ld_col, rows, cols, out,
                                                       ld_out);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
@@ -183,6 +184,14 @@ static lsrn_status dense_setup(Plan* p, const lsrn_matrix* A, bool host) {
   const int64_t ldx = xc + (xc & 1);
   double* Xo = nullptr;
   LSRN_TRY(dalloc_n(p, &Xo, xr * ldx));
+  if (host && layout_ok && A->dtype == LSRN_F64) {   // straight copy, rows of X are rows of the input
+    LSRN_CUDA_TRY(cudaMemcpy2DAsync(Xo, ldx * sizeof(double), A->values, A->ld * sizeof(double),
+                                    xc * sizeof(double), xr, cudaMemcpyHostToDevice, p->stream));
+    p->X = Xo;
+    p->owned_X = Xo;
+    p->ldx = ldx;
+    return LSRN_OK;
+  }
   const void* src = A->values;
   void* staged = nullptr;
   const size_t esz = A->dtype == LSRN_F32 ? 4 : 8;
@@ -241,6 +250,8 @@ const char* lsrn_status_string(lsrn_status s) {
 }
 
 const char* lsrn_last_error_message(void) { return g_last_error; }
+
+uint64_t lsrn_kernel_launches(void) { return (uint64_t)g_kernel_launches.load(); }
 
 lsrn_status lsrn_default_options(lsrn_options* opt) {
   if (opt == nullptr) return LSRN_ERR_INVALID_ARG;

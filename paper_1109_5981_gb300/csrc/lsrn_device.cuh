@@ -14,7 +14,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <utility>
+
 namespace lsrn {
+
+// Kernel launches issued by the library since it was loaded (diagnostic).
+extern std::atomic<unsigned long long> g_kernel_launches;
+
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   Args&&... args) {
+  kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 struct U4 {
   uint32_t x, y, z, w;
