@@ -16,6 +16,7 @@ namespace {
 constexpr int SK_BM = 64;   // sketch rows (i) per CTA
 constexpr int SK_BN = 64;   // columns of X (j) per CTA
 constexpr int SK_BK = 16;   // rows of X (l) per step
+constexpr int SK_CHUNK = 512;  // rows of X summed in plain FP64 before the double-double fold
 
 // FP64 FMA sketch tile: C[i0:i0+64, j0:j0+64] += xscale * sum_l Gamma[l, i] X[l, j]
 // over l in [lbeg, lend).  256 threads, 4x4 outputs each.  The Gamma tile is
@@ -33,12 +34,16 @@ __global__ void __launch_bounds__(256) sketch_f64_kernel(const double* __restric
   const int64_t i0 = (int64_t)blockIdx.y * SK_BM;
   const int64_t lbeg = (int64_t)blockIdx.z * lchunk;
   const int64_t lend = min(L, lbeg + lchunk);
-  double acc[4][4];
+  // Two-level accumulation: acc sums one chunk of SK_CHUNK rows of X, the
+  // chunk sums are folded into a double-double total (hi, lo), so rounding
+  // grows with sqrt(chunk) instead of with the length of the contraction.
+  double acc[4][4], hi[4][4], lo[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.0;
 
+  int steps_in_chunk = 0;
   for (int64_t l0 = lbeg; l0 < lend; l0 += SK_BK) {
     {  // Gamma tile: thread -> (row lr, group of four sketch indices)
       const int lr = tid / 16, g4 = tid % 16;
@@ -74,7 +79,24 @@ __global__ void __launch_bounds__(256) sketch_f64_kernel(const double* __restric
         for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
+    if (++steps_in_chunk == SK_CHUNK / SK_BK) {
+      steps_in_chunk = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          dd_add(hi[u][v], lo[u][v], acc[u][v], 0.0);
+          acc[u][v] = 0.0;
+        }
+    }
   }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      dd_add(hi[u][v], lo[u][v], acc[u][v], 0.0);
+      acc[u][v] = hi[u][v] + lo[u][v];
+    }
   double* o = out + (int64_t)blockIdx.z * out_stride_z;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {

@@ -262,40 +262,16 @@ lsrn_status run_precond(Plan* p) {
   int host_rot = 0;
   int sweeps = 0;
   const int max_sweeps = 40;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
   if (P > 1) {
-    LSRN_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int t = 0; t < P - 1; ++t)
-      launch(jacobi_round_kernel, rblocks, 256, 0, st, p->Wj, Q, P, t, tol, rot);
-    cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    g_kernel_launches.fetch_sub((unsigned long long)(P - 1));   // captured, not run
-    if (ce != cudaSuccess) {
-      record_cuda_error(ce, "capture jacobi sweep", __FILE__, __LINE__);
-      return LSRN_ERR_CUDA;
-    }
-    ce = cudaGraphInstantiate(&gexec, graph, 0);
-    if (ce != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      record_cuda_error(ce, "instantiate jacobi sweep", __FILE__, __LINE__);
-      return LSRN_ERR_CUDA;
-    }
     do {
-      cudaMemsetAsync(rot, 0, sizeof(int), st);
-      cudaGraphLaunch(gexec, st);
-      g_kernel_launches.fetch_add((unsigned long long)(P - 1));
-      cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st);
-      cudaError_t se = cudaStreamSynchronize(st);
-      if (se != cudaSuccess) {
-        cudaGraphExecDestroy(gexec);
-        cudaGraphDestroy(graph);
-        record_cuda_error(se, "jacobi sweep", __FILE__, __LINE__);
-        return LSRN_ERR_CUDA;
-      }
+      LSRN_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int), st));
+      for (int t = 0; t < P - 1; ++t)
+        launch(jacobi_round_kernel, dim3(rblocks), dim3(256), 0, st, p->Wj, Q, P, t, tol, rot);
+      LSRN_CUDA_TRY(cudaGetLastError());
+      LSRN_CUDA_TRY(cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LSRN_CUDA_TRY(cudaStreamSynchronize(st));
       ++sweeps;
     } while (host_rot > 0 && sweeps < max_sweeps);
-    cudaGraphExecDestroy(gexec);
-    cudaGraphDestroy(graph);
   }
   p->sweeps = sweeps;
   if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;
