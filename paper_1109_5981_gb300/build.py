@@ -69,8 +69,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     newest = max(os.path.getmtime(o) for o in objs)
     if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt",
-                                                                  "-lpthread", "-ldl"]
+        # the shared CUDA runtime: one runtime per process when the library is
+        # used next to other CUDA code (e.g. torch), which profilers rely on
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(_nvcc()))), "lib64")
+        cmd = [_nvcc()] + ARCH + ["-shared", "-cudart=shared", "-o", tmp] + objs + [
+            "-Xlinker", f"-rpath,{cudalib}", "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")

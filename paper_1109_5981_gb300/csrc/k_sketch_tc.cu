@@ -1,0 +1,458 @@
+// Tensor-core sketch with FP64 accuracy (Algorithm 1/2 step 3 on tcgen05).
+//
+// C = Gamma^T X (C: S x Q FP64, Gamma: L x S, X: L x Q FP64 row-major) is
+// computed from exact bf16 "digit" slices of both operands:
+//   Gamma = 2^-12 q, q integer, |q| <= 32767:  q = 256 h + g_lo,  |h|, |g_lo| <= 128
+//   X[l, j] = 2^(e_j - 7) sum_{p=1..7} d_p[l, j] 2^(-8(p-1))  (+ |residual| <= 2^(e_j - 56))
+// with e_j a per-column (per-segment) exponent, |d_p| <= 128.  All digits are
+// integers of at most 8 bits, exact in bf16, so every tcgen05.mma product is
+// exact and an FP32 sum of up to 512 rows of two such products stays below
+// 2^24 and is exact too.  Products of equal weight form seven groups
+//   g = 0:  h d_1;   g >= 1:  h d_{g+1} + g_lo d_g,     weight 2^(e_j - 11 - 8 g)
+// (g_lo d_7, weight 2^(e_j - 67), is dropped).  Each group is accumulated
+// exactly in TMEM over a chunk of 512 rows, then folded into FP64 registers;
+// chunk results of all groups are summed in FP64, i.e. the rounding is that of
+// an FP64 sum of a few thousand terms, while the multiplications run on the
+// tensor cores.
+//
+// Operands are split into digit planes in global memory one segment of rows at
+// a time (K-major, bf16), then a 128 x 64 output tile per CTA streams them
+// through a two-stage shared-memory pipeline (cp.async, 128B swizzle) into
+// tcgen05.mma (M=128, N=64, K=16, FP32 accumulators in TMEM, 7 x 64 columns).
+#include <algorithm>
+#include <cmath>
+
+#include "lsrn_device.cuh"
+#include "lsrn_internal.h"
+
+namespace lsrn {
+
+namespace {
+
+constexpr int TC_M = 128;              // sketch rows per tile
+constexpr int TC_N = 64;               // columns of X per tile
+constexpr int TC_KT = 64;              // K per pipeline stage (one 128-byte swizzle row)
+constexpr int TC_CHUNK = 512;          // rows summed exactly in TMEM before the FP64 fold
+constexpr int TC_GROUPS = 7;
+constexpr int TC_DIGITS = 7;
+constexpr int TC_THREADS = 128;
+constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 16 KB
+constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 8 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 88 KB
+constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024 + 64;
+constexpr long long kSpinLimit = 1ll << 26;         // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait with an iteration limit; on timeout record the failure and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
+  d |= (uint64_t)1 << 46;                       // descriptor version
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Copy a (rows x 64) bf16 K-major tile (row stride ld elements) into shared
+// memory in the 128-byte swizzled layout: 16-byte chunk c of row r goes to
+// byte r*128 + ((c ^ (r & 7)) << 4).
+__device__ __forceinline__ void load_tile(uint32_t sdst, const uint16_t* src, int rows,
+                                          int64_t ld, int tid) {
+  const int nchunks = rows * 8;
+  for (int q = tid; q < nchunks; q += TC_THREADS) {
+    const int r = q >> 3, c = q & 7;
+    const uint32_t dst = sdst + (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+    cp_async16(dst, src + (int64_t)r * ld + c * 8);
+  }
+}
+
+// Per-column exponent of a segment: e_j with max_l |X[l, j]| < 2^e_j.  ecol is
+// first set to kNoExp; a column that stays there is all zero.
+constexpr int kNoExp = -100000;
+
+__global__ void colexp_init_kernel(int* __restrict__ ecol, int64_t Q) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < Q) ecol[j] = kNoExp;
+}
+
+__global__ void colexp_kernel(const double* __restrict__ X, int64_t l0, int64_t l1, int64_t Q,
+                              int64_t ldx, int64_t rows_per_block, int* __restrict__ ecol) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Q) return;
+  const int64_t r0 = l0 + (int64_t)blockIdx.y * rows_per_block;
+  const int64_t r1 = min(l1, r0 + rows_per_block);
+  double mx = 0.0;
+  for (int64_t l = r0; l < r1; ++l) mx = fmax(mx, fabs(X[l * ldx + j]));
+  if (mx > 0.0) {
+    int e = 0;
+    frexp(mx, &e);
+    atomicMax(&ecol[j], e);
+  }
+}
+
+__device__ __forceinline__ int col_exponent(const int* ecol, int64_t j) {
+  const int e = ecol[j];
+  return e == kNoExp ? 0 : e;
+}
+
+// The tensor-core GEMM over one segment: Cseg[i, j] += 2^(e_j - 11) * scale *
+// sum_g 2^(-8 g) * sum_l (group g products).  Gh, Gl: S_pad x Lp; D: 7 planes of
+// Q_pad x Lp; all bf16, K-major.
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
+    const uint16_t* __restrict__ Gh, const uint16_t* __restrict__ Gl,
+    const uint16_t* __restrict__ D, int64_t Lp, int64_t Kext, int64_t Qp,
+    const int* __restrict__ ecol, double scale, int64_t S, int64_t Q, double* __restrict__ C,
+    int64_t ldc, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + 2 * STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * TC_N;
+  const int64_t i0 = (int64_t)blockIdx.y * TC_M;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = instr_desc(TC_M, TC_N);
+
+  double acc[TC_N];
+#pragma unroll
+  for (int c = 0; c < TC_N; ++c) acc[c] = 0.0;
+
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  const int64_t nkt = Kext / TC_KT;   // K-tiles holding rows of this segment (row stride Lp)
+  const int kt_per_chunk = TC_CHUNK / TC_KT;
+  int64_t kt = 0;
+  while (kt < nkt && ok) {
+    const int64_t kt_end = (kt + kt_per_chunk < nkt) ? kt + kt_per_chunk : nkt;
+    for (int64_t k = kt; k < kt_end && ok; ++k) {
+      const int st = (int)(k & 1);
+      if (pending[st]) {
+        ok = mbar_wait(&bars[st], phase[st], err);
+        phase[st] ^= 1u;
+        pending[st] = false;
+        tc_fence_after();
+      }
+      if (!ok) break;
+      unsigned char* sbase = smem + st * STAGE_BYTES;
+      const uint32_t s_ah = smem_addr(sbase);
+      const uint32_t s_al = s_ah + TILE_A_BYTES;
+      const uint32_t s_d = s_al + TILE_A_BYTES;
+      const int64_t l0 = k * TC_KT;
+      load_tile(s_ah, Gh + i0 * Lp + l0, TC_M, Lp, tid);
+      load_tile(s_al, Gl + i0 * Lp + l0, TC_M, Lp, tid);
+#pragma unroll 1
+      for (int p = 0; p < TC_DIGITS; ++p)
+        load_tile(s_d + p * TILE_B_BYTES, D + ((int64_t)p * Qp + j0) * Lp + l0, TC_N, Lp, tid);
+      cp_async_wait_all();
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const bool first = (k == kt);
+#pragma unroll
+        for (int ks = 0; ks < TC_KT / 16; ++ks) {
+          const uint64_t ah = smem_desc(s_ah + ks * 32);
+          const uint64_t al = smem_desc(s_al + ks * 32);
+#pragma unroll
+          for (int g = 0; g < TC_GROUPS; ++g) {
+            const uint32_t dt = tmem + (uint32_t)(g * TC_N);
+            const uint64_t bh = smem_desc(s_d + g * TILE_B_BYTES + ks * 32);
+            mma_bf16(dt, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+            if (g >= 1) {
+              const uint64_t bl = smem_desc(s_d + (g - 1) * TILE_B_BYTES + ks * 32);
+              mma_bf16(dt, al, bl, idesc, 1u);
+            }
+          }
+        }
+        mma_commit(&bars[st]);
+      }
+      pending[st] = true;
+      __syncthreads();
+    }
+    // all MMAs of this chunk done
+    for (int st = 0; st < 2 && ok; ++st) {
+      if (pending[st]) {
+        ok = mbar_wait(&bars[st], phase[st], err);
+        phase[st] ^= 1u;
+        pending[st] = false;
+      }
+    }
+    tc_fence_after();
+    if (ok) {
+      const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+      for (int g = 0; g < TC_GROUPS; ++g) {
+        const double w = ldexp(1.0, -8 * g);
+#pragma unroll
+        for (int cb = 0; cb < TC_N / 32; ++cb) {
+          float v[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(g * TC_N + cb * 32), v);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[cb * 32 + c] = fma((double)v[c], w, acc[cb * 32 + c]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    kt = kt_end;
+  }
+  // epilogue: row i0 + tid, columns j0 .. j0 + 63
+  const int64_t i = i0 + tid;
+  if (ok && i < S) {
+#pragma unroll
+    for (int c = 0; c < TC_N; ++c) {
+      const int64_t j = j0 + c;
+      if (j < Q) C[i * ldc + j] += ldexp(acc[c], col_exponent(ecol, j) - 11) * scale;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// bf16 bit pattern of an integer |v| <= 128 (exact: at most 8 significant bits).
+__device__ __forceinline__ uint16_t bf16_int(double v) {
+  return (uint16_t)(__float_as_uint((float)v) >> 16);
+}
+
+// Digit planes of X rows [l0, l0 + Ls): D[p][j][l - l0], transposed through shared memory.
+__global__ void __launch_bounds__(256) split_x_kernel(const double* __restrict__ X, int64_t l0,
+                                                      int64_t l1, int64_t Q, int64_t ldx,
+                                                      const int* __restrict__ ecol, int64_t Qp,
+                                                      int64_t Lp, uint16_t* __restrict__ D) {
+  __shared__ unsigned short tile[TC_DIGITS][32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  const int64_t jb = (int64_t)blockIdx.x * 32, lb = (int64_t)blockIdx.y * 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t l = l0 + lb + r, j = jb + tx;
+    double x = 0.0;
+    if (l < l1 && j < Q) x = ldexp(X[l * ldx + j], -col_exponent(ecol, j));
+    double d = rint(x * 128.0);
+    double rem = x * 128.0 - d;
+    tile[0][r][tx] = bf16_int(d);
+#pragma unroll
+    for (int p = 1; p < TC_DIGITS; ++p) {
+      d = rint(rem * 256.0);
+      rem = rem * 256.0 - d;
+      tile[p][r][tx] = bf16_int(d);
+    }
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = jb + r, l = lb + tx;
+    if (j < Qp && l < Lp) {
+#pragma unroll
+      for (int p = 0; p < TC_DIGITS; ++p) {
+        D[((int64_t)p * Qp + j) * Lp + l] = tile[p][tx][r];
+      }
+    }
+  }
+}
+
+// Digit planes of Gamma rows [l0, l0 + Ls): Gh[i][l - l0], Gl[i][l - l0].
+__global__ void __launch_bounds__(256) gamma_digits_kernel(uint64_t seed, uint32_t tag, int64_t l0,
+                                                           int64_t l1, int64_t S, int64_t Sp,
+                                                           int64_t Lp,
+                                                           uint16_t* __restrict__ Gh,
+                                                           uint16_t* __restrict__ Gl) {
+  __shared__ unsigned short th[32][129], tl[32][129];
+  const int64_t ib = (int64_t)blockIdx.x * 128, lb = (int64_t)blockIdx.y * 32;
+  // generate: thread -> (row r of 32, group of four sketch indices g4 of 32)
+  for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+    const int r = q >> 5, g4 = q & 31;
+    const int64_t l = l0 + lb + r;
+    const int64_t i = ib + 4 * g4;
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l < l1 && i < S) z = normal4(seed, tag, (uint64_t)l, (uint64_t)(i >> 2));
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float qv = (l < l1 && i + k < S) ? rintf(__fmul_rn(zz[k], 4096.0f)) : 0.0f;
+      qv = fminf(fmaxf(qv, -32767.0f), 32767.0f);
+      const float h = rintf(qv * (1.0f / 256.0f));
+      const float lo = qv - 256.0f * h;
+      th[r][4 * g4 + k] = (unsigned short)(__float_as_uint(h) >> 16);
+      tl[r][4 * g4 + k] = (unsigned short)(__float_as_uint(lo) >> 16);
+    }
+  }
+  __syncthreads();
+  // write: row i (128 of them), 32 consecutive l
+  for (int q = threadIdx.x; q < 128 * 32; q += 256) {
+    const int ii = q >> 5, r = q & 31;
+    const int64_t i = ib + ii, l = lb + r;
+    if (i < Sp && l < Lp) {
+      Gh[i * Lp + l] = th[r][ii];
+      Gl[i * Lp + l] = tl[r][ii];
+    }
+  }
+}
+
+__global__ void zero_kernel(double* __restrict__ C, int64_t S, int64_t Q, int64_t ldc) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < S * Q) C[(idx / Q) * ldc + idx % Q] = 0.0;
+}
+
+}  // namespace
+
+// Scratch bytes for a given segment length (rows of X per segment).
+size_t sketch_tc_scratch_bytes(int64_t Ls, int64_t Q, int64_t S) {
+  const int64_t Lp = (Ls + TC_KT - 1) / TC_KT * TC_KT;
+  const int64_t Qp = (Q + TC_N - 1) / TC_N * TC_N;
+  const int64_t Sp = (S + TC_M - 1) / TC_M * TC_M;
+  return (size_t)(2 * Sp + TC_DIGITS * Qp) * Lp * 2 + (size_t)Q * sizeof(int) + 256;
+}
+
+int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_bytes) {
+  const int64_t Qp = (Q + TC_N - 1) / TC_N * TC_N;
+  const int64_t Sp = (S + TC_M - 1) / TC_M * TC_M;
+  const int64_t per_row = (2 * Sp + TC_DIGITS * Qp) * 2;
+  int64_t rows = (int64_t)(budget_bytes / (size_t)std::max<int64_t>(per_row, 1));
+  rows = std::max<int64_t>(TC_CHUNK, rows / TC_CHUNK * TC_CHUNK);
+  const int64_t Lr = (L + TC_KT - 1) / TC_KT * TC_KT;
+  return std::min(rows, Lr);
+}
+
+lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
+                             int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
+                             void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
+                             cudaStream_t st) {
+  const int64_t Qp = (Q + TC_N - 1) / TC_N * TC_N;
+  const int64_t Sp = (S + TC_M - 1) / TC_M * TC_M;
+  const int64_t Lp = (seg_rows + TC_KT - 1) / TC_KT * TC_KT;
+  if (scratch_bytes < sketch_tc_scratch_bytes(seg_rows, Q, S)) return LSRN_ERR_INVALID_ARG;
+  static bool attr_set = false;
+  if (!attr_set) {
+    LSRN_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    attr_set = true;
+  }
+  uint16_t* Gh = (uint16_t*)scratch;
+  uint16_t* Gl = Gh + Sp * Lp;
+  uint16_t* D = Gl + Sp * Lp;
+  int* ecol = (int*)(D + (int64_t)TC_DIGITS * Qp * Lp);
+  const int64_t tot = S * Q;
+  launch(zero_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, C, S, Q, ldc);
+  for (int64_t l0 = 0; l0 < L; l0 += seg_rows) {
+    const int64_t l1 = std::min(L, l0 + seg_rows);
+    const int64_t Lseg = (l1 - l0 + TC_KT - 1) / TC_KT * TC_KT;   // K extent streamed
+    const int64_t rpb = 1024;
+    launch(colexp_init_kernel, dim3((unsigned)((Q + 255) / 256)), dim3(256), 0, st, ecol, Q);
+    launch(colexp_kernel, dim3((unsigned)((Q + 127) / 128), (unsigned)((l1 - l0 + rpb - 1) / rpb)),
+           dim3(128), 0, st, X, l0, l1, Q, ldx, rpb, ecol);
+    launch(split_x_kernel, dim3((unsigned)(Qp / 32), (unsigned)(Lp / 32)), dim3(256), 0, st, X, l0,
+           l1, Q, ldx, (const int*)ecol, Qp, Lp, D);
+    launch(gamma_digits_kernel, dim3((unsigned)(Sp / 128), (unsigned)(Lp / 32)), dim3(256), 0, st,
+           seed, tag, l0, l1, S, Sp, Lp, Gh, Gl);
+    launch(sketch_tc_kernel, dim3((unsigned)(Qp / TC_N), (unsigned)(Sp / TC_M)), dim3(TC_THREADS),
+           (size_t)TC_SMEM, st, (const uint16_t*)Gh, (const uint16_t*)Gl,
+           (const uint16_t*)D, Lp, Lseg, Qp, (const int*)ecol, xscale, S, Q, C, ldc, err);
+  }
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+}  // namespace lsrn

@@ -340,6 +340,24 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
   if (p->csr) {
     LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, p->xscale, p->s,
                                p->opt.seed, tag, p->Xs, p->q, p->stream));
+  } else if (p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
+    int64_t seg = sketch_tc_segment_rows(p->xrows, p->q, p->s, budget);
+    if (const char* env = getenv("LSRN_TC_SEGMENT_ROWS")) {   // testing: force small segments
+      const long long v = atoll(env);
+      if (v >= 64) seg = std::min<int64_t>(seg, (int64_t)(v / 64 * 64));
+    }
+    const size_t scratch = sketch_tc_scratch_bytes(seg, p->q, p->s);
+    void* buf = nullptr;
+    LSRN_CUDA_TRY(cudaMallocAsync(&buf, scratch, p->stream));
+    LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), p->stream));
+    lsrn_status st = launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
+                                      tag, p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR,
+                                      p->stream);
+    cudaFreeAsync(buf, p->stream);
+    LSRN_TRY(st);
   } else {
     const size_t scratch = sketch_f64_scratch_bytes(p->xrows, p->q, p->s);
     double* buf = nullptr;
@@ -361,6 +379,13 @@ lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
   if (p == nullptr) return LSRN_ERR_INVALID_ARG;
   if (p->state < 1) return LSRN_ERR_STATE;
   cudaSetDevice(p->device);
+  if (!p->csr && p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED) {
+    int tcerr = 0;
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&tcerr, p->iscal + IC_TCERR, sizeof(int), cudaMemcpyDeviceToHost,
+                                  p->stream));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (tcerr) return LSRN_ERR_TIMEOUT;
+  }
   cudaEventRecord(p->ev[2], p->stream);
   LSRN_TRY(run_precond(p));
   cudaEventRecord(p->ev[3], p->stream);

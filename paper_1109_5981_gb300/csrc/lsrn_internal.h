@@ -55,7 +55,7 @@ enum ScalarSlot : int {
   SC_COUNT = 32
 };
 
-enum IntSlot : int { IC_DONE = 0, IC_ITN, IC_ISTOP, IC_CAP, IC_ROT, IC_COUNT = 8 };
+enum IntSlot : int { IC_DONE = 0, IC_ITN, IC_ISTOP, IC_CAP, IC_ROT, IC_TCERR, IC_COUNT = 8 };
 
 // Row modes of the fused pass over the rows of X (see k_iter.cu).
 enum RowMode : int {
@@ -145,6 +145,15 @@ lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx
                               int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                               double* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t sketch_f64_scratch_bytes(int64_t L, int64_t Q, int64_t S);
+// Tensor-core sketch (exact bf16 digit slices, FP64-accurate), same contract as
+// launch_sketch_f64; X is processed in segments of seg_rows rows, each needing
+// sketch_tc_scratch_bytes(seg_rows, Q, S) of scratch; *err is set on a timed-out wait.
+size_t sketch_tc_scratch_bytes(int64_t Ls, int64_t Q, int64_t S);
+int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_bytes);
+lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
+                             int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
+                             void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
+                             cudaStream_t st);
 // C[i, j] = scale_c * C[i, j] + coef * Gamma[lrow0 + j, i], i < S, j < Q
 lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st);
