@@ -112,6 +112,9 @@ typedef struct {
   double rnorm_est, arnorm_est;   /* LSQR estimates of ||r||, ||(AN)^T r|| at exit */
   double anorm_est;               /* LSQR estimate of ||AN||_F */
   float t_sketch_ms, t_precond_ms, t_iter_ms, t_refine_ms;  /* device time per phase */
+  float t_sketch_gemm_ms;         /* tensor-core GEMM kernels inside the sketch (0 otherwise) */
+  float t_pass_ms;                /* fused HBM passes over A in the main sweep (sum) */
+  int32_t n_pass;                 /* number of those passes */
 } lsrn_info;
 
 typedef struct lsrn_plan_s* lsrn_plan_t;

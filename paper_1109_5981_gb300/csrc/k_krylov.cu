@@ -364,7 +364,17 @@ static lsrn_status fill(Plan* p, double* v, int64_t n, double val) {
 // One fused pass (+ ridge rows) and its reduction into out (C) and scal[SC_SS].
 static lsrn_status fused_pass(Plan* p, const double* vin, const RowArgs& a, double* out,
                               const int* done) {
-  LSRN_TRY(launch_row_pass(p, vin, a, p->pvec, p->pscal, done));
+  if (p->time_passes) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, p->stream);
+    LSRN_TRY(launch_row_pass(p, vin, a, p->pvec, p->pscal, done));
+    cudaEventRecord(e1, p->stream);
+    p->pass_events.emplace_back(e0, e1);
+  } else {
+    LSRN_TRY(launch_row_pass(p, vin, a, p->pvec, p->pscal, done));
+  }
   LSRN_TRY(launch_extra_rows(p, vin, a, p->pvec, p->pscal, done));
   const int nslots = p->nblk + (p->extra_rows > 0 ? 1 : 0);
   return launch_reduce(p->pvec, nslots, p->xcols, out, p->pscal, p->scal + SC_SS, done, p->stream);

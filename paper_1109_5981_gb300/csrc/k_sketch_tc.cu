@@ -3,13 +3,13 @@
 // C = Gamma^T X (C: S x Q FP64, Gamma: L x S, X: L x Q FP64 row-major) is
 // computed from exact bf16 "digit" slices of both operands:
 //   Gamma = 2^-12 q, q integer, |q| <= 32767:  q = 256 h + g_lo,  |h|, |g_lo| <= 128
-//   X[l, j] = 2^(e_j - 7) sum_{p=1..7} d_p[l, j] 2^(-8(p-1))  (+ |residual| <= 2^(e_j - 56))
+//   X[l, j] = 2^(e_j - 7) sum_{p=1..8} d_p[l, j] 2^(-8(p-1))  (+ |residual| <= 2^(e_j - 64))
 // with e_j a per-column (per-segment) exponent, |d_p| <= 128.  All digits are
 // integers of at most 8 bits, exact in bf16, so every tcgen05.mma product is
 // exact and an FP32 sum of up to 512 rows of two such products stays below
-// 2^24 and is exact too.  Products of equal weight form seven groups
+// 2^24 and is exact too.  Products of equal weight form eight groups
 //   g = 0:  h d_1;   g >= 1:  h d_{g+1} + g_lo d_g,     weight 2^(e_j - 11 - 8 g)
-// (g_lo d_7, weight 2^(e_j - 67), is dropped).  Each group is accumulated
+// (g_lo d_8, at most 2^(e_j - 61) per row, is dropped).  Each group is accumulated
 // exactly in TMEM over a chunk of 512 rows, then folded into FP64 registers;
 // chunk results of all groups are summed in FP64, i.e. the rounding is that of
 // an FP64 sum of a few thousand terms, while the multiplications run on the
@@ -18,7 +18,7 @@
 // Operands are split into digit planes in global memory one segment of rows at
 // a time (K-major, bf16), then a 128 x 64 output tile per CTA streams them
 // through a two-stage shared-memory pipeline (cp.async, 128B swizzle) into
-// tcgen05.mma (M=128, N=64, K=16, FP32 accumulators in TMEM, 7 x 64 columns).
+// tcgen05.mma (M=128, N=64, K=16, FP32 accumulators in TMEM, 8 x 64 columns).
 #include <algorithm>
 #include <cmath>
 
@@ -33,12 +33,12 @@ constexpr int TC_M = 128;              // sketch rows per tile
 constexpr int TC_N = 64;               // columns of X per tile
 constexpr int TC_KT = 64;              // K per pipeline stage (one 128-byte swizzle row)
 constexpr int TC_CHUNK = 512;          // rows summed exactly in TMEM before the FP64 fold
-constexpr int TC_GROUPS = 7;
-constexpr int TC_DIGITS = 7;
+constexpr int TC_GROUPS = 8;
+constexpr int TC_DIGITS = 8;
 constexpr int TC_THREADS = 128;
 constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 16 KB
 constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 8 KB
-constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 88 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 96 KB
 constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024 + 64;
 constexpr long long kSpinLimit = 1ll << 26;         // bounded mbarrier waits
 
@@ -419,7 +419,8 @@ int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_by
 lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
-                             cudaStream_t st) {
+                             cudaStream_t st,
+                             std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events) {
   const int64_t Qp = (Q + TC_N - 1) / TC_N * TC_N;
   const int64_t Sp = (S + TC_M - 1) / TC_M * TC_M;
   const int64_t Lp = (seg_rows + TC_KT - 1) / TC_KT * TC_KT;
@@ -447,9 +448,19 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
            l1, Q, ldx, (const int*)ecol, Qp, Lp, D);
     launch(gamma_digits_kernel, dim3((unsigned)(Sp / 128), (unsigned)(Lp / 32)), dim3(256), 0, st,
            seed, tag, l0, l1, S, Sp, Lp, Gh, Gl);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (gemm_events) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, st);
+    }
     launch(sketch_tc_kernel, dim3((unsigned)(Qp / TC_N), (unsigned)(Sp / TC_M)), dim3(TC_THREADS),
            (size_t)TC_SMEM, st, (const uint16_t*)Gh, (const uint16_t*)Gl,
            (const uint16_t*)D, Lp, Lseg, Qp, (const int*)ecol, xscale, S, Q, C, ldc, err);
+    if (gemm_events) {
+      cudaEventRecord(e1, st);
+      gemm_events->emplace_back(e0, e1);
+    }
   }
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;

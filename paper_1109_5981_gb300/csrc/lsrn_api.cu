@@ -120,6 +120,11 @@ static void release(Plan* p) {
   }
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  for (auto* v : {&p->gemm_events, &p->pass_events})
+    for (auto& pr : *v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
   if (p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -355,7 +360,7 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
     LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), p->stream));
     lsrn_status st = launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
                                       tag, p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR,
-                                      p->stream);
+                                      p->stream, &p->gemm_events);
     cudaFreeAsync(buf, p->stream);
     LSRN_TRY(st);
   } else {
@@ -392,6 +397,14 @@ lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
   LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[3]));
   cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
   cudaEventElapsedTime(&p->t_precond_ms, p->ev[2], p->ev[3]);
+  p->t_sketch_gemm_ms = 0.f;
+  for (auto& pr : p->gemm_events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) p->t_sketch_gemm_ms += ms;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  p->gemm_events.clear();
   p->state = 2;
   if (rank_out) *rank_out = p->rank;
   return LSRN_OK;
@@ -415,6 +428,7 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   inf.sigma_min_sketch = p->sigma_min;
   inf.t_sketch_ms = p->t_sketch_ms;
   inf.t_precond_ms = p->t_precond_ms;
+  inf.t_sketch_gemm_ms = p->t_sketch_gemm_ms;
   lsrn_status result = LSRN_OK;
   const bool xdev = is_device_pointer(x);
   double* xout = xdev ? x : p->xfull;
@@ -422,6 +436,7 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
     LSRN_TRY(finish_x(p, xout));
   } else {
     cudaEventRecord(p->ev[4], p->stream);
+    p->time_passes = true;
     if (use_cs) {
       bool diverged = false;
       LSRN_TRY(run_cs(p, &inf.iterations, &inf.sigma_L, &inf.sigma_U, &diverged));
@@ -436,6 +451,7 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
       inf.arnorm_est = sc[SC_ARNORM];
       inf.anorm_est = sc[SC_ANORM];
     }
+    p->time_passes = false;
     cudaEventRecord(p->ev[5], p->stream);
     if (result == LSRN_OK) {
       LSRN_TRY(run_refine(p, p->opt.refine_max, &inf.refine_iterations));
@@ -445,6 +461,16 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
     LSRN_TRY(finish_x(p, xout));
     LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[6]));
     cudaEventElapsedTime(&inf.t_iter_ms, p->ev[4], p->ev[5]);
+    for (auto& pr : p->pass_events) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        inf.t_pass_ms += ms;
+        inf.n_pass += 1;
+      }
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    p->pass_events.clear();
     cudaEventElapsedTime(&inf.t_refine_ms, p->ev[5], p->ev[6]);
   }
   if (!xdev)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "lsrn.h"
@@ -136,7 +137,10 @@ struct Plan {
   double* pscal = nullptr;          // (nblk + 1) scalar partials
   int nblk = 0;                     // CTAs of the fused pass
   cudaEvent_t ev[8] = {nullptr};
-  float t_sketch_ms = 0, t_precond_ms = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gemm_events;   // tensor-core GEMM launches
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;   // fused passes of the main sweep
+  bool time_passes = false;
+  float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0;
 };
 
 // ---- kernels (launchers) -------------------------------------------------
@@ -153,7 +157,8 @@ int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_by
 lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
-                             cudaStream_t st);
+                             cudaStream_t st,
+                             std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events);
 // C[i, j] = scale_c * C[i, j] + coef * Gamma[lrow0 + j, i], i < S, j < Q
 lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st);
