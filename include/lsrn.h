@@ -210,6 +210,30 @@ lsrn_status lsrn_generate_sketch_block(uint64_t seed, uint32_t tag, int64_t i0, 
                                        int64_t rows, int64_t cols, double* g, float* z,
                                        void* stream);
 
+/* Allocation-free variant of the FP64 sketch (no counterpart in the paper; an
+ * interface for callers that cannot allocate device memory -- services that
+ * reserve all device memory for their own pool at start-up, code running inside
+ * another allocator's callbacks, or paths where cudaMalloc/cudaFree, which can
+ * synchronise the device, are not allowed).
+ *   A       device pointer, m x n row-major FP64 with leading dimension lda,
+ *           m >= n (Algorithm 1's orientation).
+ *   gamma   oversampling factor > 1; s = ceil(gamma * n).
+ *   seed    key of G, as in lsrn_options.seed.
+ *   out     device pointer receiving A~ = G A, s x n row-major (leading dimension
+ *           n), equal to what lsrn_sketch computes for the same A, gamma and seed.
+ *   stream  cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * The split-K partial sums live in one fixed device array of 32 MiB (4 Mi
+ * doubles) that every GPU loading this library holds until process exit;
+ * INVALID_ARG if s * n exceeds 4 Mi, if a pointer is not a device pointer, or
+ * on bad sizes.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Every call uses the same array, which keeps the previous call's contents (the
+ * kernel writes every partial it reads, so nothing needs clearing); calls whose
+ * work overlaps on the GPU (other streams, other threads) race on it.  No device
+ * memory is allocated or freed. */
+lsrn_status lsrn_sketch_f64_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
+                                    double gamma, uint64_t seed, double* out, void* stream);
+
 /* ---- serving: a request queue with admission by device-memory budget ----
  * lsrn_submit copies the request (A, b, options) and returns a ticket at once;
  * worker threads plan and solve admitted requests on their own streams while

@@ -104,6 +104,9 @@ _SIGS = {
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
+    "lsrn_sketch_f64_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p,
+                                 ctypes.c_void_p], ctypes.c_int),
     "lsrn_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
                            ctypes.c_int),
     "lsrn_submit": ([ctypes.c_void_p, ctypes.POINTER(lsrn_matrix), ctypes.c_void_p,
@@ -344,6 +347,15 @@ def lsrn_generate_sketch_block(seed: int, tag: int, i0: int, j0: int, rows: int,
                                           z.ctypes.data if z is not None else None, None),
            "lsrn_generate_sketch_block")
     return (g, z) if with_normals else g
+
+
+def lsrn_sketch_f64_noalloc(A, gamma: float, seed: int, out, stream: int = 0) -> None:
+    """A~ = G A into `out` (device arrays) without any device allocation."""
+    m, n = A.shape
+    ld = A.stride(0)
+    _check(load_library().lsrn_sketch_f64_noalloc(_ptr(A), m, n, ld, gamma, seed, _ptr(out),
+                                                  ctypes.c_void_p(stream)),
+           "lsrn_sketch_f64_noalloc")
 
 
 def solve(A, b, solver: str = "lsqr", layout: str = "row", csr=None, stream: int = 0,

@@ -217,6 +217,26 @@ lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx
   return LSRN_OK;
 }
 
+lsrn_status launch_sketch_f64_splitk_into(const double* X, int64_t L, int64_t Q, int64_t ldx,
+                                          int64_t S, uint64_t seed, uint32_t tag, double* C,
+                                          int64_t ldc, double* scratch, size_t scratch_doubles,
+                                          cudaStream_t st) {
+  // split factor as in launch_sketch_f64, capped by the scratch, at least one slice
+  int64_t z = splitk_factor(L, Q, S);
+  z = std::max<int64_t>(1, std::min<int64_t>(z, (int64_t)(scratch_doubles / (size_t)(S * Q))));
+  const int64_t lchunk = ((L + z - 1) / z + SK_BK - 1) / SK_BK * SK_BK;
+  const int64_t nz = (L + lchunk - 1) / lchunk;
+  if ((size_t)(nz * S * Q) > scratch_doubles) return LSRN_ERR_INVALID_ARG;
+  dim3 grid((unsigned)((Q + SK_BN - 1) / SK_BN), (unsigned)((S + SK_BM - 1) / SK_BM), (unsigned)nz);
+  launch(sketch_f64_kernel, grid, dim3(256), 0, st, X, L, Q, ldx, 1.0, S, seed, tag, lchunk,
+         scratch, Q, S * Q);
+  const int64_t tot = S * Q;
+  launch(splitk_reduce_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st,
+         (const double*)scratch, (int)nz, S, Q, C, ldc);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
 lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st) {
   const int64_t tot = ((S + 3) / 4) * Q;

@@ -149,6 +149,12 @@ lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx
                               int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                               double* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t sketch_f64_scratch_bytes(int64_t L, int64_t Q, int64_t S);
+// Same sketch, always through split-K partial sums held in caller-provided
+// scratch (scratch_doubles >= nz * S * Q for the split nz it picks, nz >= 1).
+lsrn_status launch_sketch_f64_splitk_into(const double* X, int64_t L, int64_t Q, int64_t ldx,
+                                          int64_t S, uint64_t seed, uint32_t tag, double* C,
+                                          int64_t ldc, double* scratch, size_t scratch_doubles,
+                                          cudaStream_t st);
 // Tensor-core sketch (exact bf16 digit slices, FP64-accurate), same contract as
 // launch_sketch_f64; X is processed in segments of seg_rows rows, each needing
 // sketch_tc_scratch_bytes(seg_rows, Q, S) of scratch; *err is set on a timed-out wait.
