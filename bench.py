@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solver", default="lsqr", choices=["lsqr", "cs"])
     ap.add_argument("--sketch", default="tc", choices=["f64", "tc"])
+    ap.add_argument("--iter", default="f64", choices=["f64", "f32"])
     ap.add_argument("--m", type=int, default=M)
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--rank", type=int, default=RANK)
@@ -237,7 +238,8 @@ def main():
     xstar = O.minlen_from_factors(P.apply_Ut, P.sigma, P.apply_V, b.cpu().numpy())
     opts = L.default_options(seed=1234 + rank,
                              sketch_mode=L.LSRN_SKETCH_TC_SLICED if args.sketch == "tc"
-                             else L.LSRN_SKETCH_F64)
+                             else L.LSRN_SKETCH_F64,
+                             iter_mode=L.LSRN_ITER_F32 if args.iter == "f32" else L.LSRN_ITER_F64)
     solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
 
     def step():
@@ -309,14 +311,23 @@ def main():
     else:
         flops = 4.0 * args.m * args.n          # one dot + one axpy per element of A
         achieved = flops / (t_pass * 1e-3) / 1e12
-        roofline = {"kernel": "row_pass_kernel (fused A(Nv) and A^T u, FP64)", "bound": "alu",
-                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": None,
-                    "peak_source": "FP64 FMA throughput measured in this run (lsrn_probe_fp64_fma)",
-                    "work_per_launch": "4*m*n flop (8*m*n bytes of A)",
-                    "hbm_gbs": 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9,
-                    "hbm_frac_of_measured": 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
-                    / peaks.get("hbm_gbs", 6669.5)}
+        if args.iter == "f32":
+            gbs = 4.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
+            peak = peaks.get("hbm_gbs", 6669.5)
+            roofline = {"kernel": "row_pass_kernel<float> (fused A(Nv) and A^T u on FP32 A)",
+                        "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "traffic": None,
+                        "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
+                        "work_per_launch": "4*m*n bytes (FP32 copy of A read once)"}
+        else:
+            roofline = {"kernel": "row_pass_kernel (fused A(Nv) and A^T u, FP64)", "bound": "alu",
+                      "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                      "frac": achieved / fp64_peak, "traffic": None,
+                      "peak_source": "FP64 FMA throughput measured in this run (lsrn_probe_fp64_fma)",
+                      "work_per_launch": "4*m*n flop (8*m*n bytes of A)",
+                      "hbm_gbs": 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9,
+                      "hbm_frac_of_measured": 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
+                      / peaks.get("hbm_gbs", 6669.5)}
     kernel_ms = {"sketch_gemm_total": t_gemm, "pass_each": t_pass, "pass_total": t_pass_tot,
                  "passes": n_pass}
 
@@ -358,8 +369,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator, no dataset)",
             "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, cond 1e6, "
-                                   f"noise 1e-4, gamma 2, {args.solver.upper()} tol 1e-14 + 1 "
-                                   f"refinement, sketch {args.sketch}",
+                                   f"noise 1e-4, gamma 2, {args.solver.upper()} tol 1e-14 + "
+                                   f"refinement, sketch {args.sketch}, passes {args.iter}",
                        "l2": "inputs larger than L2 (A is 16 GB)",
                        "parallelism": "independent problem per GPU"},
             "accuracy": {"max_rel_err_vs_planted_xstar": max(errs), "target": 1e-10,
@@ -369,6 +380,7 @@ def main():
                           "iter": float(np.mean([i["t_iter_ms"] for i in infos])),
                           "refine": float(np.mean([i["t_refine_ms"] for i in infos]))},
             "iterations": info["iterations"], "refine_iterations": info["refine_iterations"],
+            "refine_steps": info["refine_steps"],
             "rank": info["rank"], "s": s,
             "roofline": roofline,
             "kernel_ms": kernel_ms,

@@ -65,6 +65,13 @@ typedef enum {
 typedef enum { LSRN_F64 = 0, LSRN_F32 = 1 } lsrn_dtype;
 
 typedef enum {
+  LSRN_ITER_F64 = 0,            /* every pass over A in FP64 */
+  LSRN_ITER_F32 = 1             /* passes stream an FP32 copy of A (FP32 products); the sweep
+                                   stops at max(tol, 1e-6) and double-double refinement
+                                   against the FP64 A restores full accuracy */
+} lsrn_iter_mode;
+
+typedef enum {
   LSRN_SKETCH_F64 = 0,          /* FP64 FMA arithmetic */
   LSRN_SKETCH_TC_SLICED = 1     /* tensor cores on exact bf16 slices of G and A,
                                    FP64-accurate (dense A only) */
@@ -92,10 +99,13 @@ typedef struct {
   double cs_alpha;     /* alpha of Theorem 4.5 used for the CS bounds; < 0: 1/sqrt(s) */
   double refine_tol;   /* relative tolerance of each refinement correction (default 1e-3) */
   int32_t max_iter;    /* LSQR iteration cap; < 0: ceil(1.5 * Theorem 4.6 bound) */
-  int32_t refine_max;  /* refinement steps after the iteration (default 1; 0 = paper only) */
+  int32_t refine_max;  /* refinement steps after the iteration (default 1; 0 = paper only);
+                          steps stop early once one changes x by <= 1e-12 relative */
   uint64_t seed;       /* key of the counter-based generator of G (default 0) */
   int32_t sketch_mode; /* lsrn_sketch_mode (default LSRN_SKETCH_F64) */
-  int32_t reserved;
+  int32_t iter_mode;   /* lsrn_iter_mode (default LSRN_ITER_F64); LSRN_ITER_F32 keeps an
+                          FP32 copy of A (4 bytes per entry) and allows at least four
+                          refinement steps, stopping once a step changes x by <= 1e-12 */
 } lsrn_options;
 
 typedef struct {

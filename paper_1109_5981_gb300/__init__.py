@@ -36,6 +36,7 @@ LSRN_ERR_UNSUPPORTED = -9
 LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
 LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED = 0, 1
+LSRN_ITER_F64, LSRN_ITER_F32 = 0, 1
 
 
 class lsrn_matrix(ctypes.Structure):
@@ -50,7 +51,7 @@ class lsrn_options(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("cs_alpha", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("sketch_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sketch_mode", ctypes.c_int32), ("iter_mode", ctypes.c_int32)]
 
 
 class lsrn_info(ctypes.Structure):

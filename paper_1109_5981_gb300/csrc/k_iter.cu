@@ -72,8 +72,26 @@ __device__ __forceinline__ bool mode_reads_st0(int mode) {
 }
 
 // TPR threads cover one row (2 * TPR * SLOTS columns max); R rows per step per group.
-template <int TPR, int SLOTS, int R>
-__global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __restrict__ X, int64_t rows,
+template <class T>
+__device__ __forceinline__ void load_pair(const T* p, T& x, T& y);
+template <>
+__device__ __forceinline__ void load_pair<double>(const double* p, double& x, double& y) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  x = v.x;
+  y = v.y;
+}
+template <>
+__device__ __forceinline__ void load_pair<float>(const float* p, float& x, float& y) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  x = v.x;
+  y = v.y;
+}
+
+// T = double: FP64 pass over A; T = float: the same pass over an FP32 copy of A
+// with FP32 products and per-thread sums (row sums, coefficients and partials
+// in FP64).
+template <class T, int TPR, int SLOTS, int R>
+__global__ void __launch_bounds__(kThreads) row_pass_kernel(const T* __restrict__ X, int64_t rows,
                                                             int C, int64_t ldx,
                                                             const double* __restrict__ vin,
                                                             RowArgs args, double* __restrict__ pvec,
@@ -94,19 +112,19 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
     k.c0 = args.coef[0];
     k.c1 = args.coef[1];
   }
-  double w[SLOTS][2], acc[SLOTS][2];
+  T w[SLOTS][2], acc[SLOTS][2];
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int c = 2 * gl + 2 * TPR * s;
-    w[s][0] = (need_dot && c < C) ? vin[c] : 0.0;
-    w[s][1] = (need_dot && c + 1 < C) ? vin[c + 1] : 0.0;
-    acc[s][0] = acc[s][1] = 0.0;
+    w[s][0] = (need_dot && c < C) ? (T)vin[c] : (T)0;
+    w[s][1] = (need_dot && c + 1 < C) ? (T)vin[c + 1] : (T)0;
+    acc[s][0] = acc[s][1] = (T)0;
   }
   double ss = 0.0;
   const int64_t step = (int64_t)gridDim.x * GPC * R;
   int buf = 0;
   for (int64_t base = (int64_t)blockIdx.x * GPC * R; base < rows; base += step) {
-    double a[R][SLOTS][2];
+    T a[R][SLOTS][2];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t i = base + gid * R + r;
@@ -114,14 +132,12 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
       for (int s = 0; s < SLOTS; ++s) {
         const int c = 2 * gl + 2 * TPR * s;
         if (i < rows && c + 1 < C) {
-          const double2 v = *reinterpret_cast<const double2*>(X + i * ldx + c);
-          a[r][s][0] = v.x;
-          a[r][s][1] = v.y;
+          load_pair<T>(X + i * ldx + c, a[r][s][0], a[r][s][1]);
         } else if (i < rows && c < C) {
           a[r][s][0] = X[i * ldx + c];
-          a[r][s][1] = 0.0;
+          a[r][s][1] = (T)0;
         } else {
-          a[r][s][0] = a[r][s][1] = 0.0;
+          a[r][s][0] = a[r][s][1] = (T)0;
         }
       }
     }
@@ -137,12 +153,12 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
     double d[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      double t = 0.0;
+      T t = (T)0;
       if (need_dot) {
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) t = fma(a[r][s][0], w[s][0], fma(a[r][s][1], w[s][1], t));
       }
-      d[r] = t;
+      d[r] = (double)t;
     }
     if (need_dot) {
       if (TPR <= 32) {
@@ -175,10 +191,11 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
         double ss_dummy = 0.0;
         tacc = row_coef(args, k, i, d[r], s0v[r], s1v[r], gl == 0, gl == 0 ? ss : ss_dummy);
       }
+      const T tc = (T)tacc;
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
-        acc[s][0] = fma(tacc, a[r][s][0], acc[s][0]);
-        acc[s][1] = fma(tacc, a[r][s][1], acc[s][1]);
+        acc[s][0] = fma(tc, a[r][s][0], acc[s][0]);
+        acc[s][1] = fma(tc, a[r][s][1], acc[s][1]);
       }
     }
   }
@@ -188,8 +205,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const int c = 2 * gl + 2 * TPR * s;
-      cta_acc[gid][2 * TPR * s + 2 * gl] = acc[s][0];
-      cta_acc[gid][2 * TPR * s + 2 * gl + 1] = acc[s][1];
+      cta_acc[gid][2 * TPR * s + 2 * gl] = (double)acc[s][0];
+      cta_acc[gid][2 * TPR * s + 2 * gl + 1] = (double)acc[s][1];
       (void)c;
     }
     __syncthreads();
@@ -202,8 +219,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const double* __rest
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const int c = 2 * gl + 2 * TPR * s;
-      if (c < C) out[c] = acc[s][0];
-      if (c + 1 < C) out[c + 1] = acc[s][1];
+      if (c < C) out[c] = (double)acc[s][0];
+      if (c + 1 < C) out[c + 1] = (double)acc[s][1];
     }
   }
   ss = group_sum<32>(ss);
@@ -460,6 +477,26 @@ lsrn_status launch_gemv_dd(const double* M, int64_t R, int64_t C, const double* 
   return LSRN_OK;
 }
 
+namespace {
+__global__ void to_f32_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                              float* __restrict__ Y, int64_t ldy) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * ldy) return;
+  const int64_t i = idx / ldy, j = idx % ldy;
+  Y[idx] = j < cols ? (float)X[i * ldx + j] : 0.0f;
+}
+}  // namespace
+
+lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
+                          int64_t ldy, cudaStream_t st) {
+  const int64_t tot = rows * ldy;
+  if (tot == 0) return LSRN_OK;
+  launch(to_f32_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, X, rows, cols, ldx,
+         Y, ldy);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
 static int pick_layout(int64_t C, int* tpr, int* slots) {
   if (C <= 64) { *tpr = 32; *slots = 1; }
   else if (C <= 128) { *tpr = 32; *slots = 2; }
@@ -487,16 +524,27 @@ lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, 
   if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
   const int C = (int)p->xcols;
   dim3 grid(p->nblk);
-#define LSRN_ROWPASS(T, S, R)                                                                   \
-  launch(row_pass_kernel<T, S, R>, grid, kThreads, 0, p->stream, p->X, p->xrows, C, p->ldx, vin, a, \
-                                                             pvec, pscal, done)
-  if (tpr == 32 && slots == 1) LSRN_ROWPASS(32, 1, 4);
-  else if (tpr == 32) LSRN_ROWPASS(32, 2, 4);
-  else if (tpr == 64) LSRN_ROWPASS(64, 2, 4);
-  else if (tpr == 128) LSRN_ROWPASS(128, 2, 4);
-  else if (slots == 2) LSRN_ROWPASS(256, 2, 4);
-  else if (slots == 4) LSRN_ROWPASS(256, 4, 2);
-  else LSRN_ROWPASS(256, 8, 1);
+#define LSRN_ROWPASS(E, T, S, R)                                                        \
+  launch(row_pass_kernel<E, T, S, R>, grid, kThreads, 0, p->stream, (const E*)xp, p->xrows, C, \
+         ldx, vin, a, pvec, pscal, done)
+#define LSRN_ROWPASS_ALL(E)                           \
+  if (tpr == 32 && slots == 1) LSRN_ROWPASS(E, 32, 1, 4); \
+  else if (tpr == 32) LSRN_ROWPASS(E, 32, 2, 4);          \
+  else if (tpr == 64) LSRN_ROWPASS(E, 64, 2, 4);          \
+  else if (tpr == 128) LSRN_ROWPASS(E, 128, 2, 4);        \
+  else if (slots == 2) LSRN_ROWPASS(E, 256, 2, 4);        \
+  else if (slots == 4) LSRN_ROWPASS(E, 256, 4, 2);        \
+  else LSRN_ROWPASS(E, 256, 8, 1);
+  if (p->pass_f32) {
+    const void* xp = p->X32;
+    const int64_t ldx = p->ldx32;
+    LSRN_ROWPASS_ALL(float)
+  } else {
+    const void* xp = p->X;
+    const int64_t ldx = p->ldx;
+    LSRN_ROWPASS_ALL(double)
+  }
+#undef LSRN_ROWPASS_ALL
 #undef LSRN_ROWPASS
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;

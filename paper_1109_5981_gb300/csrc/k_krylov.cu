@@ -345,7 +345,52 @@ inline unsigned grid_for(int64_t n) {
 
 }  // namespace
 
+// partial sums of ||a - b||^2 (part[2k]) and ||b||^2 (part[2k+1])
+__global__ void diffnorm_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                double* __restrict__ part) {
+  __shared__ double s1[8], s2[8];
+  double d2 = 0.0, b2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = a[i] - b[i];
+    d2 = fma(d, d, d2);
+    b2 = fma(b[i], b[i], b2);
+  }
+  d2 = group_sum<32>(d2);
+  b2 = group_sum<32>(b2);
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = d2;
+    s2[threadIdx.x >> 5] = b2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      t1 += s1[w];
+      t2 += s2[w];
+    }
+    part[2 * blockIdx.x] = t1;
+    part[2 * blockIdx.x + 1] = t2;
+  }
+}
+
 // ---- helpers used by the host drivers --------------------------------------
+// ||a - b|| / ||b|| (synchronises)
+static lsrn_status rel_change(Plan* p, const double* a, const double* b, int64_t n, double* out) {
+  const int parts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 64);
+  launch(diffnorm_kernel, dim3(parts), dim3(256), 0, p->stream, a, b, n, p->pscal);
+  double host[128];
+  LSRN_CUDA_TRY(cudaMemcpyAsync(host, p->pscal, 2 * parts * sizeof(double), cudaMemcpyDeviceToHost,
+                                p->stream));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  double d2 = 0.0, b2 = 0.0;
+  for (int i = 0; i < parts; ++i) {
+    d2 += host[2 * i];
+    b2 += host[2 * i + 1];
+  }
+  *out = b2 > 0.0 ? std::sqrt(d2 / b2) : (d2 > 0.0 ? 1.0 : 0.0);
+  return LSRN_OK;
+}
 static lsrn_status sumsq(Plan* p, const double* v, int64_t n, double* out) {
   const int parts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 2 * num_sms());
   launch(sumsq_kernel, parts, 256, 0, p->stream, v, n, p->pscal);
@@ -400,10 +445,15 @@ static lsrn_status iterate(Plan* p, int cap, F body) {
   return LSRN_OK;
 }
 
+// Tolerance of the main sweep: the option, or the FP32 floor when passes run in FP32.
+static double sweep_tol(const Plan* p) {
+  return p->opt.iter_mode == LSRN_ITER_F32 ? std::max(p->opt.tol, 1e-6) : p->opt.tol;
+}
+
 static int lsqr_cap(const Plan* p) {
   if (p->opt.max_iter >= 0) return std::max(1, p->opt.max_iter);
   const double rs = (double)p->rank / (double)p->s;
-  const double bound = (std::log(p->opt.tol) - std::log(2.0)) / std::log(std::sqrt(rs));
+  const double bound = (std::log(sweep_tol(p)) - std::log(2.0)) / std::log(std::sqrt(rs));
   return std::max(1, (int)std::ceil(1.5 * bound));
 }
 
@@ -466,7 +516,8 @@ static lsrn_status upload_coefs(Plan* p, const std::vector<double>& t) {
 
 lsrn_status run_lsqr(Plan* p, int* iters, int* istop) {
   const int64_t r = p->rank, q = p->q;
-  const double tol = p->opt.tol;
+  const double tol = sweep_tol(p);
+  p->pass_f32 = p->X32 != nullptr;
   double* v = p->vr[0];
   double* w = p->vr[1];
   double* y = p->vr[2];
@@ -543,8 +594,9 @@ lsrn_status run_cs(Plan* p, int* iters, double* sL_out, double* sU_out, bool* di
   *sL_out = sL;
   *sU_out = sU;
   int steps = 0;
-  LSRN_TRY(upload_coefs(p, cheb_table(sL, sU, p->opt.tol, &steps)));
+  LSRN_TRY(upload_coefs(p, cheb_table(sL, sU, sweep_tol(p), &steps)));
   *iters = steps;
+  p->pass_f32 = p->X32 != nullptr;
   double ss0 = 0.0, ss1 = 0.0;
   if (p->tall) {
     double* v = p->vr[0];
@@ -591,9 +643,12 @@ lsrn_status run_cs(Plan* p, int* iters, double* sL_out, double* sU_out, bool* di
 // r = b - B x and g = B^T r in double-double, then K z = N^T g with
 // K = N^T B^T B N by Algorithm 3's recurrence, y += z.  m < n: r = b - B x in
 // double-double, then Algorithm 3 on min ||M^T B d - M^T r||, x += d.
-lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
+lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
   *inner = 0;
+  *taken = 0;
+  if (p->X32 != nullptr) nsteps = std::max(nsteps, 4);
   if (nsteps <= 0 || p->rank == 0) return LSRN_OK;
+  p->pass_f32 = p->X32 != nullptr;
   const int64_t r = p->rank, q = p->q;
   double sL, sU;
   if (thm45_bounds(p, &sL, &sU) != LSRN_OK) return LSRN_OK;   // no bounds: skip refinement
@@ -601,6 +656,7 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
   LSRN_TRY(upload_coefs(p, cheb_table(sL, sU, p->opt.refine_tol, &steps)));
   const int nslots = p->nblk + (p->extra_rows ? 1 : 0);
   for (int it = 0; it < nsteps; ++it) {
+    double change = 0.0;
     if (p->tall) {
       double* y = p->vr[2];
       double* h = p->vr[3];
@@ -624,6 +680,9 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
         LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, h, h, nullptr, blk + 5, nullptr, p->stream));
       }
       launch(axpy_kernel, grid_for(r), 256, 0, p->stream, y, z, r, 1.0);
+      // relative change of x = N y made by this step
+      LSRN_TRY(launch_gemv_dd(p->Nm, q, r, y, p->tmpq, p->stream));
+      LSRN_TRY(rel_change(p, x, p->tmpq, q, &change));
       LSRN_CUDA_TRY(cudaGetLastError());
     } else {
       double* rho = p->vr[5];
@@ -635,6 +694,8 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
       LSRN_CUDA_TRY(cudaGetLastError());
       LSRN_TRY(launch_gemv(p->NT, r, q, p->tmpq, rho, nullptr, nullptr, c100(p), nullptr, p->stream));
       LSRN_TRY(fill(p, v, p->nstate, 0.0));
+      LSRN_CUDA_TRY(cudaMemcpyAsync(p->xfull, x, p->nstate * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, p->stream));
       for (int k = 0; k < steps; ++k) {
         const double* blk = p->coefs + (int64_t)k * 8;
         LSRN_TRY(launch_gemv(p->Nm, q, r, rho, p->vq2, nullptr, nullptr, c100(p), nullptr, p->stream));
@@ -642,9 +703,13 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner) {
         LSRN_TRY(fused_pass(p, p->vq2, a, p->vq, nullptr));
         LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, rho, rho, nullptr, blk + 5, nullptr, p->stream));
       }
+      LSRN_TRY(rel_change(p, p->xfull, x, p->nstate, &change));
     }
     *inner += steps;
+    *taken += 1;
+    if (change <= 1e-12) break;
   }
+  p->pass_f32 = false;
   return LSRN_OK;
 }
 

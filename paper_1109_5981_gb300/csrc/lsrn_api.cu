@@ -13,7 +13,7 @@ namespace lsrn {
 
 lsrn_status run_lsqr(Plan* p, int* iters, int* istop);
 lsrn_status run_cs(Plan* p, int* iters, double* sL, double* sU, bool* diverged);
-lsrn_status run_refine(Plan* p, int nsteps, int* inner);
+lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken);
 lsrn_status finish_x(Plan* p, double* xout);
 int pass_blocks(int64_t rows, int64_t C);
 lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host);
@@ -137,6 +137,7 @@ static lsrn_status validate_options(const lsrn_options& o) {
   if (!(o.refine_tol > 0.0) || !(o.refine_tol < 1.0)) return LSRN_ERR_INVALID_ARG;
   if (o.sketch_mode != LSRN_SKETCH_F64 && o.sketch_mode != LSRN_SKETCH_TC_SLICED)
     return LSRN_ERR_INVALID_ARG;
+  if (o.iter_mode != LSRN_ITER_F64 && o.iter_mode != LSRN_ITER_F32) return LSRN_ERR_INVALID_ARG;
   return LSRN_OK;
 }
 
@@ -327,6 +328,14 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   lsrn_status st;
   if (p->csr) st = csr_plan_setup(p, A, host);
   else st = dense_setup(p, A, host);
+  if (st == LSRN_OK && o.iter_mode == LSRN_ITER_F32 && !p->csr) {
+    p->ldx32 = p->xcols + (p->xcols & 1);
+    float* x32 = nullptr;
+    st = dalloc_n(p, &x32, p->xrows * p->ldx32);
+    if (st == LSRN_OK)
+      st = launch_to_f32(p->X, p->xrows, p->xcols, p->ldx, x32, p->ldx32, p->stream);
+    p->X32 = x32;
+  }
   if (st == LSRN_OK) st = plan_workspace(p);
   if (st == LSRN_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LSRN_ERR_CUDA;
   if (st != LSRN_OK) {
@@ -454,8 +463,7 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
     p->time_passes = false;
     cudaEventRecord(p->ev[5], p->stream);
     if (result == LSRN_OK) {
-      LSRN_TRY(run_refine(p, p->opt.refine_max, &inf.refine_iterations));
-      inf.refine_steps = inf.refine_iterations > 0 ? p->opt.refine_max : 0;
+      LSRN_TRY(run_refine(p, p->opt.refine_max, &inf.refine_iterations, &inf.refine_steps));
     }
     cudaEventRecord(p->ev[6], p->stream);
     LSRN_TRY(finish_x(p, xout));

@@ -97,6 +97,9 @@ struct Plan {
   double extra_coef = 0.0;
   int64_t nstate = 0;               // xrows + extra_rows
   double* owned_X = nullptr;        // plan-owned copy of X, if any
+  const float* X32 = nullptr;       // FP32 copy of X (iteration mode LSRN_ITER_F32)
+  int64_t ldx32 = 0;
+  bool pass_f32 = false;            // fused passes currently stream X32
 
   // CSR (m >= n: A; m < n: A^T) in both orientations for deterministic passes
   const int64_t* rp = nullptr;  const int32_t* ci = nullptr;  const double* cv = nullptr;   // rows of X
@@ -197,6 +200,9 @@ lsrn_status launch_reduce_dd(const double* phi, const double* plo, int nslots, i
 lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, double* out,
                         const double* y, double* y2, const double* c, const int* done,
                         cudaStream_t st);
+// Y (rows x ldy, FP32, zero beyond cols) = X (rows x cols, FP64, ldx)
+lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
+                          int64_t ldy, cudaStream_t st);
 // out[i] = M_i . v accumulated in double-double (warp per row)
 lsrn_status launch_gemv_dd(const double* M, int64_t R, int64_t C, const double* v, double* out,
                            cudaStream_t st);
