@@ -66,9 +66,12 @@ typedef enum { LSRN_F64 = 0, LSRN_F32 = 1 } lsrn_dtype;
 
 typedef enum {
   LSRN_ITER_F64 = 0,            /* every pass over A in FP64 */
-  LSRN_ITER_F32 = 1             /* passes stream an FP32 copy of A (FP32 products); the sweep
-                                   stops at max(tol, 1e-6) and double-double refinement
-                                   against the FP64 A restores full accuracy */
+  LSRN_ITER_F32 = 1             /* m >= n: passes stream an FP32 copy of A (FP32 products); the
+                                   sweep stops at max(tol, 1e-6) and double-double refinement
+                                   against the FP64 A restores full accuracy.  x = N y stays in
+                                   range(N) whatever the pass precision.  For m < n the option
+                                   is ignored (FP64 passes): there x is iterated in R^n and
+                                   FP32 rounding of A would add components in null(A). */
 } lsrn_iter_mode;
 
 typedef enum {

@@ -328,7 +328,9 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   lsrn_status st;
   if (p->csr) st = csr_plan_setup(p, A, host);
   else st = dense_setup(p, A, host);
-  if (st == LSRN_OK && o.iter_mode == LSRN_ITER_F32 && !p->csr) {
+  // FP32 passes only for m >= n: there x = N y stays in range(N), which the sketch fixes;
+  // for m < n the iterate lives in R^n and FP32 rounding of A would let null(A) in.
+  if (st == LSRN_OK && o.iter_mode == LSRN_ITER_F32 && !p->csr && p->tall) {
     p->ldx32 = p->xcols + (p->xcols & 1);
     float* x32 = nullptr;
     st = dalloc_n(p, &x32, p->xrows * p->ldx32);

@@ -34,6 +34,7 @@ def test_mixed_c1(solver, sketch):
 
 @pytest.mark.parametrize("solver", ["lsqr", "cs"])
 def test_mixed_fat_and_ridge(solver):
+    # m < n keeps FP64 passes (the option is ignored there); m >= n ridge uses FP32 passes
     P = W.dense_haar(1500, 70, 55, 1e5, 0.0, seed=4)
     A = np.ascontiguousarray(P.A.T)
     b = A @ np.random.Generator(np.random.PCG64(5)).standard_normal(1500)
