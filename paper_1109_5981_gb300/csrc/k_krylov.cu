@@ -447,7 +447,7 @@ static lsrn_status iterate(Plan* p, int cap, F body) {
 
 // Tolerance of the main sweep: the option, or the FP32 floor when passes run in FP32.
 static double sweep_tol(const Plan* p) {
-  return p->opt.iter_mode == LSRN_ITER_F32 ? std::max(p->opt.tol, 1e-6) : p->opt.tol;
+  return p->X32 != nullptr ? std::max(p->opt.tol, 1e-6) : p->opt.tol;
 }
 
 static int lsqr_cap(const Plan* p) {
