@@ -107,8 +107,10 @@ typedef struct {
   uint64_t seed;       /* key of the counter-based generator of G (default 0) */
   int32_t sketch_mode; /* lsrn_sketch_mode (default LSRN_SKETCH_F64) */
   int32_t iter_mode;   /* lsrn_iter_mode (default LSRN_ITER_F64); LSRN_ITER_F32 keeps an
-                          FP32 copy of A (4 bytes per entry) and allows at least four
-                          refinement steps, stopping once a step changes x by <= 1e-12 */
+                          FP32 copy of A (4 bytes per entry) and allows at least six
+                          refinement steps, stopping once a step changes x by <= 1e-12;
+                          correction passes switch from FP32 to FP64 as soon as a step
+                          shrinks the change by less than 20x */
 } lsrn_options;
 
 typedef struct {

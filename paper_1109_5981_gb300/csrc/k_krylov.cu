@@ -646,9 +646,13 @@ lsrn_status run_cs(Plan* p, int* iters, double* sL_out, double* sU_out, bool* di
 lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
   *inner = 0;
   *taken = 0;
-  if (p->X32 != nullptr) nsteps = std::max(nsteps, 4);
+  // With an FP32 copy of A, correction passes start in FP32 and switch to FP64
+  // for the remaining steps once a step contracts the change by less than 20x
+  // (FP32 rounding of A perturbs the preconditioned operator by ~u32 kappa(A)).
+  if (p->X32 != nullptr) nsteps = std::max(nsteps, 6);
   if (nsteps <= 0 || p->rank == 0) return LSRN_OK;
   p->pass_f32 = p->X32 != nullptr;
+  double prev_change = 1.0;
   const int64_t r = p->rank, q = p->q;
   double sL, sU;
   if (thm45_bounds(p, &sL, &sU) != LSRN_OK) return LSRN_OK;   // no bounds: skip refinement
@@ -708,6 +712,8 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
     *inner += steps;
     *taken += 1;
     if (change <= 1e-12) break;
+    if (p->pass_f32 && change > prev_change / 20.0) p->pass_f32 = false;
+    prev_change = change;
   }
   p->pass_f32 = false;
   return LSRN_OK;
