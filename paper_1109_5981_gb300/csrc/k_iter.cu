@@ -123,24 +123,30 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const T* __restrict_
   double ss = 0.0;
   const int64_t step = (int64_t)gridDim.x * GPC * R;
   int buf = 0;
-  for (int64_t base = (int64_t)blockIdx.x * GPC * R; base < rows; base += step) {
-    T a[R][SLOTS][2];
+  // rows of the next step are loaded while the current ones are reduced and
+  // accumulated (register double buffering keeps HBM requests in flight)
+  auto load_rows = [&](T (&dst)[R][SLOTS][2], int64_t b) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int64_t i = base + gid * R + r;
+      const int64_t i = b + gid * R + r;
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int c = 2 * gl + 2 * TPR * s;
         if (i < rows && c + 1 < C) {
-          load_pair<T>(X + i * ldx + c, a[r][s][0], a[r][s][1]);
+          load_pair<T>(X + i * ldx + c, dst[r][s][0], dst[r][s][1]);
         } else if (i < rows && c < C) {
-          a[r][s][0] = X[i * ldx + c];
-          a[r][s][1] = (T)0;
+          dst[r][s][0] = X[i * ldx + c];
+          dst[r][s][1] = (T)0;
         } else {
-          a[r][s][0] = a[r][s][1] = (T)0;
+          dst[r][s][0] = dst[r][s][1] = (T)0;
         }
       }
     }
+  };
+  T a[R][SLOTS][2], an[R][SLOTS][2];
+  load_rows(a, (int64_t)blockIdx.x * GPC * R);
+  for (int64_t base = (int64_t)blockIdx.x * GPC * R; base < rows; base += step) {
+    load_rows(an, base + step);
     // row state, read by every thread of the group before the barrier below;
     // the group's writer updates it only after that barrier
     double s0v[R], s1v[R];
@@ -198,6 +204,13 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const T* __restrict_
         acc[s][1] = fma(tc, a[r][s][1], acc[s][1]);
       }
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        a[r][s][0] = an[r][s][0];
+        a[r][s][1] = an[r][s][1];
+      }
   }
   // combine the groups of this CTA and write the CTA's partial vector
   double* out = pvec + (int64_t)blockIdx.x * C;
