@@ -246,6 +246,193 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const T* __restrict_
   }
 }
 
+// ---- staged variant for wide rows ------------------------------------------
+// One persistent CTA per SM streams blocks of RB rows of X through a ring of
+// shared-memory stages filled by bulk asynchronous copies (cp.async.bulk with
+// mbarrier transaction counts), so ~150 KB per SM are in flight while earlier
+// stages are reduced and accumulated.  The rows' LSQR/CS state (st0, st1)
+// travels with them.  Same arithmetic and outputs as row_pass_kernel.
+constexpr int kMaxStages = 8;
+constexpr long long kPassSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t sm_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool bar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(sm_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kPassSpinLimit; ++it)
+    if (bar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          sm_u32(dst)),
+      "l"(src), "r"(bytes), "r"(sm_u32(bar))
+      : "memory");
+}
+
+template <class T, int SLOTS, int RB>
+__global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
+    const T* __restrict__ X, int64_t rows, int C, int64_t ldx, const double* __restrict__ vin,
+    RowArgs args, double* __restrict__ pvec, double* __restrict__ pscal, const int* __restrict__ done,
+    int* __restrict__ err, int rowbytes, int nstages) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ double red[2][kThreads / 32][RB];
+  __shared__ double sred[kThreads / 32];
+  const int tid = threadIdx.x;
+  const bool need_dot = args.mode != RM_ACC_STATE;
+  const bool reads0 = mode_reads_st0(args.mode);
+  const bool reads1 = args.mode == RM_FAT_CS;
+  const int stage_bytes = RB * rowbytes;
+  double* state = (double*)(smem + (size_t)nstages * stage_bytes);   // [nstages][2][RB]
+  Coef k{0.0, 0.0};
+  if (args.coef) {
+    k.c0 = args.coef[0];
+    k.c1 = args.coef[1];
+  }
+  T w[SLOTS][2], acc[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int c = 2 * tid + 2 * kThreads * s;
+    w[s][0] = (need_dot && c < C) ? (T)vin[c] : (T)0;
+    w[s][1] = (need_dot && c + 1 < C) ? (T)vin[c + 1] : (T)0;
+    acc[s][0] = acc[s][1] = (T)0;
+  }
+  const int64_t nrb = (rows + RB - 1) / RB;
+  const int64_t my_n = blockIdx.x < nrb ? (nrb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (tid == 0) {
+    for (int st = 0; st < nstages; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&bars[st])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t kk) {
+    if (tid != 0 || kk >= my_n) return;
+    const int st = (int)(kk % nstages);
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    const int nr = (int)min((int64_t)RB, rows - r0);
+    const uint32_t sbytes = (uint32_t)(((nr * 8) + 15) / 16 * 16);
+    uint32_t bytes = (uint32_t)nr * rowbytes + (reads0 ? sbytes : 0u) + (reads1 ? sbytes : 0u);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_u32(&bars[st])),
+                 "r"(bytes)
+                 : "memory");
+    unsigned char* dst = smem + (size_t)st * stage_bytes;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before async writes
+    for (int r = 0; r < nr; ++r)
+      bulk_copy(dst + (size_t)r * rowbytes, X + (r0 + r) * ldx, (uint32_t)rowbytes, &bars[st]);
+    if (reads0) bulk_copy(state + (size_t)st * 2 * RB, args.st0 + r0, sbytes, &bars[st]);
+    if (reads1) bulk_copy(state + (size_t)st * 2 * RB + RB, args.st1 + r0, sbytes, &bars[st]);
+  };
+  for (int kk = 0; kk < nstages - 1; ++kk) issue(kk);
+  double ss = 0.0;
+  int buf = 0;
+  bool ok = true;
+  int64_t kk = 0;
+  for (; kk < my_n; ++kk) {
+    issue(kk + nstages - 1);
+    const int st = (int)(kk % nstages);
+    if (!bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1))) {
+      ok = false;
+      break;
+    }
+    const T* rowp = (const T*)(smem + (size_t)st * stage_bytes);
+    const double* sst = state + (size_t)st * 2 * RB;
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    double d[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      T t = (T)0;
+      if (need_dot) {
+        const T* row = rowp + (size_t)r * (rowbytes / sizeof(T));
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int c = 2 * tid + 2 * kThreads * s;
+          if (c < C) {
+            T x0, x1;
+            load_pair<T>(row + c, x0, x1);
+            if (c + 1 >= C) x1 = (T)0;
+            t = fma(x0, w[s][0], fma(x1, w[s][1], t));
+          }
+        }
+      }
+      d[r] = (double)t;
+    }
+    if (need_dot) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) d[r] = group_sum<32>(d[r]);
+      if ((tid & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) red[buf][tid >> 5][r] = d[r];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        double t = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) t += red[buf][q][r];
+        d[r] = t;
+      }
+      buf ^= 1;
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t i = r0 + r;
+      if (i >= rows) continue;
+      double ss_dummy = 0.0;
+      const double s0 = reads0 ? sst[r] : 0.0;
+      const double s1 = reads1 ? sst[RB + r] : 0.0;
+      const double tacc = row_coef(args, k, i, d[r], s0, s1, tid == 0, tid == 0 ? ss : ss_dummy);
+      const T tc = (T)tacc;
+      const T* row = rowp + (size_t)r * (rowbytes / sizeof(T));
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int c = 2 * tid + 2 * kThreads * s;
+        if (c < C) {
+          T x0, x1;
+          load_pair<T>(row + c, x0, x1);
+          if (c + 1 >= C) x1 = (T)0;
+          acc[s][0] = fma(tc, x0, acc[s][0]);
+          acc[s][1] = fma(tc, x1, acc[s][1]);
+        }
+      }
+    }
+    __syncthreads();   // stage st is free again
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // let copies already issued land before the CTA exits
+    for (int64_t q = kk; q < my_n && q < kk + nstages - 1; ++q)
+      bar_wait(&bars[q % nstages], (uint32_t)((q / nstages) & 1));
+  }
+  double* out = pvec + (int64_t)blockIdx.x * C;
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int c = 2 * tid + 2 * kThreads * s;
+    if (c < C) out[c] = (double)acc[s][0];
+    if (c + 1 < C) out[c + 1] = (double)acc[s][1];
+  }
+  ss = group_sum<32>(ss);
+  if ((tid & 31) == 0) sred[tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += sred[q];
+    pscal[blockIdx.x] = t;
+  }
+}
+
 // Rows appended to X by the Tikhonov augmentation: row (xrows + j) = coef * e_j.
 // Writes one extra partial slot (vector of length C and one scalar).
 __global__ void extra_rows_kernel(int64_t nextra, int64_t xrows, int C, double coef,
@@ -510,6 +697,8 @@ lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t l
   return LSRN_OK;
 }
 
+bool pass_is_staged(int64_t C);
+
 static int pick_layout(int64_t C, int* tpr, int* slots) {
   if (C <= 64) { *tpr = 32; *slots = 1; }
   else if (C <= 128) { *tpr = 32; *slots = 2; }
@@ -525,10 +714,48 @@ static int pick_layout(int64_t C, int* tpr, int* slots) {
 int pass_blocks(int64_t rows, int64_t C) {
   int tpr, slots;
   if (pick_layout(C, &tpr, &slots) != 0) return 0;
+  if (pass_is_staged(C)) return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), rows));
   const int64_t gpc = kThreads / tpr;
   const int64_t per = gpc * 2;
   const int64_t want = (rows + per - 1) / per;
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * num_sms()));
+}
+
+// Staged pass geometry for element size esz: rows per stage and stage count,
+// or false when the staged kernel does not apply.
+static bool staged_geometry(int64_t C, int64_t ldx, size_t esz, int* rowbytes, int* rb,
+                            int* nstages) {
+  if (C <= 512 || C > 4096) return false;
+  const int64_t rbytes = (C * (int64_t)esz + 15) / 16 * 16;
+  if (rbytes > ldx * (int64_t)esz || (ldx * (int64_t)esz) % 16 != 0) return false;
+  int r = (int)std::max<int64_t>(2, (32768 / rbytes) / 2 * 2);
+  r = std::min(r, 8);
+  if (r != 2 && r != 4 && r != 8) r = r >= 8 ? 8 : (r >= 4 ? 4 : 2);
+  int ns = (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / (r * rbytes + 2 * r * 8));
+  if (ns < 2) return false;
+  *rowbytes = (int)rbytes;
+  *rb = r;
+  *nstages = ns;
+  return true;
+}
+
+bool pass_is_staged(int64_t C) { return C > 512 && C <= 4096; }
+
+template <class T, int SLOTS, int RB>
+static lsrn_status launch_staged(const Plan* p, const T* X, int64_t ldx, const double* vin,
+                                 const RowArgs& a, double* pvec, double* pscal, const int* done,
+                                 int rowbytes, int nstages) {
+  const size_t smem = (size_t)nstages * RB * rowbytes + (size_t)nstages * 2 * RB * sizeof(double);
+  auto kern = row_pass_staged_kernel<T, SLOTS, RB>;
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    LSRN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured = true;
+  }
+  launch(kern, dim3(p->nblk), dim3(kThreads), smem, p->stream, X, p->xrows, (int)p->xcols, ldx, vin,
+         a, pvec, pscal, done, p->iscal + IC_PASSERR, rowbytes, nstages);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
 }
 
 lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
@@ -536,6 +763,19 @@ lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, 
   int tpr, slots;
   if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
   const int C = (int)p->xcols;
+  int rowbytes = 0, rb = 0, ns = 0;
+  if (p->pass_f32 && staged_geometry(C, p->ldx32, sizeof(float), &rowbytes, &rb, &ns)) {
+    const float* xp = p->X32;
+    if (slots == 2 && rb == 8) return launch_staged<float, 2, 8>(p, xp, p->ldx32, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 4 && rb == 4) return launch_staged<float, 4, 4>(p, xp, p->ldx32, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 8 && rb == 2) return launch_staged<float, 8, 2>(p, xp, p->ldx32, vin, a, pvec, pscal, done, rowbytes, ns);
+  }
+  if (!p->pass_f32 && staged_geometry(C, p->ldx, sizeof(double), &rowbytes, &rb, &ns)) {
+    const double* xp = p->X;
+    if (slots == 2 && rb == 4) return launch_staged<double, 2, 4>(p, xp, p->ldx, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 4 && rb == 2) return launch_staged<double, 4, 2>(p, xp, p->ldx, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 8 && rb == 2) return launch_staged<double, 8, 2>(p, xp, p->ldx, vin, a, pvec, pscal, done, rowbytes, ns);
+  }
   dim3 grid(p->nblk);
 #define LSRN_ROWPASS(E, T, S, R)                                                        \
   launch(row_pass_kernel<E, T, S, R>, grid, kThreads, 0, p->stream, (const E*)xp, p->xrows, C, \

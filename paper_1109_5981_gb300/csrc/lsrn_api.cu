@@ -154,8 +154,9 @@ static lsrn_status plan_workspace(Plan* p) {
   LSRN_TRY(dalloc_n(p, &p->NT, q * q));
   LSRN_TRY(dalloc_n(p, &p->scal, (int64_t)SC_COUNT));
   LSRN_TRY(dalloc_n(p, &p->iscal, (int64_t)IC_COUNT));
-  LSRN_TRY(dalloc_n(p, &p->st0, p->nstate));
-  LSRN_TRY(dalloc_n(p, &p->st1, p->nstate));
+  // +2: the staged pass copies row state in 16-byte units
+  LSRN_TRY(dalloc_n(p, &p->st0, p->nstate + 2));
+  LSRN_TRY(dalloc_n(p, &p->st1, p->nstate + 2));
   LSRN_TRY(dalloc_n(p, &p->vq, q));
   LSRN_TRY(dalloc_n(p, &p->vq2, q));
   LSRN_TRY(dalloc_n(p, &p->tmpq, q));
@@ -485,7 +486,11 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   }
   if (!xdev)
     LSRN_CUDA_TRY(cudaMemcpyAsync(x, xout, p->n * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  int passerr = 0;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(&passerr, p->iscal + IC_PASSERR, sizeof(int),
+                                cudaMemcpyDeviceToHost, p->stream));
   LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  if (passerr) result = LSRN_ERR_TIMEOUT;   // a bounded wait of a staged pass gave up
   inf.status = result;
   if (info) *info = inf;
   return result;

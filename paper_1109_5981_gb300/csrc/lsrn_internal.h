@@ -56,7 +56,7 @@ enum ScalarSlot : int {
   SC_COUNT = 32
 };
 
-enum IntSlot : int { IC_DONE = 0, IC_ITN, IC_ISTOP, IC_CAP, IC_ROT, IC_TCERR, IC_COUNT = 8 };
+enum IntSlot : int { IC_DONE = 0, IC_ITN, IC_ISTOP, IC_CAP, IC_ROT, IC_TCERR, IC_PASSERR, IC_COUNT = 8 };
 
 // Row modes of the fused pass over the rows of X (see k_iter.cu).
 enum RowMode : int {
