@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   __shared__ double red[2][kThreads / 32][RB];
+  __shared__ double tco[2][RB];
   __shared__ double sred[kThreads / 32];
   const int tid = threadIdx.x;
   const bool need_dot = args.mode != RM_ACC_STATE;
@@ -351,7 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
     const T* rowp = (const T*)(smem + (size_t)st * stage_bytes);
     const double* sst = state + (size_t)st * 2 * RB;
     const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
-    double d[RB];
+    // dot products: per-thread partials in T, warp sums in T, cross-warp sum and
+    // the row's LSQR/CS update by one thread per row (FP64), broadcast via smem
+    T dp[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       T t = (T)0;
@@ -367,34 +370,34 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
             t = fma(x0, w[s][0], fma(x1, w[s][1], t));
           }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       }
-      d[r] = (double)t;
+      dp[r] = t;
     }
-    if (need_dot) {
+    if ((tid & 31) == 0) {
 #pragma unroll
-      for (int r = 0; r < RB; ++r) d[r] = group_sum<32>(d[r]);
-      if ((tid & 31) == 0) {
-#pragma unroll
-        for (int r = 0; r < RB; ++r) red[buf][tid >> 5][r] = d[r];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        double t = 0.0;
-        for (int q = 0; q < kThreads / 32; ++q) t += red[buf][q][r];
-        d[r] = t;
-      }
-      buf ^= 1;
+      for (int r = 0; r < RB; ++r) red[buf][tid >> 5][r] = (double)dp[r];
     }
+    __syncthreads();
+    if (tid < RB) {
+      const int r = tid;
+      const int64_t i = r0 + r;
+      double tacc = 0.0;
+      if (i < rows) {
+        double d = 0.0;
+        if (need_dot)
+          for (int q = 0; q < kThreads / 32; ++q) d += red[buf][q][r];
+        const double s0 = reads0 ? sst[r] : 0.0;
+        const double s1 = reads1 ? sst[RB + r] : 0.0;
+        tacc = row_coef(args, k, i, d, s0, s1, true, ss);
+      }
+      tco[buf][r] = tacc;
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const int64_t i = r0 + r;
-      if (i >= rows) continue;
-      double ss_dummy = 0.0;
-      const double s0 = reads0 ? sst[r] : 0.0;
-      const double s1 = reads1 ? sst[RB + r] : 0.0;
-      const double tacc = row_coef(args, k, i, d[r], s0, s1, tid == 0, tid == 0 ? ss : ss_dummy);
-      const T tc = (T)tacc;
+      const T tc = (T)tco[buf][r];
       const T* row = rowp + (size_t)r * (rowbytes / sizeof(T));
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
@@ -408,6 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
         }
       }
     }
+    buf ^= 1;
     __syncthreads();   // stage st is free again
   }
   if (!ok) {
