@@ -287,7 +287,8 @@ def lsrn_precond(plan: Plan) -> int:
 def _solve(fn_name: str, plan: Plan, b, x=None, allow=(LSRN_OK,)):
     lib = load_library()
     if x is None:
-        x = np.empty(plan.n, dtype=np.float64) if isinstance(b, np.ndarray) else b.new_empty(plan.n)
+        x = (np.empty(plan.n, dtype=np.float64) if isinstance(b, np.ndarray)
+             else b.new_empty(plan.n))
     info = lsrn_info()
     st = getattr(lib, fn_name)(plan.handle, _ptr(b), _ptr(x), ctypes.byref(info))
     _check(st, fn_name, allow)

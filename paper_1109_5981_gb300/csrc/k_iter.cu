@@ -817,9 +817,43 @@ lsrn_status launch_extra_rows(const Plan* p, const double* vin, const RowArgs& a
   return LSRN_OK;
 }
 
+namespace {
+__global__ void add_vec_kernel(double* __restrict__ out, const double* __restrict__ v, int64_t n,
+                               const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += v[i];
+}
+}  // namespace
+
+// Ridge rows for the sparse passes: their contribution is added into out.
+lsrn_status launch_row_coef_extra(const Plan* p, const double* vin, const RowArgs& a, double* out,
+                                  double* pscal_slot, const int* done) {
+  launch(extra_rows_kernel, 1, 1024, 0, p->stream, p->extra_rows, p->xrows, (int)p->xcols,
+         p->extra_coef, vin, a, p->pvec, pscal_slot, done);
+  launch(add_vec_kernel, dim3((unsigned)((p->xcols + 255) / 256)), dim3(256), 0, p->stream, out,
+         (const double*)p->pvec, p->xcols, done);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status csr_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
+                        double* phi, double* plo, double* tbuf);
+
 lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
                            double* pvec_hi, double* pvec_lo, const int* done) {
   (void)done;
+  if (p->csr) {
+    LSRN_TRY(csr_dd_pass(p, vin, bvec, rout, pvec_hi, pvec_lo, p->tcsr));
+    if (p->extra_rows > 0) {
+      const int C = (int)p->xcols;
+      launch(dd_extra_kernel, dim3((unsigned)((p->xcols + 255) / 256)), dim3(256), 0, p->stream,
+             p->extra_rows, p->xrows, C, p->extra_coef, vin, bvec != nullptr, rout,
+             pvec_hi + (int64_t)p->nblk * C, pvec_lo + (int64_t)p->nblk * C);
+    }
+    LSRN_CUDA_TRY(cudaGetLastError());
+    return LSRN_OK;
+  }
   int tpr, slots;
   if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
   const int C = (int)p->xcols;

@@ -409,6 +409,7 @@ static lsrn_status fill(Plan* p, double* v, int64_t n, double val) {
 // One fused pass (+ ridge rows) and its reduction into out (C) and scal[SC_SS].
 static lsrn_status fused_pass(Plan* p, const double* vin, const RowArgs& a, double* out,
                               const int* done) {
+  if (p->csr) return csr_fused_pass(p, vin, a, out, p->tcsr, p->scal + SC_SS, done);
   if (p->time_passes) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -531,9 +532,8 @@ lsrn_status run_lsqr(Plan* p, int* iters, int* istop) {
     LSRN_TRY(fill(p, p->st0 + p->m, p->nstate - p->m, 0.0));
     LSRN_TRY(sumsq(p, p->bdev, p->m, p->scal + SC_SS));
     RowArgs a0{RM_ACC_STATE, p->st0, nullptr, nullptr, 1.0};
-    LSRN_TRY(launch_row_pass(p, nullptr, a0, p->pvec, p->pscal, nullptr));
-    LSRN_TRY(launch_extra_rows(p, nullptr, a0, p->pvec, p->pscal, nullptr));
-    LSRN_TRY(launch_reduce(p->pvec, p->nblk + (p->extra_rows ? 1 : 0), q, p->vq, p->pscal, nullptr, nullptr, p->stream));
+    LSRN_TRY(fused_pass(p, nullptr, a0, p->vq, nullptr));
+    LSRN_TRY(sumsq(p, p->bdev, p->m, p->scal + SC_SS));   // the pass overwrote SC_SS
     LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, tmpr, nullptr, nullptr, c100(p), nullptr, p->stream));
     launch(lsqr_tall_init_kernel, 1, kCtl, 0, p->stream, p->scal, p->iscal, tmpr, v, w, y, r);
     LSRN_CUDA_TRY(cudaGetLastError());

@@ -143,7 +143,7 @@ static lsrn_status validate_options(const lsrn_options& o) {
 
 static lsrn_status plan_workspace(Plan* p) {
   const int64_t q = p->q, s = p->s;
-  p->nblk = pass_blocks(p->xrows, p->xcols);
+  p->nblk = p->csr ? 1 : pass_blocks(p->xrows, p->xcols);   // sparse passes write whole vectors
   if (p->nblk <= 0) return LSRN_ERR_UNSUPPORTED;
   LSRN_TRY(dalloc_n(p, &p->Xs, s * q));
   LSRN_TRY(dalloc_n(p, &p->Wj, q * q));
@@ -165,7 +165,8 @@ static lsrn_status plan_workspace(Plan* p) {
   LSRN_TRY(dalloc_n(p, &p->bdev, std::max<int64_t>(p->m, 1)));
   LSRN_TRY(dalloc_n(p, &p->pvec, (int64_t)(p->nblk + 1) * p->xcols));
   LSRN_TRY(dalloc_n(p, &p->pvec2, (int64_t)(p->nblk + 1) * p->xcols));
-  LSRN_TRY(dalloc_n(p, &p->pscal, std::max<int64_t>(p->nblk + 1, 4 * (int64_t)num_sms())));
+  LSRN_TRY(dalloc_n(p, &p->pscal, std::max<int64_t>(p->nblk + 1, 8 * (int64_t)num_sms() + 2)));
+  if (p->csr) LSRN_TRY(dalloc_n(p, &p->tcsr, p->xrows));
   LSRN_CUDA_TRY(cudaMemsetAsync(p->scal, 0, SC_COUNT * sizeof(double), p->stream));
   LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal, 0, IC_COUNT * sizeof(int), p->stream));
   const double one = 1.0;

@@ -105,6 +105,7 @@ struct Plan {
   const int64_t* rp = nullptr;  const int32_t* ci = nullptr;  const double* cv = nullptr;   // rows of X
   const int64_t* rpT = nullptr; const int32_t* ciT = nullptr; const double* cvT = nullptr;  // columns of X
   int64_t nnz = 0;
+  double* tcsr = nullptr;           // row coefficients between the two sparse passes (xrows)
   std::vector<void*> owned;         // device buffers freed at destroy
 
   // sketch and preconditioner
@@ -207,8 +208,8 @@ lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t l
 lsrn_status launch_gemv_dd(const double* M, int64_t R, int64_t C, const double* v, double* out,
                            cudaStream_t st);
 // CSR pass: t = Xrow . vin per row, epilogue as RowArgs; then the transpose product
-lsrn_status launch_csr_rowdot(const Plan* p, const double* vin, const RowArgs& a, double* tout,
-                              double* pscal, const int* done);
-lsrn_status launch_csr_coldot(const Plan* p, const double* t, double* out, const int* done);
+// Sparse fused pass: out (xcols) = X^T t, t from the row pass (+ ridge rows); ss -> *scal_ss
+lsrn_status csr_fused_pass(const Plan* p, const double* vin, const RowArgs& a, double* out,
+                           double* tbuf, double* scal_ss, const int* done);
 
 }  // namespace lsrn
