@@ -257,8 +257,14 @@ lsrn_status lsrn_sketch_f64_noalloc(const double* A, int64_t m, int64_t n, int64
  *   hbm_budget_bytes  device bytes that admitted requests may hold at once.
  *   max_slots         requests that may run concurrently (>= 1).
  *   solver            0 = LSQR, 1 = CS.
- * QUEUE_FULL when a single request alone exceeds the budget.  The server is
- * thread-safe.  lsrn_server_destroy waits for running requests. */
+ * A request is admitted when a slot is free and its estimated device footprint
+ * (the copy of A, the sketch, the factors, the vectors, the tensor-core
+ * scratch) fits what the running requests leave of the budget; the oldest
+ * queued request that fits goes first.  Each slot has its own worker thread
+ * and non-blocking stream on the device current at lsrn_server_create.
+ * QUEUE_FULL when a single request alone exceeds the budget; INVALID_ARG for
+ * an unknown or already collected ticket.  The server is thread-safe.
+ * lsrn_server_destroy waits for running requests and drops queued ones. */
 lsrn_status lsrn_server_create(size_t hbm_budget_bytes, int32_t max_slots, lsrn_server_t* out);
 lsrn_status lsrn_submit(lsrn_server_t s, const lsrn_matrix* A, const double* b,
                         const lsrn_options* opt, int32_t solver, uint64_t* ticket);

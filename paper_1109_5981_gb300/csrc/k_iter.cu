@@ -751,11 +751,8 @@ static lsrn_status launch_staged(const Plan* p, const T* X, int64_t ldx, const d
                                  int rowbytes, int nstages) {
   const size_t smem = (size_t)nstages * RB * rowbytes + (size_t)nstages * 2 * RB * sizeof(double);
   auto kern = row_pass_staged_kernel<T, SLOTS, RB>;
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    LSRN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
+  // per launch: the attribute is per device, and server threads may share a device
+  LSRN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   launch(kern, dim3(p->nblk), dim3(kThreads), smem, p->stream, X, p->xrows, (int)p->xcols, ldx, vin,
          a, pvec, pscal, done, p->iscal + IC_PASSERR, rowbytes, nstages);
   LSRN_CUDA_TRY(cudaGetLastError());

@@ -425,12 +425,8 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
   const int64_t Sp = (S + TC_M - 1) / TC_M * TC_M;
   const int64_t Lp = (seg_rows + TC_KT - 1) / TC_KT * TC_KT;
   if (scratch_bytes < sketch_tc_scratch_bytes(seg_rows, Q, S)) return LSRN_ERR_INVALID_ARG;
-  static bool attr_set = false;
-  if (!attr_set) {
-    LSRN_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    attr_set = true;
-  }
+  LSRN_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   uint16_t* Gh = (uint16_t*)scratch;
   uint16_t* Gl = Gh + Sp * Lp;
   uint16_t* D = Gl + Sp * Lp;

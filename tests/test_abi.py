@@ -62,3 +62,16 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(L.LsrnError) as e:
         L.solve(np.ones((20, 4)), np.ones(20))
     assert e.value.status in (L.LSRN_ERR_CUDA,)
+
+
+def test_server_needs_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1109_5981_gb300 as L
+    with pytest.raises(L.LsrnError) as e:
+        L.lsrn_server_create(1 << 30, 2)
+    assert e.value.status == L.LSRN_ERR_CUDA
+    with pytest.raises(L.LsrnError) as e:
+        L.lsrn_server_create(0, 2)
+    assert e.value.status == L.LSRN_ERR_INVALID_ARG

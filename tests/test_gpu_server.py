@@ -1,0 +1,176 @@
+"""GPU tests of the serving boundary (lsrn_server_create / lsrn_submit /
+lsrn_poll / lsrn_server_destroy): admitted requests run concurrently on their
+own streams, and each result equals what a direct plan + solve of the same
+request gives, bit for bit, and the oracle's minimum-length solution within
+the parity tolerance."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+L = pytest.importorskip("paper_1109_5981_gb300")
+
+GiB = 1 << 30
+
+
+def _wait(srv, ticket, x, limit_s=120.0):
+    t0 = time.monotonic()
+    while True:
+        st, info = L.lsrn_poll(srv, ticket, x)
+        if st != L.LSRN_PENDING:
+            return st, info
+        assert time.monotonic() - t0 < limit_s, "request did not finish"
+        time.sleep(0.002)
+
+
+def _requests():
+    """A mix of tall/fat dense, CSR, LSQR/CS and ridge requests."""
+    out = []
+    for k, (m, n) in enumerate([(3000, 120), (150, 2500), (2500, 90), (4000, 200)]):
+        P = W.dense_householder(m, n, rank=min(m, n) - 5, cond=1e4, noise=1e-3, seed=30 + k)
+        out.append(dict(A=torch.from_numpy(P.A), b=torch.from_numpy(P.b), solver=k % 2,
+                        opt=dict(seed=7 + k), dense=P.A, bnp=P.b, csr=None))
+    C = W.csr_random_density(3000, 80, 0.05, seed=41)
+    bc = np.random.Generator(np.random.PCG64(42)).standard_normal(3000)
+    out.append(dict(A=None, b=torch.from_numpy(bc), solver=0, opt=dict(seed=3), dense=C.to_dense(),
+                    bnp=bc, csr=(C.m, C.n, torch.from_numpy(C.row_ptr), torch.from_numpy(C.col_idx),
+                                 torch.from_numpy(C.values))))
+    P = W.dense_householder(2000, 60, rank=60, cond=1e3, noise=1e-2, seed=50)
+    out.append(dict(A=torch.from_numpy(P.A), b=torch.from_numpy(P.b), solver=1,
+                    opt=dict(seed=9, lambda_=0.3), dense=P.A, bnp=P.b, csr=None, lam=0.3))
+    return out
+
+
+def _direct(r):
+    solver = "cs" if r["solver"] == 1 else "lsqr"
+    x, _ = L.solve(r["A"], r["b"], solver=solver, csr=r["csr"], **r["opt"])
+    return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+
+def _expected(r):
+    lam = r.get("lam", 0.0)
+    if lam > 0:
+        return O.ridge_closed_form(r["dense"], r["bnp"], lam)
+    return O.minlen_svd(r["dense"], r["bnp"])
+
+
+def test_server_results_match_direct_solves_and_oracle():
+    reqs = _requests()
+    srv = L.lsrn_server_create(64 * GiB, max_slots=3)
+    try:
+        tickets = [L.lsrn_submit(srv, r["A"], r["b"], L.default_options(**r["opt"]), r["solver"],
+                                 csr=r["csr"]) for r in reqs]
+        assert len(set(tickets)) == len(tickets)
+        outs = []
+        for r, t in zip(reqs, tickets):
+            x = np.zeros(r["dense"].shape[1])
+            st, info = _wait(srv, t, x)
+            assert st == L.LSRN_OK, L.status_string(st)
+            assert info["n"] == r["dense"].shape[1]
+            outs.append(x)
+    finally:
+        L.lsrn_server_destroy(srv)
+    for r, x in zip(reqs, outs):
+        assert np.array_equal(x, _direct(r)), "server result differs from a direct solve"
+        assert O.rel_err(x, _expected(r)) <= 1e-10
+
+
+def test_budget_for_one_request_still_serves_all():
+    # each of these requests is estimated at ~65-80 MiB (64 MiB of it a fixed
+    # allowance), so a 100 MiB budget admits one at a time: the queue drains in order
+    reqs = _requests()[:3]
+    srv = L.lsrn_server_create(100 << 20, max_slots=4)
+    try:
+        tickets = [L.lsrn_submit(srv, r["A"], r["b"], L.default_options(**r["opt"]), r["solver"])
+                   for r in reqs]
+        for r, t in zip(reqs, tickets):
+            x = np.zeros(r["dense"].shape[1])
+            st, _ = _wait(srv, t, x)
+            assert st == L.LSRN_OK
+            assert np.array_equal(x, _direct(r))
+    finally:
+        L.lsrn_server_destroy(srv)
+
+
+def test_oversize_request_and_bad_tickets_are_rejected():
+    r = _requests()[0]
+    srv = L.lsrn_server_create(1 << 20, max_slots=1)   # 1 MiB: nothing fits
+    try:
+        with pytest.raises(L.LsrnError) as e:
+            L.lsrn_submit(srv, r["A"], r["b"], None, 0)
+        assert e.value.status == L.LSRN_ERR_QUEUE_FULL
+        st, _ = L.lsrn_poll(srv, 12345, None)
+        assert st == L.LSRN_ERR_INVALID_ARG
+    finally:
+        L.lsrn_server_destroy(srv)
+    srv = L.lsrn_server_create(64 * GiB, max_slots=1)
+    try:
+        t = L.lsrn_submit(srv, r["A"], r["b"], None, 0)
+        x = np.zeros(r["dense"].shape[1])
+        assert _wait(srv, t, x)[0] == L.LSRN_OK
+        assert L.lsrn_poll(srv, t, x)[0] == L.LSRN_ERR_INVALID_ARG   # already collected
+        with pytest.raises(L.LsrnError) as e:
+            L.lsrn_submit(srv, r["A"], r["b"], None, 7)                # no such solver
+        assert e.value.status == L.LSRN_ERR_INVALID_ARG
+    finally:
+        L.lsrn_server_destroy(srv)
+
+
+def test_invalid_request_reports_its_status():
+    # gamma <= 1 passes submission and fails in the worker's lsrn_plan
+    r = _requests()[0]
+    srv = L.lsrn_server_create(64 * GiB, max_slots=2)
+    try:
+        t = L.lsrn_submit(srv, r["A"], r["b"], L.default_options(gamma=1.0), 0)
+        st, _ = _wait(srv, t, None)
+        assert st == L.LSRN_ERR_INVALID_ARG
+    finally:
+        L.lsrn_server_destroy(srv)
+
+
+def test_concurrent_submitters():
+    reqs = _requests()[:4]
+    srv = L.lsrn_server_create(64 * GiB, max_slots=4)
+    results, errors = {}, []
+
+    def client(i):
+        try:
+            r = reqs[i]
+            for rep in range(2):
+                t = L.lsrn_submit(srv, r["A"], r["b"], L.default_options(**r["opt"]), r["solver"])
+                x = np.zeros(r["dense"].shape[1])
+                st, _ = _wait(srv, t, x)
+                assert st == L.LSRN_OK
+                results[(i, rep)] = x
+        except Exception as exc:   # reported on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=client, args=(i,)) for i in range(4)]
+    try:
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(300)
+    finally:
+        L.lsrn_server_destroy(srv)
+    assert not errors, errors
+    for i in range(4):
+        assert np.array_equal(results[(i, 0)], results[(i, 1)])
+        assert np.array_equal(results[(i, 0)], _direct(reqs[i]))
+
+
+def test_destroy_with_queued_requests_returns():
+    reqs = _requests()
+    srv = L.lsrn_server_create(64 * GiB, max_slots=1)
+    for r in reqs:
+        L.lsrn_submit(srv, r["A"], r["b"], L.default_options(**r["opt"]), r["solver"], csr=r["csr"])
+    t0 = time.monotonic()
+    L.lsrn_server_destroy(srv)
+    assert time.monotonic() - t0 < 60
