@@ -58,7 +58,9 @@ def _expected(r):
     lam = r.get("lam", 0.0)
     if lam > 0:
         return O.ridge_closed_form(r["dense"], r["bnp"], lam)
-    return O.minlen_svd(r["dense"], r["bnp"])
+    # the refined x*: with a nonzero residual the plain FP64 SVD solution is
+    # itself ~1e-10 away from x* at cond 1e4 (its error grows like cond^2 * |r|)
+    return O.minlen_refined(r["dense"], r["bnp"])[0]
 
 
 def test_server_results_match_direct_solves_and_oracle():
