@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solver", default="lsqr", choices=["lsqr", "cs"])
     ap.add_argument("--sketch", default="tc", choices=["f64", "tc"])
-    ap.add_argument("--iter", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--iter", default="f64", choices=["f64", "f32", "x2"])
     ap.add_argument("--m", type=int, default=M)
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--rank", type=int, default=RANK)
@@ -239,7 +239,8 @@ def main():
     opts = L.default_options(seed=1234 + rank,
                              sketch_mode=L.LSRN_SKETCH_TC_SLICED if args.sketch == "tc"
                              else L.LSRN_SKETCH_F64,
-                             iter_mode=L.LSRN_ITER_F32 if args.iter == "f32" else L.LSRN_ITER_F64)
+                             iter_mode={"f32": L.LSRN_ITER_F32, "x2": L.LSRN_ITER_F32X2}.get(
+                                 args.iter, L.LSRN_ITER_F64))
     solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
 
     def step():
@@ -319,6 +320,14 @@ def main():
                         "frac": gbs / peak, "traffic": None,
                         "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
                         "work_per_launch": "4*m*n bytes (FP32 copy of A read once)"}
+        elif args.iter == "x2":
+            gbs = 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
+            peak = peaks.get("hbm_gbs", 6669.5)
+            roofline = {"kernel": "row_pass_x2_kernel (fused A(Nv) and A^T u, double-float planes)",
+                        "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "traffic": None,
+                        "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
+                        "work_per_launch": "8*m*n bytes (hi and lo FP32 planes of A read once)"}
         else:
             roofline = {"kernel": "row_pass_kernel (fused A(Nv) and A^T u, FP64)", "bound": "alu",
                       "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",

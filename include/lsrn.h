@@ -66,12 +66,21 @@ typedef enum { LSRN_F64 = 0, LSRN_F32 = 1 } lsrn_dtype;
 
 typedef enum {
   LSRN_ITER_F64 = 0,            /* every pass over A in FP64 */
-  LSRN_ITER_F32 = 1             /* m >= n: passes stream an FP32 copy of A (FP32 products); the
+  LSRN_ITER_F32 = 1,            /* m >= n: passes stream an FP32 copy of A (FP32 products); the
                                    sweep stops at max(tol, 1e-6) and double-double refinement
                                    against the FP64 A restores full accuracy.  x = N y stays in
                                    range(N) whatever the pass precision.  For m < n the option
                                    is ignored (FP64 passes): there x is iterated in R^n and
                                    FP32 rounding of A would add components in null(A). */
+  LSRN_ITER_F32X2 = 2           /* dense A whose short side q has 512 < q <= 4096 (other
+                                   shapes: FP64 passes): the plan keeps A / 2^e as two FP32
+                                   planes hi + lo (48 significant bits, 8 bytes per entry, e
+                                   the exponent of max |A_ij|) and every pass runs on the FP32
+                                   pipe with error-free products and double-float sums folded
+                                   into FP64 every 64 rows (relative error of each product and
+                                   sum ~2^-48, against 2^-53 in FP64).  Tall and fat; the
+                                   sweep keeps tol, and refinement stays double-double on the
+                                   FP64 A. */
 } lsrn_iter_mode;
 
 typedef enum {
@@ -168,7 +177,9 @@ lsrn_status lsrn_default_options(lsrn_options* opt);
  *           with lsrn_plan_destroy.
  * INVALID_ARG: m or n < 1, gamma <= 1, lambda < 0, tol <= 0, NULL data, bad ld,
  * CSR indices out of range or row_ptr not monotone (checked on the device).
- * OOM when the workspace does not fit.  Nothing is allocated on failure. */
+ * UNSUPPORTED: dense A with min(m, n) > 4096 (the fused pass keeps a whole row
+ * of X in registers / one shared-memory stage).  OOM when the workspace does
+ * not fit.  Nothing is allocated on failure. */
 lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
                       lsrn_plan_t* out);
 

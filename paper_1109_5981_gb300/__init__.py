@@ -36,7 +36,7 @@ LSRN_ERR_UNSUPPORTED = -9
 LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
 LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED = 0, 1
-LSRN_ITER_F64, LSRN_ITER_F32 = 0, 1
+LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2 = 0, 1, 2
 
 
 class lsrn_matrix(ctypes.Structure):

@@ -9,6 +9,7 @@
 // order by a second kernel, so results do not depend on scheduling.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "lsrn_device.cuh"
 #include "lsrn_internal.h"
@@ -437,6 +438,221 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
   }
 }
 
+// ---- double-float variant (iteration mode LSRN_ITER_F32X2) ------------------
+// X is held as two FP32 planes, Xh = fl32(X / xs) and Xl = fl32(X / xs - Xh)
+// with one power-of-two scale xs, so Xh + Xl carries 48 significant bits of
+// each element.  Every element operation runs on the FP32 pipe with
+// error-free transformations: the product of two (hi, lo) pairs is
+// TwoProd(hi, hi) plus the two cross terms, and sums are TwoSum into
+// (hi, lo) accumulators.  The column accumulators are folded into FP64 every
+// kFoldRows rows, which bounds the error of the lazy low words.  Only the
+// per-row LSQR/CS update (one thread per row) is FP64.  Same staging, row
+// modes and outputs as row_pass_staged_kernel.
+constexpr int kFoldRows = 64;
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) += (ah + al) * (bh + bl), dropping al * bl (below 2^-48 of the product)
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  float s, er;
+  two_sum_f(h, p, s, er);
+  h = s;
+  l += er + e;
+}
+__device__ __forceinline__ void split_df(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+template <int SLOTS, int RB>
+__global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
+    const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t rows, int C, int64_t ldx,
+    double xs, const double* __restrict__ vin, RowArgs args, double* __restrict__ pvec,
+    double* __restrict__ pscal, const int* __restrict__ done, int* __restrict__ err, int rowbytes,
+    int nstages) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ float redh[2][kThreads / 32][RB], redl[2][kThreads / 32][RB];
+  __shared__ float tch[2][RB], tcl[2][RB];
+  __shared__ double sred[kThreads / 32];
+  const int tid = threadIdx.x;
+  const bool need_dot = args.mode != RM_ACC_STATE;
+  const bool reads0 = mode_reads_st0(args.mode);
+  const bool reads1 = args.mode == RM_FAT_CS;
+  const int stage_bytes = 2 * RB * rowbytes;   // RB rows of Xh, then RB rows of Xl
+  double* state = (double*)(smem + (size_t)nstages * stage_bytes);   // [nstages][2][RB]
+  Coef k{0.0, 0.0};
+  if (args.coef) {
+    k.c0 = args.coef[0];
+    k.c1 = args.coef[1];
+  }
+  float vh[SLOTS][2], vl[SLOTS][2], wh[SLOTS][2], wl[SLOTS][2];
+  double wd[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int c = 2 * tid + 2 * kThreads * s + e;
+      split_df((need_dot && c < C) ? vin[c] : 0.0, vh[s][e], vl[s][e]);
+      wh[s][e] = wl[s][e] = 0.0f;
+      wd[s][e] = 0.0;
+    }
+  const int64_t nrb = (rows + RB - 1) / RB;
+  const int64_t my_n = blockIdx.x < nrb ? (nrb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (tid == 0) {
+    for (int st = 0; st < nstages; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&bars[st])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t kk) {
+    if (tid != 0 || kk >= my_n) return;
+    const int st = (int)(kk % nstages);
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    const int nr = (int)min((int64_t)RB, rows - r0);
+    const uint32_t sbytes = (uint32_t)(((nr * 8) + 15) / 16 * 16);
+    uint32_t bytes = 2u * (uint32_t)nr * rowbytes + (reads0 ? sbytes : 0u) + (reads1 ? sbytes : 0u);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_u32(&bars[st])),
+                 "r"(bytes)
+                 : "memory");
+    unsigned char* dst = smem + (size_t)st * stage_bytes;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int r = 0; r < nr; ++r) {
+      bulk_copy(dst + (size_t)r * rowbytes, Xh + (r0 + r) * ldx, (uint32_t)rowbytes, &bars[st]);
+      bulk_copy(dst + (size_t)(RB + r) * rowbytes, Xl + (r0 + r) * ldx, (uint32_t)rowbytes,
+                &bars[st]);
+    }
+    if (reads0) bulk_copy(state + (size_t)st * 2 * RB, args.st0 + r0, sbytes, &bars[st]);
+    if (reads1) bulk_copy(state + (size_t)st * 2 * RB + RB, args.st1 + r0, sbytes, &bars[st]);
+  };
+  for (int kk = 0; kk < nstages - 1; ++kk) issue(kk);
+  double ss = 0.0;
+  int buf = 0;
+  bool ok = true;
+  int64_t kk = 0;
+  const int rstride = rowbytes / (int)sizeof(float);
+  for (; kk < my_n; ++kk) {
+    issue(kk + nstages - 1);
+    const int st = (int)(kk % nstages);
+    if (!bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1))) {
+      ok = false;
+      break;
+    }
+    const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
+    const float* lp = hp + (size_t)RB * rstride;
+    const double* sst = state + (size_t)st * 2 * RB;
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    if (need_dot) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        float h = 0.0f, l = 0.0f;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int c = 2 * tid + 2 * kThreads * s;
+          if (c < C) {
+            const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
+            const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
+            df_fma(a.x, b.x, vh[s][0], vl[s][0], h, l);
+            if (c + 1 < C) df_fma(a.y, b.y, vh[s][1], vl[s][1], h, l);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+          const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+          float sum, er;
+          two_sum_f(h, oh, sum, er);
+          h = sum;
+          l += ol + er;
+        }
+        if ((tid & 31) == 0) {
+          redh[buf][tid >> 5][r] = h;
+          redl[buf][tid >> 5][r] = l;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < RB) {
+      const int r = tid;
+      const int64_t i = r0 + r;
+      double tacc = 0.0;
+      if (i < rows) {
+        double d = 0.0;
+        if (need_dot) {
+          float h = 0.0f, l = 0.0f;
+          for (int q = 0; q < kThreads / 32; ++q) {
+            float sum, er;
+            two_sum_f(h, redh[buf][q][r], sum, er);
+            h = sum;
+            l += redl[buf][q][r] + er;
+          }
+          d = xs * ((double)h + (double)l);
+        }
+        const double s0 = reads0 ? sst[r] : 0.0;
+        const double s1 = reads1 ? sst[RB + r] : 0.0;
+        tacc = row_coef(args, k, i, d, s0, s1, true, ss) * xs;
+      }
+      float th, tl;
+      split_df(tacc, th, tl);
+      tch[buf][r] = th;
+      tcl[buf][r] = tl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const float th = tch[buf][r], tl = tcl[buf][r];
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int c = 2 * tid + 2 * kThreads * s;
+        if (c < C) {
+          const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
+          const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
+          df_fma(th, tl, a.x, b.x, wh[s][0], wl[s][0]);
+          df_fma(th, tl, a.y, b.y, wh[s][1], wl[s][1]);
+        }
+      }
+    }
+    if (((kk + 1) * RB) % kFoldRows == 0) {
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          wd[s][e] += (double)wh[s][e] + (double)wl[s][e];
+          wh[s][e] = wl[s][e] = 0.0f;
+        }
+    }
+    buf ^= 1;
+    __syncthreads();   // stage st is free again
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    for (int64_t q = kk; q < my_n && q < kk + nstages - 1; ++q)
+      bar_wait(&bars[q % nstages], (uint32_t)((q / nstages) & 1));
+  }
+  double* out = pvec + (int64_t)blockIdx.x * C;
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int c = 2 * tid + 2 * kThreads * s;
+    if (c < C) out[c] = wd[s][0] + ((double)wh[s][0] + (double)wl[s][0]);
+    if (c + 1 < C) out[c + 1] = wd[s][1] + ((double)wh[s][1] + (double)wl[s][1]);
+  }
+  ss = group_sum<32>(ss);
+  if ((tid & 31) == 0) sred[tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += sred[q];
+    pscal[blockIdx.x] = t;
+  }
+}
+
 // Rows appended to X by the Tikhonov augmentation: row (xrows + j) = coef * e_j.
 // Writes one extra partial slot (vector of length C and one scalar).
 __global__ void extra_rows_kernel(int64_t nextra, int64_t xrows, int C, double coef,
@@ -689,7 +905,63 @@ __global__ void to_f32_kernel(const double* __restrict__ X, int64_t rows, int64_
   const int64_t i = idx / ldy, j = idx % ldy;
   Y[idx] = j < cols ? (float)X[i * ldx + j] : 0.0f;
 }
+// Largest |X_ij| as the bit pattern of a non-negative double (ordered like the value).
+__global__ void maxabs_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                              unsigned long long* __restrict__ out) {
+  __shared__ double sm[32];
+  double mx = 0.0;
+  const int64_t tot = rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fabs(X[(idx / cols) * ldx + idx % cols]);
+    mx = v > mx ? v : mx;   // NaN entries are skipped
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x / 32); ++q) mx = fmax(mx, sm[q]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// Xh = fl32(X * inv), Xl = fl32(X * inv - Xh); zero padding for j >= cols.
+__global__ void to_x2_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                             double inv, float* __restrict__ Yh, float* __restrict__ Yl,
+                             int64_t ldy) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * ldy) return;
+  const int64_t i = idx / ldy, j = idx % ldy;
+  const double v = j < cols ? X[i * ldx + j] * inv : 0.0;
+  const float h = __double2float_rn(v);
+  Yh[idx] = h;
+  Yl[idx] = __double2float_rn(v - (double)h);
+}
 }  // namespace
+
+lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Yh,
+                         float* Yl, int64_t ldy, unsigned long long* maxbits, double* xs,
+                         cudaStream_t st) {
+  const int64_t tot = rows * ldy;
+  *xs = 1.0;
+  if (tot == 0) return LSRN_OK;
+  LSRN_CUDA_TRY(cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st));
+  const int64_t want = (rows * cols + 255) / 256;
+  launch(maxabs_kernel, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * num_sms()))),
+         dim3(256), 0, st, X, rows, cols, ldx, maxbits);
+  unsigned long long bits = 0;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(&bits, maxbits, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+  double mx;
+  std::memcpy(&mx, &bits, sizeof(mx));
+  // power-of-two scale with the largest |X| / xs in [1, 2): no FP32 overflow,
+  // and elements below 2^-126 of the largest are the only ones that lose bits
+  if (mx > 0.0 && std::isfinite(mx)) *xs = std::ldexp(1.0, std::ilogb(mx));
+  launch(to_x2_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, X, rows, cols, ldx,
+         1.0 / *xs, Yh, Yl, ldy);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
 
 lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
                           int64_t ldy, cudaStream_t st) {
@@ -727,11 +999,14 @@ int pass_blocks(int64_t rows, int64_t C) {
 
 // Staged pass geometry for element size esz: rows per stage and stage count,
 // or false when the staged kernel does not apply.
+// With planes = 2 (the double-float pass) a staged row is one row of each plane
+// and *rowbytes is the bytes of both.
 static bool staged_geometry(int64_t C, int64_t ldx, size_t esz, int* rowbytes, int* rb,
-                            int* nstages) {
+                            int* nstages, int planes = 1) {
   if (C <= 512 || C > 4096) return false;
-  const int64_t rbytes = (C * (int64_t)esz + 15) / 16 * 16;
-  if (rbytes > ldx * (int64_t)esz || (ldx * (int64_t)esz) % 16 != 0) return false;
+  const int64_t pbytes = (C * (int64_t)esz + 15) / 16 * 16;
+  if (pbytes > ldx * (int64_t)esz || (ldx * (int64_t)esz) % 16 != 0) return false;
+  const int64_t rbytes = planes * pbytes;
   int r = (int)std::max<int64_t>(2, (32768 / rbytes) / 2 * 2);
   r = std::min(r, 8);
   if (r != 2 && r != 4 && r != 8) r = r >= 8 ? 8 : (r >= 4 ? 4 : 2);
@@ -759,12 +1034,36 @@ static lsrn_status launch_staged(const Plan* p, const T* X, int64_t ldx, const d
   return LSRN_OK;
 }
 
+template <int SLOTS, int RB>
+static lsrn_status launch_x2(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
+                             double* pscal, const int* done, int rowbytes, int nstages) {
+  const size_t smem = (size_t)nstages * RB * rowbytes + (size_t)nstages * 2 * RB * sizeof(double);
+  auto kern = row_pass_x2_kernel<SLOTS, RB>;
+  LSRN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  launch(kern, dim3(p->nblk), dim3(kThreads), smem, p->stream, p->X2h, p->X2l, p->xrows,
+         (int)p->xcols, p->ldx2, p->x2scale, vin, a, pvec, pscal, done, p->iscal + IC_PASSERR,
+         rowbytes / 2, nstages);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+bool x2_applies(int64_t C) {
+  int rowbytes, rb, ns;
+  const int64_t ld = (C + 3) / 4 * 4;
+  return staged_geometry(C, ld, sizeof(float), &rowbytes, &rb, &ns, 2);
+}
+
 lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
                             double* pscal, const int* done) {
   int tpr, slots;
   if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
   const int C = (int)p->xcols;
   int rowbytes = 0, rb = 0, ns = 0;
+  if (p->X2h != nullptr && staged_geometry(C, p->ldx2, sizeof(float), &rowbytes, &rb, &ns, 2)) {
+    if (slots == 2 && rb == 4) return launch_x2<2, 4>(p, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 4 && rb == 2) return launch_x2<4, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 8 && rb == 2) return launch_x2<8, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
+  }
   if (p->pass_f32 && staged_geometry(C, p->ldx32, sizeof(float), &rowbytes, &rb, &ns)) {
     const float* xp = p->X32;
     if (slots == 2 && rb == 8) return launch_staged<float, 2, 8>(p, xp, p->ldx32, vin, a, pvec, pscal, done, rowbytes, ns);

@@ -137,7 +137,9 @@ static lsrn_status validate_options(const lsrn_options& o) {
   if (!(o.refine_tol > 0.0) || !(o.refine_tol < 1.0)) return LSRN_ERR_INVALID_ARG;
   if (o.sketch_mode != LSRN_SKETCH_F64 && o.sketch_mode != LSRN_SKETCH_TC_SLICED)
     return LSRN_ERR_INVALID_ARG;
-  if (o.iter_mode != LSRN_ITER_F64 && o.iter_mode != LSRN_ITER_F32) return LSRN_ERR_INVALID_ARG;
+  if (o.iter_mode != LSRN_ITER_F64 && o.iter_mode != LSRN_ITER_F32 &&
+      o.iter_mode != LSRN_ITER_F32X2)
+    return LSRN_ERR_INVALID_ARG;
   return LSRN_OK;
 }
 
@@ -339,6 +341,19 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
     if (st == LSRN_OK)
       st = launch_to_f32(p->X, p->xrows, p->xcols, p->ldx, x32, p->ldx32, p->stream);
     p->X32 = x32;
+  }
+  if (st == LSRN_OK && o.iter_mode == LSRN_ITER_F32X2 && !p->csr && x2_applies(p->xcols)) {
+    p->ldx2 = (p->xcols + 3) / 4 * 4;
+    float *xh = nullptr, *xl = nullptr;
+    unsigned long long* mb = nullptr;
+    st = dalloc_n(p, &xh, p->xrows * p->ldx2);
+    if (st == LSRN_OK) st = dalloc_n(p, &xl, p->xrows * p->ldx2);
+    if (st == LSRN_OK) st = dalloc_n(p, &mb, 1);
+    if (st == LSRN_OK)
+      st = launch_to_x2(p->X, p->xrows, p->xcols, p->ldx, xh, xl, p->ldx2, mb, &p->x2scale,
+                        p->stream);
+    p->X2h = xh;
+    p->X2l = xl;
   }
   if (st == LSRN_OK) st = plan_workspace(p);
   if (st == LSRN_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LSRN_ERR_CUDA;

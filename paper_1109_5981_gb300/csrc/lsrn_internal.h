@@ -100,6 +100,10 @@ struct Plan {
   const float* X32 = nullptr;       // FP32 copy of X (iteration mode LSRN_ITER_F32)
   int64_t ldx32 = 0;
   bool pass_f32 = false;            // fused passes currently stream X32
+  const float* X2h = nullptr;       // double-float planes of X / x2scale (LSRN_ITER_F32X2)
+  const float* X2l = nullptr;
+  int64_t ldx2 = 0;
+  double x2scale = 1.0;
 
   // CSR (m >= n: A; m < n: A^T) in both orientations for deterministic passes
   const int64_t* rp = nullptr;  const int32_t* ci = nullptr;  const double* cv = nullptr;   // rows of X
@@ -202,6 +206,10 @@ lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, 
                         const double* y, double* y2, const double* c, const int* done,
                         cudaStream_t st);
 // Y (rows x ldy, FP32, zero beyond cols) = X (rows x cols, FP64, ldx)
+bool x2_applies(int64_t C);
+lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Yh,
+                         float* Yl, int64_t ldy, unsigned long long* maxbits, double* xs,
+                         cudaStream_t st);
 lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
                           int64_t ldy, cudaStream_t st);
 // out[i] = M_i . v accumulated in double-double (warp per row)

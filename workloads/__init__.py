@@ -49,6 +49,8 @@ class DenseProblem:
     apply_Ut: Callable[[np.ndarray], np.ndarray]   # b (m,) -> U^T b (rank,)
     apply_V: Callable[[np.ndarray], np.ndarray]    # c (rank,) -> V c (n,)
     meta: dict
+    apply_U: Optional[Callable[[np.ndarray], np.ndarray]] = None    # c (rank,) -> U c (m,)
+    apply_Vt: Optional[Callable[[np.ndarray], np.ndarray]] = None   # v (n,) -> V^T v (rank,)
 
 
 def _haar(rng: np.random.Generator, n: int, k: int) -> np.ndarray:
@@ -147,7 +149,16 @@ def dense_householder(m: int, n: int, rank: int, cond: float, noise: float, seed
     def apply_V(c: np.ndarray) -> np.ndarray:
         return V @ np.asarray(c, dtype=np.float64)
 
+    def apply_U(c: np.ndarray) -> np.ndarray:
+        z = np.zeros((m, 1))
+        z[:rank, 0] = np.asarray(c, dtype=np.float64)
+        return QU.apply(z)[:, 0]
+
+    def apply_Vt(v: np.ndarray) -> np.ndarray:
+        return V.T @ np.asarray(v, dtype=np.float64)
+
     return DenseProblem(A=A, b=b, x0=x0, sigma=sigma, apply_Ut=apply_Ut, apply_V=apply_V,
+                        apply_U=apply_U, apply_Vt=apply_Vt,
                         meta=dict(kind="householder", m=m, n=n, rank=rank, cond=cond,
                                   noise=noise, seed=seed, n_reflectors=k, V=V))
 
