@@ -80,7 +80,9 @@ typedef enum {
                                    into FP64 every 64 rows (relative error of each product and
                                    sum ~2^-48, against 2^-53 in FP64).  Tall and fat; the
                                    sweep keeps tol, and refinement stays double-double on the
-                                   FP64 A. */
+                                   FP64 A with at least two steps (early stop as usual).
+                                   Vectors and row coefficients are rescaled by powers of two
+                                   inside the pass, so any finite A, b work. */
 } lsrn_iter_mode;
 
 typedef enum {

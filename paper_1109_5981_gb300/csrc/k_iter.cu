@@ -444,11 +444,18 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
 // each element.  Every element operation runs on the FP32 pipe with
 // error-free transformations: the product of two (hi, lo) pairs is
 // TwoProd(hi, hi) plus the two cross terms, and sums are TwoSum into
-// (hi, lo) accumulators.  The column accumulators are folded into FP64 every
-// kFoldRows rows, which bounds the error of the lazy low words.  Only the
-// per-row LSQR/CS update (one thread per row) is FP64.  Same staging, row
-// modes and outputs as row_pass_staged_kernel.
-constexpr int kFoldRows = 64;
+// (hi, lo) accumulators.  Only the per-row LSQR/CS update (one thread per
+// row) is FP64.  Same staging, row modes and outputs as row_pass_staged_kernel.
+//
+// Range: vin enters as vin / 2^ve with ve the exponent of max |vin| (per CTA);
+// row coefficients enter as t / 2^E with a running exponent E shared by the
+// CTA.  E is raised when a row's |t| would exceed 2^(E + 60); the column
+// accumulators are folded into FP64 (times 2^E) before it changes, and every
+// kFoldRows rows, which also bounds the error of their lazy low words.  Only
+// contributions below 2^-126 of the largest vin entry or row coefficient lose
+// bits.
+constexpr int kFoldRows = 128;
+constexpr int kNoExp = -100000;
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
   s = a + b;
@@ -469,6 +476,9 @@ __device__ __forceinline__ void split_df(double x, float& h, float& l) {
   h = __double2float_rn(x);
   l = __double2float_rn(x - (double)h);
 }
+__device__ __forceinline__ int exp_of(double x) {   // ilogb for finite nonzero x, else kNoExp
+  return (x != 0.0 && isfinite(x)) ? ilogb(x) : kNoExp;
+}
 
 template <int SLOTS, int RB>
 __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
@@ -481,6 +491,8 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
   __shared__ uint64_t bars[kMaxStages];
   __shared__ float redh[2][kThreads / 32][RB], redl[2][kThreads / 32][RB];
   __shared__ float tch[2][RB], tcl[2][RB];
+  __shared__ int texp[2];
+  __shared__ int vexp[kThreads / 32];
   __shared__ double sred[kThreads / 32];
   const int tid = threadIdx.x;
   const bool need_dot = args.mode != RM_ACC_STATE;
@@ -493,25 +505,43 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
     k.c0 = args.coef[0];
     k.c1 = args.coef[1];
   }
-  float vh[SLOTS][2], vl[SLOTS][2], wh[SLOTS][2], wl[SLOTS][2];
-  double wd[SLOTS][2];
+  // exponent of max |vin| over the whole vector (each thread sees its slots)
+  double vv[SLOTS][2];
+  int ve = kNoExp;
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s)
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int c = 2 * tid + 2 * kThreads * s + e;
-      split_df((need_dot && c < C) ? vin[c] : 0.0, vh[s][e], vl[s][e]);
-      wh[s][e] = wl[s][e] = 0.0f;
-      wd[s][e] = 0.0;
+      vv[s][e] = (need_dot && c < C) ? vin[c] : 0.0;
+      ve = max(ve, exp_of(vv[s][e]));
     }
-  const int64_t nrb = (rows + RB - 1) / RB;
-  const int64_t my_n = blockIdx.x < nrb ? (nrb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  for (int o = 16; o > 0; o >>= 1) ve = max(ve, __shfl_xor_sync(0xffffffffu, ve, o));
+  if ((tid & 31) == 0) vexp[tid >> 5] = ve;
   if (tid == 0) {
     for (int st = 0; st < nstages; ++st)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&bars[st])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  for (int q = 0; q < kThreads / 32; ++q) ve = max(ve, vexp[q]);
+  if (ve == kNoExp) ve = 0;
+  const double vscale = ldexp(1.0, ve);
+  const double dscale = xs * vscale;
+  float vh[SLOTS][2], vl[SLOTS][2], wh[SLOTS][2], wl[SLOTS][2];
+  double wd[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      split_df(ldexp(vv[s][e], -ve), vh[s][e], vl[s][e]);
+      wh[s][e] = wl[s][e] = 0.0f;
+      wd[s][e] = 0.0;
+    }
+  int E = kNoExp;          // running exponent of the row coefficients (uniform)
+  double escale = 0.0;     // 2^E * xs once E is set
+  const int64_t nrb = (rows + RB - 1) / RB;
+  const int64_t my_n = blockIdx.x < nrb ? (nrb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   auto issue = [&](int64_t kk) {
     if (tid != 0 || kk >= my_n) return;
     const int st = (int)(kk % nstages);
@@ -537,7 +567,20 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
   int buf = 0;
   bool ok = true;
   int64_t kk = 0;
+  int since_fold = 0;
   const int rstride = rowbytes / (int)sizeof(float);
+  auto fold = [&]() {
+    if (E != kNoExp) {
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          wd[s][e] += escale * ((double)wh[s][e] + (double)wl[s][e]);
+          wh[s][e] = wl[s][e] = 0.0f;
+        }
+    }
+    since_fold = 0;
+  };
   for (; kk < my_n; ++kk) {
     issue(kk + nstages - 1);
     const int st = (int)(kk % nstages);
@@ -560,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
             const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
             const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
             df_fma(a.x, b.x, vh[s][0], vl[s][0], h, l);
-            if (c + 1 < C) df_fma(a.y, b.y, vh[s][1], vl[s][1], h, l);
+            df_fma(a.y, b.y, vh[s][1], vl[s][1], h, l);   // vin is 0 past C
           }
         }
 #pragma unroll
@@ -579,11 +622,12 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
       }
     }
     __syncthreads();
-    if (tid < RB) {
+    if (tid < 32) {
+      // warp 0: lane r < RB finishes row r; the lanes agree on the new exponent
       const int r = tid;
       const int64_t i = r0 + r;
       double tacc = 0.0;
-      if (i < rows) {
+      if (r < RB && i < rows) {
         double d = 0.0;
         if (need_dot) {
           float h = 0.0f, l = 0.0f;
@@ -593,18 +637,30 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
             h = sum;
             l += redl[buf][q][r] + er;
           }
-          d = xs * ((double)h + (double)l);
+          d = dscale * ((double)h + (double)l);
         }
         const double s0 = reads0 ? sst[r] : 0.0;
         const double s1 = reads1 ? sst[RB + r] : 0.0;
-        tacc = row_coef(args, k, i, d, s0, s1, true, ss) * xs;
+        tacc = row_coef(args, k, i, d, s0, s1, true, ss);
       }
-      float th, tl;
-      split_df(tacc, th, tl);
-      tch[buf][r] = th;
-      tcl[buf][r] = tl;
+      int me = exp_of(tacc);
+      for (int o = 16; o > 0; o >>= 1) me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
+      const int En = (me != kNoExp && (E == kNoExp || me > E + 60)) ? me : E;
+      if (r < RB) {
+        float th = 0.0f, tl = 0.0f;
+        if (En != kNoExp) split_df(ldexp(tacc, -En), th, tl);
+        tch[buf][r] = th;
+        tcl[buf][r] = tl;
+      }
+      if (r == 0) texp[buf] = En;
     }
     __syncthreads();
+    const int En = texp[buf];
+    if (En != E) {
+      fold();
+      E = En;
+      escale = ldexp(xs, E);
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const float th = tch[buf][r], tl = tcl[buf][r];
@@ -619,15 +675,8 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
         }
       }
     }
-    if (((kk + 1) * RB) % kFoldRows == 0) {
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          wd[s][e] += (double)wh[s][e] + (double)wl[s][e];
-          wh[s][e] = wl[s][e] = 0.0f;
-        }
-    }
+    since_fold += RB;
+    if (since_fold >= kFoldRows) fold();
     buf ^= 1;
     __syncthreads();   // stage st is free again
   }
@@ -636,12 +685,13 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
     for (int64_t q = kk; q < my_n && q < kk + nstages - 1; ++q)
       bar_wait(&bars[q % nstages], (uint32_t)((q / nstages) & 1));
   }
+  fold();
   double* out = pvec + (int64_t)blockIdx.x * C;
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int c = 2 * tid + 2 * kThreads * s;
-    if (c < C) out[c] = wd[s][0] + ((double)wh[s][0] + (double)wl[s][0]);
-    if (c + 1 < C) out[c + 1] = wd[s][1] + ((double)wh[s][1] + (double)wl[s][1]);
+    if (c < C) out[c] = wd[s][0];
+    if (c + 1 < C) out[c + 1] = wd[s][1];
   }
   ss = group_sum<32>(ss);
   if ((tid & 31) == 0) sred[tid >> 5] = ss;

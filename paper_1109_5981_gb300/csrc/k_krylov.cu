@@ -650,6 +650,9 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
   // for the remaining steps once a step contracts the change by less than 20x
   // (FP32 rounding of A perturbs the preconditioned operator by ~u32 kappa(A)).
   if (p->X32 != nullptr) nsteps = std::max(nsteps, 6);
+  // Double-float passes perturb A by ~2^-46 relative, so with a nonzero
+  // residual a step contracts by ~kappa^2 2^-46 |r| / (|A||x|): two steps at least.
+  if (p->X2h != nullptr && nsteps > 0) nsteps = std::max(nsteps, 2);
   if (nsteps <= 0 || p->rank == 0) return LSRN_OK;
   p->pass_f32 = p->X32 != nullptr;
   double prev_change = 1.0;
