@@ -355,11 +355,13 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
     const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
     // dot products: per-thread partials in T, warp sums in T, cross-warp sum and
     // the row's LSQR/CS update by one thread per row (FP64), broadcast via smem
+    // rows past the end of X (last block) hold stale shared memory: skipped
+    const int nr = (int)min((int64_t)RB, rows - r0);
     T dp[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       T t = (T)0;
-      if (need_dot) {
+      if (need_dot && r < nr) {
         const T* row = rowp + (size_t)r * (rowbytes / sizeof(T));
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
@@ -398,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
+      if (r >= nr) break;
       const T tc = (T)tco[buf][r];
       const T* row = rowp + (size_t)r * (rowbytes / sizeof(T));
 #pragma unroll
@@ -480,32 +483,51 @@ __device__ __forceinline__ int exp_of(double x) {   // ilogb for finite nonzero 
   return (x != 0.0 && isfinite(x)) ? ilogb(x) : kNoExp;
 }
 
+// Named barriers of the pipelined pass (0 is __syncthreads).
+constexpr int kBarDot = 1;     // + parity: partial dots of a stage are in shared memory
+constexpr int kBarCoef = 3;    // + parity: row coefficients of a stage are in shared memory
+constexpr int kBarFree = 5;    // compute warps are done with a stage
+constexpr int kX2Threads = kThreads + 32;
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Warp-specialised: warps 0-7 compute the partial dots of stage k while warp 8
+// turns the dots of stage k - 1 into row coefficients (FP64, one lane per row),
+// then warps 0-7 accumulate stage k - 1.  The FP64 row update is thus off the
+// compute warps' critical path.
 template <int SLOTS, int RB>
-__global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
+__global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
     const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t rows, int C, int64_t ldx,
     double xs, const double* __restrict__ vin, RowArgs args, double* __restrict__ pvec,
     double* __restrict__ pscal, const int* __restrict__ done, int* __restrict__ err, int rowbytes,
     int nstages) {
+  static_assert(RB * (kThreads / 32) <= 32, "one coefficient-warp lane per (row, warp) partial");
   if (done != nullptr && *done) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
-  __shared__ float redh[2][kThreads / 32][RB], redl[2][kThreads / 32][RB];
+  __shared__ float redh[2][RB][kThreads / 32], redl[2][RB][kThreads / 32];
   __shared__ float tch[2][RB], tcl[2][RB];
   __shared__ int texp[2];
   __shared__ int vexp[kThreads / 32];
-  __shared__ double sred[kThreads / 32];
+  __shared__ int abort_flag;
   const int tid = threadIdx.x;
+  const bool coef_warp = tid >= kThreads;
   const bool need_dot = args.mode != RM_ACC_STATE;
   const bool reads0 = mode_reads_st0(args.mode);
   const bool reads1 = args.mode == RM_FAT_CS;
   const int stage_bytes = 2 * RB * rowbytes;   // RB rows of Xh, then RB rows of Xl
   double* state = (double*)(smem + (size_t)nstages * stage_bytes);   // [nstages][2][RB]
+  const int rstride = rowbytes / (int)sizeof(float);
   Coef k{0.0, 0.0};
   if (args.coef) {
     k.c0 = args.coef[0];
     k.c1 = args.coef[1];
   }
-  // exponent of max |vin| over the whole vector (each thread sees its slots)
+  // exponent of max |vin| over the whole vector (compute threads see their slots)
   double vv[SLOTS][2];
   int ve = kNoExp;
 #pragma unroll
@@ -513,37 +535,28 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int c = 2 * tid + 2 * kThreads * s + e;
-      vv[s][e] = (need_dot && c < C) ? vin[c] : 0.0;
+      vv[s][e] = (!coef_warp && need_dot && c < C) ? vin[c] : 0.0;
       ve = max(ve, exp_of(vv[s][e]));
     }
   for (int o = 16; o > 0; o >>= 1) ve = max(ve, __shfl_xor_sync(0xffffffffu, ve, o));
-  if ((tid & 31) == 0) vexp[tid >> 5] = ve;
+  if (!coef_warp && (tid & 31) == 0) vexp[tid >> 5] = ve;
   if (tid == 0) {
+    abort_flag = 0;
     for (int st = 0; st < nstages; ++st)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&bars[st])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  ve = kNoExp;
   for (int q = 0; q < kThreads / 32; ++q) ve = max(ve, vexp[q]);
   if (ve == kNoExp) ve = 0;
-  const double vscale = ldexp(1.0, ve);
-  const double dscale = xs * vscale;
-  float vh[SLOTS][2], vl[SLOTS][2], wh[SLOTS][2], wl[SLOTS][2];
-  double wd[SLOTS][2];
-#pragma unroll
-  for (int s = 0; s < SLOTS; ++s)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      split_df(ldexp(vv[s][e], -ve), vh[s][e], vl[s][e]);
-      wh[s][e] = wl[s][e] = 0.0f;
-      wd[s][e] = 0.0;
-    }
-  int E = kNoExp;          // running exponent of the row coefficients (uniform)
-  double escale = 0.0;     // 2^E * xs once E is set
+  const double dscale = ldexp(xs, ve);
   const int64_t nrb = (rows + RB - 1) / RB;
   const int64_t my_n = blockIdx.x < nrb ? (nrb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  int64_t issued_upto = -1, waited_upto = -1;   // bookkeeping of thread 0 (the producer)
   auto issue = [&](int64_t kk) {
-    if (tid != 0 || kk >= my_n) return;
+    if (tid != 0 || kk >= my_n || abort_flag != 0) return;
+    issued_upto = kk;
     const int st = (int)(kk % nstages);
     const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
     const int nr = (int)min((int64_t)RB, rows - r0);
@@ -562,13 +575,77 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
     if (reads0) bulk_copy(state + (size_t)st * 2 * RB, args.st0 + r0, sbytes, &bars[st]);
     if (reads1) bulk_copy(state + (size_t)st * 2 * RB + RB, args.st1 + r0, sbytes, &bars[st]);
   };
-  for (int kk = 0; kk < nstages - 1; ++kk) issue(kk);
-  double ss = 0.0;
-  int buf = 0;
-  bool ok = true;
-  int64_t kk = 0;
+  int E = kNoExp;   // running exponent of the row coefficients (same in every thread)
+
+  if (coef_warp) {
+    // ---- coefficient warp: lane = (row r, partial q) for the cross-warp sums ----
+    const int lane = tid - kThreads;
+    const int rq = lane / (kThreads / 32), qq = lane % (kThreads / 32);
+    double ss = 0.0;
+    for (int64_t kk = 0; kk < my_n; ++kk) {
+      const int par = (int)(kk & 1);
+      named_sync(kBarDot + par, kX2Threads);
+      const int st = (int)(kk % nstages);
+      const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+      const int nr = (int)min((int64_t)RB, rows - r0);
+      const bool aborted = abort_flag != 0;
+      // the stage's state words came by bulk copy: observe its completed phase
+      if (!aborted && (reads0 || reads1)) bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1));
+      float h = 0.0f, l = 0.0f;
+      if (need_dot && rq < RB) {
+        h = redh[par][rq][qq];
+        l = redl[par][rq][qq];
+      }
+#pragma unroll
+      for (int o = (kThreads / 32) / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float sum, er;
+        two_sum_f(h, oh, sum, er);
+        h = sum;
+        l += ol + er;
+      }
+      double tacc = 0.0;
+      const bool owner = qq == 0 && rq < nr && !aborted;
+      if (owner) {
+        const int64_t i = r0 + rq;
+        const double d = need_dot ? dscale * ((double)h + (double)l) : 0.0;
+        const double* sst = state + (size_t)st * 2 * RB;
+        const double s0 = reads0 ? sst[rq] : 0.0;
+        const double s1 = reads1 ? sst[RB + rq] : 0.0;
+        tacc = row_coef(args, k, i, d, s0, s1, true, ss);
+      }
+      int me = exp_of(tacc);
+      for (int o = 16; o > 0; o >>= 1) me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
+      if (me != kNoExp && (E == kNoExp || me > E + 60)) E = me;
+      if (qq == 0 && rq < RB) {
+        float th = 0.0f, tl = 0.0f;
+        if (owner && E != kNoExp) split_df(ldexp(tacc, -E), th, tl);
+        tch[par][rq] = th;
+        tcl[par][rq] = tl;
+      }
+      if (lane == 0) texp[par] = E;
+      __threadfence_block();
+      named_arrive(kBarCoef + par, kX2Threads);
+    }
+    ss = group_sum<32>(ss);
+    if (lane == 0) pscal[blockIdx.x] = ss;
+    return;
+  }
+
+  // ---- compute warps ----
+  float vh[SLOTS][2], vl[SLOTS][2], wh[SLOTS][2], wl[SLOTS][2];
+  double wd[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      split_df(ldexp(vv[s][e], -ve), vh[s][e], vl[s][e]);
+      wh[s][e] = wl[s][e] = 0.0f;
+      wd[s][e] = 0.0;
+    }
+  double escale = 0.0;
   int since_fold = 0;
-  const int rstride = rowbytes / (int)sizeof(float);
   auto fold = [&]() {
     if (E != kNoExp) {
 #pragma unroll
@@ -581,89 +658,23 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
     }
     since_fold = 0;
   };
-  for (; kk < my_n; ++kk) {
-    issue(kk + nstages - 1);
-    const int st = (int)(kk % nstages);
-    if (!bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1))) {
-      ok = false;
-      break;
-    }
-    const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
-    const float* lp = hp + (size_t)RB * rstride;
-    const double* sst = state + (size_t)st * 2 * RB;
-    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
-    if (need_dot) {
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        float h = 0.0f, l = 0.0f;
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const int c = 2 * tid + 2 * kThreads * s;
-          if (c < C) {
-            const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
-            const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
-            df_fma(a.x, b.x, vh[s][0], vl[s][0], h, l);
-            df_fma(a.y, b.y, vh[s][1], vl[s][1], h, l);   // vin is 0 past C
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-          const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-          float sum, er;
-          two_sum_f(h, oh, sum, er);
-          h = sum;
-          l += ol + er;
-        }
-        if ((tid & 31) == 0) {
-          redh[buf][tid >> 5][r] = h;
-          redl[buf][tid >> 5][r] = l;
-        }
-      }
-    }
-    __syncthreads();
-    if (tid < 32) {
-      // warp 0: lane r < RB finishes row r; the lanes agree on the new exponent
-      const int r = tid;
-      const int64_t i = r0 + r;
-      double tacc = 0.0;
-      if (r < RB && i < rows) {
-        double d = 0.0;
-        if (need_dot) {
-          float h = 0.0f, l = 0.0f;
-          for (int q = 0; q < kThreads / 32; ++q) {
-            float sum, er;
-            two_sum_f(h, redh[buf][q][r], sum, er);
-            h = sum;
-            l += redl[buf][q][r] + er;
-          }
-          d = dscale * ((double)h + (double)l);
-        }
-        const double s0 = reads0 ? sst[r] : 0.0;
-        const double s1 = reads1 ? sst[RB + r] : 0.0;
-        tacc = row_coef(args, k, i, d, s0, s1, true, ss);
-      }
-      int me = exp_of(tacc);
-      for (int o = 16; o > 0; o >>= 1) me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
-      const int En = (me != kNoExp && (E == kNoExp || me > E + 60)) ? me : E;
-      if (r < RB) {
-        float th = 0.0f, tl = 0.0f;
-        if (En != kNoExp) split_df(ldexp(tacc, -En), th, tl);
-        tch[buf][r] = th;
-        tcl[buf][r] = tl;
-      }
-      if (r == 0) texp[buf] = En;
-    }
-    __syncthreads();
-    const int En = texp[buf];
+  auto accumulate = [&](int64_t kk) {
+    const int par = (int)(kk & 1);
+    named_sync(kBarCoef + par, kX2Threads);
+    const int En = texp[par];
     if (En != E) {
       fold();
       E = En;
       escale = ldexp(xs, E);
     }
+    const int st = (int)(kk % nstages);
+    const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
+    const float* lp = hp + (size_t)RB * rstride;
+    const int nr = (int)min((int64_t)RB, rows - (blockIdx.x + kk * gridDim.x) * RB);
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const float th = tch[buf][r], tl = tcl[buf][r];
+      if (r >= nr) break;
+      const float th = tch[par][r], tl = tcl[par][r];
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int c = 2 * tid + 2 * kThreads * s;
@@ -677,12 +688,65 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
     }
     since_fold += RB;
     if (since_fold >= kFoldRows) fold();
-    buf ^= 1;
-    __syncthreads();   // stage st is free again
+  };
+  for (int kk = 0; kk < nstages; ++kk) issue(kk);
+  for (int64_t kk = 0; kk < my_n; ++kk) {
+    const int par = (int)(kk & 1);
+    const int st = (int)(kk % nstages);
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    const int nr = (int)min((int64_t)RB, rows - r0);
+    bool have = abort_flag == 0;
+    if (have && !bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1))) {
+      abort_flag = 1;   // later waits and copies are skipped; the barrier sequence continues
+      have = false;
+    }
+    if (have && tid == 0) waited_upto = kk;
+    if (need_dot) {
+      const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
+      const float* lp = hp + (size_t)RB * rstride;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        float h = 0.0f, l = 0.0f;
+        if (have && r < nr) {
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            const int c = 2 * tid + 2 * kThreads * s;
+            if (c < C) {
+              const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
+              const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
+              df_fma(a.x, b.x, vh[s][0], vl[s][0], h, l);
+              df_fma(a.y, b.y, vh[s][1], vl[s][1], h, l);   // vin is 0 past C
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+          const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+          float sum, er;
+          two_sum_f(h, oh, sum, er);
+          h = sum;
+          l += ol + er;
+        }
+        if ((tid & 31) == 0) {
+          redh[par][r][tid >> 5] = h;
+          redl[par][r][tid >> 5] = l;
+        }
+      }
+    }
+    __threadfence_block();
+    named_arrive(kBarDot + par, kX2Threads);
+    if (kk >= 1) {
+      accumulate(kk - 1);
+      named_sync(kBarFree, kThreads);   // stage (kk - 1) may be refilled
+      issue(kk - 1 + nstages);
+    }
   }
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    for (int64_t q = kk; q < my_n && q < kk + nstages - 1; ++q)
+  if (my_n >= 1) accumulate(my_n - 1);
+  if (tid == 0 && abort_flag != 0) {
+    atomicExch(err, 1);
+    // copies issued but not observed must land before the CTA exits
+    for (int64_t q = waited_upto + 1; q <= issued_upto; ++q)
       bar_wait(&bars[q % nstages], (uint32_t)((q / nstages) & 1));
   }
   fold();
@@ -692,14 +756,6 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_x2_kernel(
     const int c = 2 * tid + 2 * kThreads * s;
     if (c < C) out[c] = wd[s][0];
     if (c + 1 < C) out[c + 1] = wd[s][1];
-  }
-  ss = group_sum<32>(ss);
-  if ((tid & 31) == 0) sred[tid >> 5] = ss;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) t += sred[q];
-    pscal[blockIdx.x] = t;
   }
 }
 
@@ -1084,23 +1140,39 @@ static lsrn_status launch_staged(const Plan* p, const T* X, int64_t ldx, const d
   return LSRN_OK;
 }
 
+// Geometry of the double-float pass: RB rows of both planes per stage (RB = 4
+// up to 2048 columns, 2 above), as many stages as fit in 196 KB (at most 8).
+static bool x2_geometry(int64_t C, int64_t ldx2, int* planebytes, int* rb, int* nstages) {
+  if (C <= 512 || C > 4096) return false;
+  const int64_t pbytes = (C * 4 + 15) / 16 * 16;
+  if (pbytes > ldx2 * 4 || (ldx2 * 4) % 16 != 0) return false;
+  const int r = C <= 2048 ? 4 : 2;
+  const int64_t stage = 2 * r * pbytes + 2 * r * 8;
+  const int ns = (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / stage);
+  if (ns < 3) return false;
+  *planebytes = (int)pbytes;
+  *rb = r;
+  *nstages = ns;
+  return true;
+}
+
 template <int SLOTS, int RB>
 static lsrn_status launch_x2(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
-                             double* pscal, const int* done, int rowbytes, int nstages) {
-  const size_t smem = (size_t)nstages * RB * rowbytes + (size_t)nstages * 2 * RB * sizeof(double);
+                             double* pscal, const int* done, int planebytes, int nstages) {
+  const size_t smem =
+      (size_t)nstages * 2 * RB * planebytes + (size_t)nstages * 2 * RB * sizeof(double);
   auto kern = row_pass_x2_kernel<SLOTS, RB>;
   LSRN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  launch(kern, dim3(p->nblk), dim3(kThreads), smem, p->stream, p->X2h, p->X2l, p->xrows,
+  launch(kern, dim3(p->nblk), dim3(kX2Threads), smem, p->stream, p->X2h, p->X2l, p->xrows,
          (int)p->xcols, p->ldx2, p->x2scale, vin, a, pvec, pscal, done, p->iscal + IC_PASSERR,
-         rowbytes / 2, nstages);
+         planebytes, nstages);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }
 
 bool x2_applies(int64_t C) {
-  int rowbytes, rb, ns;
-  const int64_t ld = (C + 3) / 4 * 4;
-  return staged_geometry(C, ld, sizeof(float), &rowbytes, &rb, &ns, 2);
+  int pb, rb, ns;
+  return x2_geometry(C, (C + 3) / 4 * 4, &pb, &rb, &ns);
 }
 
 lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
@@ -1109,9 +1181,9 @@ lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, 
   if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
   const int C = (int)p->xcols;
   int rowbytes = 0, rb = 0, ns = 0;
-  if (p->X2h != nullptr && staged_geometry(C, p->ldx2, sizeof(float), &rowbytes, &rb, &ns, 2)) {
+  if (p->X2h != nullptr && x2_geometry(C, p->ldx2, &rowbytes, &rb, &ns)) {
     if (slots == 2 && rb == 4) return launch_x2<2, 4>(p, vin, a, pvec, pscal, done, rowbytes, ns);
-    if (slots == 4 && rb == 2) return launch_x2<4, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 4 && rb == 4) return launch_x2<4, 4>(p, vin, a, pvec, pscal, done, rowbytes, ns);
     if (slots == 8 && rb == 2) return launch_x2<8, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
   }
   if (p->pass_f32 && staged_geometry(C, p->ldx32, sizeof(float), &rowbytes, &rb, &ns)) {
