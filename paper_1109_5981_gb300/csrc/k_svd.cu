@@ -156,6 +156,113 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ 
   if (lane == 0) atomicAdd(rot_count, 1);
 }
 
+// One round with the rows of a pair held in registers: a CTA of kJacThreads per
+// pair, EPT elements of each row per thread (Q <= kJacThreads * EPT).  Squared
+// row norms are carried in nrm2 (exact at the start of each sweep) and updated
+// after a rotation by the Hestenes identities aa' = aa - t ab, bb' = bb + t ab,
+// so a pair costs one dot product unless it rotates.  A norm that falls below
+// a quarter of its value is recomputed from the rotated row (cancellation).
+constexpr int kJacThreads = 128;
+
+__device__ __forceinline__ double jac_block_sum(double v, double* sh) {
+  v = group_sum<32>(v);
+  __syncthreads();   // sh may still be read from the previous sum
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < kJacThreads / 32; ++q) t += sh[q];
+  return t;
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __restrict__ W, int64_t Q,
+                                                                  int P, int t, double tol,
+                                                                  double* __restrict__ nrm2,
+                                                                  int* __restrict__ rot_count) {
+  __shared__ double sh[kJacThreads / 32];
+  const int pr = blockIdx.x;
+  int a, b;
+  if (pr == 0) {
+    a = P - 1;
+    b = t;
+  } else {
+    a = (t + pr) % (P - 1);
+    b = (t - pr + P - 1) % (P - 1);
+  }
+  if (a >= Q || b >= Q) return;
+  if (a > b) {
+    const int tmp = a;
+    a = b;
+    b = tmp;
+  }
+  double* wa = W + (int64_t)a * Q;
+  double* wb = W + (int64_t)b * Q;
+  double x[EPT], y[EPT];
+  double ab = 0.0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
+    x[e] = c < Q ? wa[c] : 0.0;
+    y[e] = c < Q ? wb[c] : 0.0;
+    ab = fma(x[e], y[e], ab);
+  }
+  ab = jac_block_sum(ab, sh);
+  const double aa = nrm2[a], bb = nrm2[b];
+  if (aa == 0.0 || bb == 0.0) return;
+  if (fabs(ab) <= tol * sqrt(aa) * sqrt(bb)) return;
+  const double zeta = (bb - aa) / (2.0 * ab);
+  double tt;
+  if (fabs(zeta) > 1e150) {
+    tt = 0.5 / zeta;
+  } else {
+    tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  }
+  const double cs = 1.0 / sqrt(1.0 + tt * tt);
+  const double sn = cs * tt;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
+    const double xa = cs * x[e] - sn * y[e];
+    const double yb = sn * x[e] + cs * y[e];
+    x[e] = xa;
+    y[e] = yb;
+    if (c < Q) {
+      wa[c] = xa;
+      wb[c] = yb;
+    }
+  }
+  double na = aa - tt * ab, nb = bb + tt * ab;
+  if (na < 0.25 * aa || nb < 0.25 * bb) {   // uniform: every thread has the same values
+    double sa = 0.0, sb = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      sa = fma(x[e], x[e], sa);
+      sb = fma(y[e], y[e], sb);
+    }
+    na = jac_block_sum(sa, sh);
+    nb = jac_block_sum(sb, sh);
+  }
+  if (threadIdx.x == 0) {
+    nrm2[a] = na;
+    nrm2[b] = nb;
+    atomicAdd(rot_count, 1);
+  }
+}
+
+__global__ void row_sqnorms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm2) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= Q) return;
+  double acc = 0.0;
+  for (int64_t c = lane; c < Q; c += 32) {
+    const double x = W[row * Q + c];
+    acc = fma(x, x, acc);
+  }
+  acc = group_sum<32>(acc);
+  if (lane == 0) nrm2[row] = acc;
+}
+
 __global__ void row_norms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -262,11 +369,24 @@ lsrn_status run_precond(Plan* p) {
   int host_rot = 0;
   int sweeps = 0;
   const int max_sweeps = 40;
+  // rows in registers when they fit (Q <= 4096), else the streaming warp-per-pair kernel
+  const int ept = Q <= 512 ? 4 : Q <= 1024 ? 8 : Q <= 2048 ? 16 : Q <= 4096 ? 32 : 0;
+  double* nrm2 = p->tmpq;
   if (P > 1) {
     do {
       LSRN_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int), st));
-      for (int t = 0; t < P - 1; ++t)
-        launch(jacobi_round_kernel, dim3(rblocks), dim3(256), 0, st, p->Wj, Q, P, t, tol, rot);
+      if (ept > 0)
+        launch(row_sqnorms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, nrm2);
+      for (int t = 0; t < P - 1; ++t) {
+        const dim3 pg((unsigned)(P / 2));
+        switch (ept) {
+          case 4: launch(jacobi_pair_kernel<4>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          case 8: launch(jacobi_pair_kernel<8>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          case 16: launch(jacobi_pair_kernel<16>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          case 32: launch(jacobi_pair_kernel<32>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          default: launch(jacobi_round_kernel, dim3(rblocks), dim3(256), 0, st, p->Wj, Q, P, t, tol, rot);
+        }
+      }
       LSRN_CUDA_TRY(cudaGetLastError());
       LSRN_CUDA_TRY(cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st));
       LSRN_CUDA_TRY(cudaStreamSynchronize(st));
