@@ -386,9 +386,11 @@ def main():
                          "ok": bool(max(errs) <= 1e-10)},
             "phases_ms": {"sketch": t_sketch,
                           "precond": float(np.mean([i["t_precond_ms"] for i in infos])),
+                          "precond_qr": float(np.mean([i["t_qr_ms"] for i in infos])),
                           "iter": float(np.mean([i["t_iter_ms"] for i in infos])),
                           "refine": float(np.mean([i["t_refine_ms"] for i in infos]))},
             "iterations": info["iterations"], "refine_iterations": info["refine_iterations"],
+            "jacobi_sweeps": info["jacobi_sweeps"],
             "refine_steps": info["refine_steps"],
             "rank": info["rank"], "s": s,
             "roofline": roofline,

@@ -141,6 +141,8 @@ typedef struct {
   float t_sketch_gemm_ms;         /* tensor-core GEMM kernels inside the sketch (0 otherwise) */
   float t_pass_ms;                /* fused HBM passes over A in the main sweep (sum) */
   int32_t n_pass;                 /* number of those passes */
+  float t_qr_ms;                  /* Householder QR of the sketch inside t_precond_ms */
+  int32_t jacobi_sweeps;          /* one-sided Jacobi sweeps of the preconditioner */
 } lsrn_info;
 
 typedef struct lsrn_plan_s* lsrn_plan_t;

@@ -65,7 +65,8 @@ class lsrn_info(ctypes.Structure):
                 ("anorm_est", ctypes.c_double), ("t_sketch_ms", ctypes.c_float),
                 ("t_precond_ms", ctypes.c_float), ("t_iter_ms", ctypes.c_float),
                 ("t_refine_ms", ctypes.c_float), ("t_sketch_gemm_ms", ctypes.c_float),
-                ("t_pass_ms", ctypes.c_float), ("n_pass", ctypes.c_int32)]
+                ("t_pass_ms", ctypes.c_float), ("n_pass", ctypes.c_int32),
+                ("t_qr_ms", ctypes.c_float), ("jacobi_sweeps", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -357,6 +357,7 @@ lsrn_status run_precond(Plan* p) {
     launch(hh_update_kernel, grid, 128, 0, st, X, S, Q, k, rpb, (int)nrb, wpart, p->tau);
   }
   LSRN_CUDA_TRY(cudaGetLastError());
+  cudaEventRecord(p->ev[8], st);
   // 2. One-sided Jacobi on the rows of R.
   const int64_t QQ = Q * Q;
   launch(extract_r_kernel, (unsigned)((QQ + 255) / 256), 256, 0, st, X, Q, p->Wj);

@@ -425,6 +425,10 @@ lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
   LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[3]));
   cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
   cudaEventElapsedTime(&p->t_precond_ms, p->ev[2], p->ev[3]);
+  if (cudaEventElapsedTime(&p->t_qr_ms, p->ev[2], p->ev[8]) != cudaSuccess) {
+    cudaGetLastError();
+    p->t_qr_ms = 0.f;
+  }
   p->t_sketch_gemm_ms = 0.f;
   for (auto& pr : p->gemm_events) {
     float ms = 0.f;
@@ -456,6 +460,8 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   inf.sigma_min_sketch = p->sigma_min;
   inf.t_sketch_ms = p->t_sketch_ms;
   inf.t_precond_ms = p->t_precond_ms;
+  inf.t_qr_ms = p->t_qr_ms;
+  inf.jacobi_sweeps = p->sweeps;
   inf.t_sketch_gemm_ms = p->t_sketch_gemm_ms;
   lsrn_status result = LSRN_OK;
   const bool xdev = is_device_pointer(x);

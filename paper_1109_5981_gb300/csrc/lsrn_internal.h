@@ -144,11 +144,11 @@ struct Plan {
   double* pvec2 = nullptr;          // second partial buffer (double-double low parts)
   double* pscal = nullptr;          // (nblk + 1) scalar partials
   int nblk = 0;                     // CTAs of the fused pass
-  cudaEvent_t ev[8] = {nullptr};
+  cudaEvent_t ev[9] = {nullptr};   // [8]: end of the QR inside the preconditioner
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gemm_events;   // tensor-core GEMM launches
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;   // fused passes of the main sweep
   bool time_passes = false;
-  float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0;
+  float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0, t_qr_ms = 0;
 };
 
 // ---- kernels (launchers) -------------------------------------------------
