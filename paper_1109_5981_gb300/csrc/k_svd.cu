@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
   }
   double* wa = W + (int64_t)a * Q;
   double* wb = W + (int64_t)b * Q;
+  const double aa = nrm2[a], bb = nrm2[b];   // issued with the row loads
   double x[EPT], y[EPT];
   double ab = 0.0;
 #pragma unroll
@@ -208,7 +209,6 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
     ab = fma(x[e], y[e], ab);
   }
   ab = jac_block_sum(ab, sh);
-  const double aa = nrm2[a], bb = nrm2[b];
   if (aa == 0.0 || bb == 0.0) return;
   if (fabs(ab) <= tol * sqrt(aa) * sqrt(bb)) return;
   const double zeta = (bb - aa) / (2.0 * ab);
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
   if (threadIdx.x == 0) {
     nrm2[a] = na;
     nrm2[b] = nb;
-    atomicAdd(rot_count, 1);
+    *rot_count = 1;   // "some pair rotated in this sweep" (every writer stores 1)
   }
 }
 
