@@ -210,16 +210,26 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
   }
   ab = jac_block_sum(ab, sh);
   if (aa == 0.0 || bb == 0.0) return;
-  if (fabs(ab) <= tol * sqrt(aa) * sqrt(bb)) return;
-  const double zeta = (bb - aa) / (2.0 * ab);
-  double tt;
-  if (fabs(zeta) > 1e150) {
-    tt = 0.5 / zeta;
-  } else {
-    tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  // the angle (square roots and divisions, ~70 FP64 operations) once per pair
+  __shared__ double rot[3];
+  if (threadIdx.x == 0) {
+    double tt = 0.0, cs = 1.0;
+    if (fabs(ab) > tol * sqrt(aa) * sqrt(bb)) {
+      const double zeta = (bb - aa) / (2.0 * ab);
+      if (fabs(zeta) > 1e150) {
+        tt = 0.5 / zeta;
+      } else {
+        tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      }
+      cs = 1.0 / sqrt(1.0 + tt * tt);
+    }
+    rot[0] = tt;
+    rot[1] = cs;
+    rot[2] = cs * tt;
   }
-  const double cs = 1.0 / sqrt(1.0 + tt * tt);
-  const double sn = cs * tt;
+  __syncthreads();
+  const double tt = rot[0], cs = rot[1], sn = rot[2];
+  if (tt == 0.0) return;   // converged pair (uniform)
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
