@@ -759,6 +759,324 @@ __global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
   }
 }
 
+// ---- triple-float residual pass (refinement in iteration mode LSRN_ITER_F32X2) ----
+// With a third plane X3 = fl32(X / xs - Xh - Xl), Xh + Xl + X3 equals X / xs
+// exactly (X3 holds the last <= 6 bits).  The refinement's residual pass
+// r_i = b_i - X_i . v (m >= n) and g = sum_i t_i X_i then runs on the FP32 pipe:
+// every product of two exact three-float values keeps its terms down to
+// 2^-48 of the leading product (TwoProd for the two leading weights), sums are
+// TwoSum chains into three-float accumulators, and column sums are folded into
+// double-double every kFoldRows rows.  The result matches the FP64
+// double-double pass to ~2^-65 of sum |terms|.
+__device__ __forceinline__ void split_tf(double v, float& a, float& b, float& c) {
+  a = __double2float_rn(v);
+  const double r = v - (double)a;
+  b = __double2float_rn(r);
+  c = __double2float_rn(r - (double)b);
+}
+// (h, m, l) += (a1 + a2 + a3)(b1 + b2 + b3), terms below 2^-48 of a1 b1 dropped
+__device__ __forceinline__ void tf_fma(float a1, float a2, float a3, float b1, float b2, float b3,
+                                       float& h, float& m, float& l) {
+  const float p0 = a1 * b1;
+  const float e0 = fmaf(a1, b1, -p0);
+  const float p1 = a1 * b2;
+  const float e1 = fmaf(a1, b2, -p1);
+  const float p2 = a2 * b1;
+  const float e2 = fmaf(a2, b1, -p2);
+  const float q = fmaf(a1, b3, fmaf(a2, b2, fmaf(a3, b1, e1 + e2)));
+  float s, c, t, d;
+  two_sum_f(h, p0, s, c);
+  h = s;
+  two_sum_f(m, p1, t, d);
+  m = t;
+  l += d;
+  two_sum_f(m, p2, t, d);
+  m = t;
+  l += d;
+  two_sum_f(m, e0, t, d);
+  m = t;
+  l += d;
+  two_sum_f(m, c, t, d);
+  m = t;
+  l += d + q;
+}
+__device__ __forceinline__ void tf_combine(float& h, float& m, float& l, float oh, float om, float ol) {
+  float s, c, t, d, d2;
+  two_sum_f(h, oh, s, c);
+  h = s;
+  two_sum_f(m, om, t, d);
+  two_sum_f(t, c, m, d2);
+  l += ol + d + d2;
+}
+// (h + m + l) as double-double
+__device__ __forceinline__ void tf_to_dd(float h, float m, float l, double& dh, double& dl) {
+  two_sum((double)h, (double)m, dh, dl);
+  dd_add(dh, dl, (double)l, 0.0);
+}
+
+template <int SLOTS, int RB>
+__global__ void __launch_bounds__(kX2Threads, 1) dd_pass_x3_kernel(
+    const float* __restrict__ Xh, const float* __restrict__ Xl, const float* __restrict__ X3,
+    int64_t rows, int C, int64_t ldx, double xs, const double* __restrict__ vin,
+    const double* __restrict__ rowvec, double sx, int tall, double* __restrict__ rout,
+    double* __restrict__ phi, double* __restrict__ plo, int* __restrict__ err, int planebytes,
+    int nstages) {
+  static_assert(RB * (kThreads / 32) <= 32, "one coefficient-warp lane per (row, warp) partial");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ float redh[2][RB][kThreads / 32], redm[2][RB][kThreads / 32], redl[2][RB][kThreads / 32];
+  __shared__ float tc1[2][RB], tc2[2][RB], tc3[2][RB];
+  __shared__ int texp[2];
+  __shared__ int vexp[kThreads / 32];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const bool coef_warp = tid >= kThreads;
+  const int stage_bytes = 3 * RB * planebytes;   // RB rows of Xh, of Xl, of X3
+  double* state = (double*)(smem + (size_t)nstages * stage_bytes);   // [nstages][RB]
+  const int rstride = planebytes / (int)sizeof(float);
+  double vv[SLOTS][2];
+  int ve = kNoExp;
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int c = 2 * tid + 2 * kThreads * s + e;
+      vv[s][e] = (!coef_warp && tall && c < C) ? vin[c] : 0.0;
+      ve = max(ve, exp_of(vv[s][e]));
+    }
+  for (int o = 16; o > 0; o >>= 1) ve = max(ve, __shfl_xor_sync(0xffffffffu, ve, o));
+  if (!coef_warp && (tid & 31) == 0) vexp[tid >> 5] = ve;
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < nstages; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_u32(&bars[st])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  ve = kNoExp;
+  for (int q = 0; q < kThreads / 32; ++q) ve = max(ve, vexp[q]);
+  if (ve == kNoExp) ve = 0;
+  const double dscale = ldexp(xs, ve);
+  const int64_t nrb = (rows + RB - 1) / RB;
+  const int64_t my_n = blockIdx.x < nrb ? (nrb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  int64_t issued_upto = -1, waited_upto = -1;
+  auto issue = [&](int64_t kk) {
+    if (tid != 0 || kk >= my_n || abort_flag != 0) return;
+    issued_upto = kk;
+    const int st = (int)(kk % nstages);
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    const int nr = (int)min((int64_t)RB, rows - r0);
+    const uint32_t sbytes = (uint32_t)(((nr * 8) + 15) / 16 * 16);
+    const uint32_t bytes = 3u * (uint32_t)nr * planebytes + sbytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_u32(&bars[st])),
+                 "r"(bytes)
+                 : "memory");
+    unsigned char* dst = smem + (size_t)st * stage_bytes;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int r = 0; r < nr; ++r) {
+      bulk_copy(dst + (size_t)r * planebytes, Xh + (r0 + r) * ldx, (uint32_t)planebytes, &bars[st]);
+      bulk_copy(dst + (size_t)(RB + r) * planebytes, Xl + (r0 + r) * ldx, (uint32_t)planebytes,
+                &bars[st]);
+      bulk_copy(dst + (size_t)(2 * RB + r) * planebytes, X3 + (r0 + r) * ldx,
+                (uint32_t)planebytes, &bars[st]);
+    }
+    bulk_copy(state + (size_t)st * RB, rowvec + r0, sbytes, &bars[st]);
+  };
+  int E = kNoExp;
+
+  if (coef_warp) {
+    const int lane = tid - kThreads;
+    const int rq = lane / (kThreads / 32), qq = lane % (kThreads / 32);
+    for (int64_t kk = 0; kk < my_n; ++kk) {
+      const int par = (int)(kk & 1);
+      named_sync(kBarDot + par, kX2Threads);
+      const int st = (int)(kk % nstages);
+      const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+      const int nr = (int)min((int64_t)RB, rows - r0);
+      const bool aborted = abort_flag != 0;
+      if (!aborted) bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1));
+      float h = 0.0f, m = 0.0f, l = 0.0f;
+      if (tall && rq < RB) {
+        h = redh[par][rq][qq];
+        m = redm[par][rq][qq];
+        l = redl[par][rq][qq];
+      }
+#pragma unroll
+      for (int o = (kThreads / 32) / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float om = __shfl_xor_sync(0xffffffffu, m, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        tf_combine(h, m, l, oh, om, ol);
+      }
+      double t = 0.0;
+      const bool owner = qq == 0 && rq < nr && !aborted;
+      if (owner) {
+        const double sv = state[(size_t)st * RB + rq];
+        if (tall) {
+          double dh, dl;
+          tf_to_dd(h, m, l, dh, dl);
+          double rh = sv, rl = 0.0;
+          dd_add(rh, rl, -dscale * dh, -dscale * dl);
+          t = rh + rl;
+          rout[r0 + rq] = t;
+        } else {
+          t = sx * sv;
+        }
+      }
+      int me = exp_of(t);
+      for (int o = 16; o > 0; o >>= 1) me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
+      if (me != kNoExp && (E == kNoExp || me > E + 60)) E = me;
+      if (qq == 0 && rq < RB) {
+        float a = 0.0f, b = 0.0f, c = 0.0f;
+        if (owner && E != kNoExp) split_tf(ldexp(t, -E), a, b, c);
+        tc1[par][rq] = a;
+        tc2[par][rq] = b;
+        tc3[par][rq] = c;
+      }
+      if (lane == 0) texp[par] = E;
+      __threadfence_block();
+      named_arrive(kBarCoef + par, kX2Threads);
+    }
+    return;
+  }
+
+  float v1[SLOTS][2], v2[SLOTS][2], v3[SLOTS][2];
+  float wh[SLOTS][2], wm[SLOTS][2], wl[SLOTS][2];
+  double gh[SLOTS][2], gl[SLOTS][2];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      split_tf(ldexp(vv[s][e], -ve), v1[s][e], v2[s][e], v3[s][e]);
+      wh[s][e] = wm[s][e] = wl[s][e] = 0.0f;
+      gh[s][e] = gl[s][e] = 0.0;
+    }
+  double escale = 0.0;
+  int since_fold = 0;
+  auto fold = [&]() {
+    if (E != kNoExp) {
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          double dh, dl;
+          tf_to_dd(wh[s][e], wm[s][e], wl[s][e], dh, dl);
+          dd_add(gh[s][e], gl[s][e], escale * dh, escale * dl);
+          wh[s][e] = wm[s][e] = wl[s][e] = 0.0f;
+        }
+    }
+    since_fold = 0;
+  };
+  auto accumulate = [&](int64_t kk) {
+    const int par = (int)(kk & 1);
+    named_sync(kBarCoef + par, kX2Threads);
+    const int En = texp[par];
+    if (En != E) {
+      fold();
+      E = En;
+      escale = ldexp(xs, E);
+    }
+    const int st = (int)(kk % nstages);
+    const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
+    const float* lp = hp + (size_t)RB * rstride;
+    const float* tp = hp + (size_t)2 * RB * rstride;
+    const int nr = (int)min((int64_t)RB, rows - (blockIdx.x + kk * gridDim.x) * RB);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      if (r >= nr) break;
+      const float t1 = tc1[par][r], t2 = tc2[par][r], t3 = tc3[par][r];
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int c = 2 * tid + 2 * kThreads * s;
+        if (c < C) {
+          const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
+          const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
+          const float2 d = *reinterpret_cast<const float2*>(tp + (size_t)r * rstride + c);
+          tf_fma(t1, t2, t3, a.x, b.x, d.x, wh[s][0], wm[s][0], wl[s][0]);
+          tf_fma(t1, t2, t3, a.y, b.y, d.y, wh[s][1], wm[s][1], wl[s][1]);
+        }
+      }
+    }
+    since_fold += RB;
+    if (since_fold >= kFoldRows) fold();
+  };
+  for (int kk = 0; kk < nstages; ++kk) issue(kk);
+  for (int64_t kk = 0; kk < my_n; ++kk) {
+    const int par = (int)(kk & 1);
+    const int st = (int)(kk % nstages);
+    const int64_t r0 = (blockIdx.x + kk * gridDim.x) * RB;
+    const int nr = (int)min((int64_t)RB, rows - r0);
+    bool have = abort_flag == 0;
+    if (have && !bar_wait(&bars[st], (uint32_t)((kk / nstages) & 1))) {
+      abort_flag = 1;
+      have = false;
+    }
+    if (have && tid == 0) waited_upto = kk;
+    if (tall) {
+      const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
+      const float* lp = hp + (size_t)RB * rstride;
+      const float* tp = hp + (size_t)2 * RB * rstride;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        float h = 0.0f, m = 0.0f, l = 0.0f;
+        if (have && r < nr) {
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            const int c = 2 * tid + 2 * kThreads * s;
+            if (c < C) {
+              const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
+              const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
+              const float2 d = *reinterpret_cast<const float2*>(tp + (size_t)r * rstride + c);
+              tf_fma(a.x, b.x, d.x, v1[s][0], v2[s][0], v3[s][0], h, m, l);
+              tf_fma(a.y, b.y, d.y, v1[s][1], v2[s][1], v3[s][1], h, m, l);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+          const float om = __shfl_xor_sync(0xffffffffu, m, o);
+          const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+          tf_combine(h, m, l, oh, om, ol);
+        }
+        if ((tid & 31) == 0) {
+          redh[par][r][tid >> 5] = h;
+          redm[par][r][tid >> 5] = m;
+          redl[par][r][tid >> 5] = l;
+        }
+      }
+    }
+    __threadfence_block();
+    named_arrive(kBarDot + par, kX2Threads);
+    if (kk >= 1) {
+      accumulate(kk - 1);
+      named_sync(kBarFree, kThreads);
+      issue(kk - 1 + nstages);
+    }
+  }
+  if (my_n >= 1) accumulate(my_n - 1);
+  if (tid == 0 && abort_flag != 0) {
+    atomicExch(err, 1);
+    for (int64_t q = waited_upto + 1; q <= issued_upto; ++q)
+      bar_wait(&bars[q % nstages], (uint32_t)((q / nstages) & 1));
+  }
+  fold();
+  double* oh = phi + (int64_t)blockIdx.x * C;
+  double* ol = plo + (int64_t)blockIdx.x * C;
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int c = 2 * tid + 2 * kThreads * s;
+    if (c < C) {
+      oh[c] = gh[s][0];
+      ol[c] = gl[s][0];
+    }
+    if (c + 1 < C) {
+      oh[c + 1] = gh[s][1];
+      ol[c + 1] = gl[s][1];
+    }
+  }
+}
+
 // Rows appended to X by the Tikhonov augmentation: row (xrows + j) = coef * e_j.
 // Writes one extra partial slot (vector of length C and one scalar).
 __global__ void extra_rows_kernel(int64_t nextra, int64_t xrows, int C, double coef,
@@ -1031,22 +1349,26 @@ __global__ void maxabs_kernel(const double* __restrict__ X, int64_t rows, int64_
   }
 }
 
-// Xh = fl32(X * inv), Xl = fl32(X * inv - Xh); zero padding for j >= cols.
+// Xh = fl32(X * inv), Xl = fl32(X * inv - Xh), X3 = fl32(X * inv - Xh - Xl) (exact);
+// zero padding for j >= cols.
 __global__ void to_x2_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                              double inv, float* __restrict__ Yh, float* __restrict__ Yl,
-                             int64_t ldy) {
+                             float* __restrict__ Y3, int64_t ldy) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * ldy) return;
   const int64_t i = idx / ldy, j = idx % ldy;
   const double v = j < cols ? X[i * ldx + j] * inv : 0.0;
   const float h = __double2float_rn(v);
+  const double r = v - (double)h;
+  const float l = __double2float_rn(r);
   Yh[idx] = h;
-  Yl[idx] = __double2float_rn(v - (double)h);
+  Yl[idx] = l;
+  Y3[idx] = __double2float_rn(r - (double)l);
 }
 }  // namespace
 
 lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Yh,
-                         float* Yl, int64_t ldy, unsigned long long* maxbits, double* xs,
+                         float* Yl, float* Y3, int64_t ldy, unsigned long long* maxbits, double* xs,
                          cudaStream_t st) {
   const int64_t tot = rows * ldy;
   *xs = 1.0;
@@ -1064,7 +1386,7 @@ lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ld
   // and elements below 2^-126 of the largest are the only ones that lose bits
   if (mx > 0.0 && std::isfinite(mx)) *xs = std::ldexp(1.0, std::ilogb(mx));
   launch(to_x2_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, X, rows, cols, ldx,
-         1.0 / *xs, Yh, Yl, ldy);
+         1.0 / *xs, Yh, Yl, Y3, ldy);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }
@@ -1258,6 +1580,38 @@ lsrn_status launch_row_coef_extra(const Plan* p, const double* vin, const RowArg
 lsrn_status csr_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
                         double* phi, double* plo, double* tbuf);
 
+// Geometry of the triple-float residual pass: RB rows of the three planes per
+// stage (RB = 4 up to 1024 columns, 2 above), at least three stages in 196 KB.
+static bool x3_geometry(int64_t C, int64_t ldx2, int* planebytes, int* rb, int* nstages) {
+  if (C <= 512 || C > 4096) return false;
+  const int64_t pbytes = (C * 4 + 15) / 16 * 16;
+  if (pbytes > ldx2 * 4 || (ldx2 * 4) % 16 != 0) return false;
+  const int r = C <= 1024 ? 4 : 2;
+  const int64_t stage = 3 * r * pbytes + ((int64_t)r * 8 + 15) / 16 * 16;
+  const int ns = (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / stage);
+  if (ns < 3) return false;
+  *planebytes = (int)pbytes;
+  *rb = r;
+  *nstages = ns;
+  return true;
+}
+
+template <int SLOTS, int RB>
+static lsrn_status launch_x3(const Plan* p, const double* vin, const double* rowvec, bool tall,
+                             double* rout, double* phi, double* plo, int planebytes, int nstages) {
+  const size_t stage = (size_t)3 * RB * planebytes + ((size_t)RB * 8 + 15) / 16 * 16;
+  // the state region is indexed [stage][RB]: its size rounds each stage's RB doubles up
+  const size_t smem = (size_t)nstages * 3 * RB * planebytes + (size_t)nstages * RB * sizeof(double) + 16;
+  (void)stage;
+  auto kern = dd_pass_x3_kernel<SLOTS, RB>;
+  LSRN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  launch(kern, dim3(p->nblk), dim3(kX2Threads), smem, p->stream, p->X2h, p->X2l, p->X3, p->xrows,
+         (int)p->xcols, p->ldx2, p->x2scale, vin, rowvec, p->xscale, tall ? 1 : 0, rout, phi, plo,
+         p->iscal + IC_PASSERR, planebytes, nstages);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
 lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
                            double* pvec_hi, double* pvec_lo, const int* done) {
   (void)done;
@@ -1275,6 +1629,25 @@ lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec,
   int tpr, slots;
   if (pick_layout(p->xcols, &tpr, &slots) != 0) return LSRN_ERR_UNSUPPORTED;
   const int C = (int)p->xcols;
+  int pb = 0, rb = 0, ns = 0;
+  if (p->X3 != nullptr && x3_geometry(C, p->ldx2, &pb, &rb, &ns)) {
+    const bool tall = bvec != nullptr;
+    const double* rowvec = tall ? bvec : vin;
+    lsrn_status st = LSRN_ERR_UNSUPPORTED;
+    if (slots == 2 && rb == 4) st = launch_x3<2, 4>(p, vin, rowvec, tall, rout, pvec_hi, pvec_lo, pb, ns);
+    else if (slots == 4 && rb == 2) st = launch_x3<4, 2>(p, vin, rowvec, tall, rout, pvec_hi, pvec_lo, pb, ns);
+    else if (slots == 8 && rb == 2) st = launch_x3<8, 2>(p, vin, rowvec, tall, rout, pvec_hi, pvec_lo, pb, ns);
+    if (st != LSRN_ERR_UNSUPPORTED) {
+      LSRN_TRY(st);
+      if (p->extra_rows > 0) {
+        launch(dd_extra_kernel, (unsigned)((p->xcols + 255) / 256), 256, 0, p->stream,
+               p->extra_rows, p->xrows, C, p->extra_coef, vin, tall, rout,
+               pvec_hi + (int64_t)p->nblk * C, pvec_lo + (int64_t)p->nblk * C);
+      }
+      LSRN_CUDA_TRY(cudaGetLastError());
+      return LSRN_OK;
+    }
+  }
   dim3 grid(p->nblk);
 #define LSRN_DDPASS(T, S)                                                                       \
   launch(dd_pass_kernel<T, S>, grid, kThreads, 0, p->stream, p->X, p->xrows, C, p->ldx, vin, bvec,   \

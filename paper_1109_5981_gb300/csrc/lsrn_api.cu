@@ -164,7 +164,7 @@ static lsrn_status plan_workspace(Plan* p) {
   LSRN_TRY(dalloc_n(p, &p->tmpq, q));
   for (auto& v : p->vr) LSRN_TRY(dalloc_n(p, &v, q));
   LSRN_TRY(dalloc_n(p, &p->xfull, std::max(q, p->nstate)));
-  LSRN_TRY(dalloc_n(p, &p->bdev, std::max<int64_t>(p->m, 1)));
+  LSRN_TRY(dalloc_n(p, &p->bdev, std::max<int64_t>(p->m, 1) + 2));   // + 2: 16-byte bulk copies
   LSRN_TRY(dalloc_n(p, &p->pvec, (int64_t)(p->nblk + 1) * p->xcols));
   LSRN_TRY(dalloc_n(p, &p->pvec2, (int64_t)(p->nblk + 1) * p->xcols));
   LSRN_TRY(dalloc_n(p, &p->pscal, std::max<int64_t>(p->nblk + 1, 8 * (int64_t)num_sms() + 2)));
@@ -344,16 +344,18 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   }
   if (st == LSRN_OK && o.iter_mode == LSRN_ITER_F32X2 && !p->csr && x2_applies(p->xcols)) {
     p->ldx2 = (p->xcols + 3) / 4 * 4;
-    float *xh = nullptr, *xl = nullptr;
+    float *xh = nullptr, *xl = nullptr, *x3 = nullptr;
     unsigned long long* mb = nullptr;
     st = dalloc_n(p, &xh, p->xrows * p->ldx2);
     if (st == LSRN_OK) st = dalloc_n(p, &xl, p->xrows * p->ldx2);
+    if (st == LSRN_OK) st = dalloc_n(p, &x3, p->xrows * p->ldx2);
     if (st == LSRN_OK) st = dalloc_n(p, &mb, 1);
     if (st == LSRN_OK)
-      st = launch_to_x2(p->X, p->xrows, p->xcols, p->ldx, xh, xl, p->ldx2, mb, &p->x2scale,
+      st = launch_to_x2(p->X, p->xrows, p->xcols, p->ldx, xh, xl, x3, p->ldx2, mb, &p->x2scale,
                         p->stream);
     p->X2h = xh;
     p->X2l = xl;
+    p->X3 = x3;
   }
   if (st == LSRN_OK) st = plan_workspace(p);
   if (st == LSRN_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LSRN_ERR_CUDA;

@@ -102,6 +102,7 @@ struct Plan {
   bool pass_f32 = false;            // fused passes currently stream X32
   const float* X2h = nullptr;       // double-float planes of X / x2scale (LSRN_ITER_F32X2)
   const float* X2l = nullptr;
+  const float* X3 = nullptr;        // third plane: X / x2scale = X2h + X2l + X3 exactly
   int64_t ldx2 = 0;
   double x2scale = 1.0;
 
@@ -208,7 +209,7 @@ lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, 
 // Y (rows x ldy, FP32, zero beyond cols) = X (rows x cols, FP64, ldx)
 bool x2_applies(int64_t C);
 lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Yh,
-                         float* Yl, int64_t ldy, unsigned long long* maxbits, double* xs,
+                         float* Yl, float* Y3, int64_t ldy, unsigned long long* maxbits, double* xs,
                          cudaStream_t st);
 lsrn_status launch_to_f32(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
                           int64_t ldy, cudaStream_t st);
