@@ -50,7 +50,7 @@ def parse(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solver", default="lsqr", choices=["lsqr", "cs"])
     ap.add_argument("--sketch", default="tc", choices=["f64", "tc"])
-    ap.add_argument("--iter", default="f64", choices=["f64", "f32", "x2"])
+    ap.add_argument("--iter", default="x2", choices=["f64", "f32", "x2"])
     ap.add_argument("--m", type=int, default=M)
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--rank", type=int, default=RANK)
@@ -392,7 +392,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"x2": "f32x2 passes, f32x3 residual, f64 SVD/recurrences",
+                      "f32": "f32 passes, f64 SVD/recurrences/residual",
+                      "f64": "f64"}[args.iter],
             "data": "synthetic (seeded generator, no dataset)",
             "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, cond 1e6, "
                                    f"noise 1e-4, gamma 2, {args.solver.upper()} tol 1e-14 + "
