@@ -10,13 +10,14 @@
 // 2^24 and is exact too.  Products of equal weight form eight groups
 //   g = 0:  h d_1;   g >= 1:  h d_{g+1} + g_lo d_g,     weight 2^(e_j - 11 - 8 g)
 // (g_lo d_8, at most 2^(e_j - 61) per row, is dropped).  Each group is accumulated
-// exactly in TMEM over a chunk of 512 rows, then folded into FP64 registers;
-// chunk results of all groups are summed in FP64, i.e. the rounding is that of
-// an FP64 sum of a few thousand terms, while the multiplications run on the
-// tensor cores.
+// exactly in TMEM over a chunk of 512 rows; the chunk's group sums (integers
+// below 2^24) are added exactly into two int64 accumulators per column, so
+// the only rounding of the whole segment is the final conversion to FP64,
+// while the multiplications run on the tensor cores.
 //
 // Operands are split into digit planes in global memory one segment of rows at
-// a time (K-major, bf16), then a 128 x 64 output tile per CTA streams them
+// a time (K-major, bf16; the digits of X are cut from its 64-bit fixed-point
+// form with integer shifts), then a 128 x 64 output tile per CTA streams them
 // through a two-stage shared-memory pipeline (cp.async, 128B swizzle) into
 // tcgen05.mma (M=128, N=64, K=16, FP32 accumulators in TMEM, 8 x 64 columns).
 #include <algorithm>
@@ -32,10 +33,10 @@ namespace {
 constexpr int TC_M = 128;              // sketch rows per tile
 constexpr int TC_N = 64;               // columns of X per tile
 constexpr int TC_KT = 64;              // K per pipeline stage (one 128-byte swizzle row)
-constexpr int TC_CHUNK = 512;          // rows summed exactly in TMEM before the FP64 fold
+constexpr int TC_CHUNK = 512;          // rows summed exactly in TMEM before the int64 fold
 constexpr int TC_GROUPS = 8;
 constexpr int TC_DIGITS = 8;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;              // two warpgroups share the TMEM lane quadrants
 constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 16 KB
 constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 8 KB
 constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 96 KB
@@ -213,9 +214,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   const uint32_t tmem = *tmem_slot;
   constexpr uint32_t idesc = instr_desc(TC_M, TC_N);
 
-  double acc[TC_N];
+  // Exact column sums: group sums S_g (integers, |S_g| <= 2^24) of every chunk
+  // go into two int64 accumulators per column,
+  //   A1 += S_0 2^24 + S_1 2^16 + S_2 2^8 + S_3,  A2 += S_4 2^24 + ... + S_7,
+  // each below 2^48.01 per chunk (safe for 2^14 chunks); the value is
+  // A1 2^-24 + A2 2^-56.  Warpgroup h drains columns [32 h, 32 h + 32).
+  const int wg = warp >> 2;
+  long long a1[32], a2[32];
 #pragma unroll
-  for (int c = 0; c < TC_N; ++c) acc[c] = 0.0;
+  for (int c = 0; c < 32; ++c) a1[c] = a2[c] = 0;
 
   uint32_t phase[2] = {0u, 0u};
   bool pending[2] = {false, false};
@@ -280,30 +287,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
     }
     tc_fence_after();
     if (ok) {
-      const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+      const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
-      for (int g = 0; g < TC_GROUPS; ++g) {
-        const double w = ldexp(1.0, -8 * g);
+      for (int g = 0; g < 4; ++g) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(g * TC_N + wg * 32), v);
+        const long long w = 1ll << (24 - 8 * g);
 #pragma unroll
-        for (int cb = 0; cb < TC_N / 32; ++cb) {
-          float v[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(g * TC_N + cb * 32), v);
+        for (int c = 0; c < 32; ++c) a1[c] += (long long)__float2int_rn(v[c]) * w;   // exact
+      }
+#pragma unroll 1
+      for (int g = 4; g < TC_GROUPS; ++g) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(g * TC_N + wg * 32), v);
+        const long long w = 1ll << (24 - 8 * (g - 4));
 #pragma unroll
-          for (int c = 0; c < 32; ++c) acc[cb * 32 + c] = fma((double)v[c], w, acc[cb * 32 + c]);
-        }
+        for (int c = 0; c < 32; ++c) a2[c] += (long long)__float2int_rn(v[c]) * w;
       }
     }
     tc_fence_before();
     __syncthreads();
     kt = kt_end;
   }
-  // epilogue: row i0 + tid, columns j0 .. j0 + 63
-  const int64_t i = i0 + tid;
+  // epilogue: row i0 + 32 (warp % 4) + lane, columns j0 + 32 wg .. + 31
+  const int64_t i = i0 + (warp & 3) * 32 + (tid & 31);
   if (ok && i < S) {
 #pragma unroll
-    for (int c = 0; c < TC_N; ++c) {
-      const int64_t j = j0 + c;
-      if (j < Q) C[i * ldc + j] += ldexp(acc[c], col_exponent(ecol, j) - 11) * scale;
+    for (int c = 0; c < 32; ++c) {
+      const int64_t j = j0 + wg * 32 + c;
+      if (j < Q) {
+        const double v = fma((double)a2[c], 0x1p-56, (double)a1[c] * 0x1p-24);
+        C[i * ldc + j] += ldexp(v, col_exponent(ecol, j) - 11) * scale;
+      }
     }
   }
   tc_fence_before();
@@ -314,12 +329,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   }
 }
 
-// bf16 bit pattern of an integer |v| <= 128 (exact: at most 8 significant bits).
-__device__ __forceinline__ uint16_t bf16_int(double v) {
-  return (uint16_t)(__float_as_uint((float)v) >> 16);
+// Digit planes of X rows [l0, l0 + Ls): D[p][j][l - l0], transposed through shared memory.
+// y = X 2^(7 - e_j) (|y| < 128) is formed exactly as the 64-bit fixed-point
+// integer Y = y 2^56 (bits below 2^-56 are rounded off), and its balanced
+// base-256 digits are cut with integer shifts: d_1 = round(Y / 2^56),
+// Y -= d_1 2^56, d_2 = round(Y / 2^48), ..., d_8 = Y (|d_p| <= 128), so that
+// y = sum_p d_p 2^(8 - 8p) up to the rounding of Y.
+__device__ __forceinline__ long long fixed56(double x, int ej) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return 0;                       // zero (and subnormals, below 2^-1022)
+  long long mant = (long long)((bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int sh = ex - 1075 - ej + 63;           // Y = mant 2^sh
+  long long y;
+  if (sh >= 0) y = mant * (1ll << sh);          // |Y| < 2^63 since |x| < 2^e_j
+  else if (sh > -64) y = (mant + (1ll << (-sh - 1))) >> (-sh);
+  else y = 0;
+  return (bits >> 63) ? -y : y;
 }
 
-// Digit planes of X rows [l0, l0 + Ls): D[p][j][l - l0], transposed through shared memory.
 __global__ void __launch_bounds__(256) split_x_kernel(const double* __restrict__ X, int64_t l0,
                                                       int64_t l1, int64_t Q, int64_t ldx,
                                                       const int* __restrict__ ecol, int64_t Qp,
@@ -329,16 +357,14 @@ __global__ void __launch_bounds__(256) split_x_kernel(const double* __restrict__
   const int64_t jb = (int64_t)blockIdx.x * 32, lb = (int64_t)blockIdx.y * 32;
   for (int r = ty; r < 32; r += 8) {
     const int64_t l = l0 + lb + r, j = jb + tx;
-    double x = 0.0;
-    if (l < l1 && j < Q) x = ldexp(X[l * ldx + j], -col_exponent(ecol, j));
-    double d = rint(x * 128.0);
-    double rem = x * 128.0 - d;
-    tile[0][r][tx] = bf16_int(d);
+    long long y = 0;
+    if (l < l1 && j < Q) y = fixed56(X[l * ldx + j], col_exponent(ecol, j));
 #pragma unroll
-    for (int p = 1; p < TC_DIGITS; ++p) {
-      d = rint(rem * 256.0);
-      rem = rem * 256.0 - d;
-      tile[p][r][tx] = bf16_int(d);
+    for (int p = 0; p < TC_DIGITS; ++p) {
+      const int s = 56 - 8 * p;
+      const long long d = s > 0 ? ((y + (1ll << (s - 1))) >> s) : y;
+      y -= d * (1ll << s);
+      tile[p][r][tx] = (unsigned short)(__float_as_uint(__int2float_rn((int)d)) >> 16);
     }
   }
   __syncthreads();
@@ -412,6 +438,7 @@ int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_by
   const int64_t per_row = (2 * Sp + TC_DIGITS * Qp) * 2;
   int64_t rows = (int64_t)(budget_bytes / (size_t)std::max<int64_t>(per_row, 1));
   rows = std::max<int64_t>(TC_CHUNK, rows / TC_CHUNK * TC_CHUNK);
+  rows = std::min<int64_t>(rows, (int64_t)8192 * TC_CHUNK);   // int64 column sums stay exact
   const int64_t Lr = (L + TC_KT - 1) / TC_KT * TC_KT;
   return std::min(rows, Lr);
 }
