@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
 // integer Y = y 2^56 (bits below 2^-56 are rounded off), and its balanced
 // base-256 digits are cut with integer shifts: d_1 = round(Y / 2^56),
 // Y -= d_1 2^56, d_2 = round(Y / 2^48), ..., d_8 = Y (|d_p| <= 128), so that
-// y = sum_p d_p 2^(8 - 8p) up to the rounding of Y.
+// y = sum_p d_p 2^(8 - 8p) up to the rounding of Y.  |Y| may come within
+// 2^55 of 2^63, so rounding shifts before adding and the subtraction wraps.
 __device__ __forceinline__ long long fixed56(double x, int ej) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
@@ -362,8 +363,10 @@ __global__ void __launch_bounds__(256) split_x_kernel(const double* __restrict__
 #pragma unroll
     for (int p = 0; p < TC_DIGITS; ++p) {
       const int s = 56 - 8 * p;
-      const long long d = s > 0 ? ((y + (1ll << (s - 1))) >> s) : y;
-      y -= d * (1ll << s);
+      // round(y / 2^s) without forming y + 2^(s-1), which can exceed 2^63
+      const long long d = s > 0 ? (((y >> (s - 1)) + 1) >> 1) : y;
+      // |y - d 2^s| <= 2^(s-1): exact in modular arithmetic even when d 2^s = 2^63
+      y = (long long)((unsigned long long)y - ((unsigned long long)d << s));
       tile[p][r][tx] = (unsigned short)(__float_as_uint(__int2float_rn((int)d)) >> 16);
     }
   }

@@ -88,3 +88,17 @@ def test_tc_solve_householder_medium():
     x, info = L.solve(_dev(P.A), _dev(P.b), seed=1, sketch_mode=L.LSRN_SKETCH_TC_SLICED)
     assert info["rank"] == 270
     assert O.rel_err(x.cpu().numpy(), xf) <= 1e-10
+
+
+def test_tc_sketch_column_maxima_just_below_a_power_of_two():
+    # |X_lj| / 2^e_j close to 1 puts the fixed-point digit split at the edge of
+    # its 64-bit range (the first digit rounds to 128)
+    rng = np.random.Generator(np.random.PCG64(17))
+    A = rng.standard_normal((1500, 120))
+    for j in range(120):
+        k = 1 + j % 53
+        A[rng.integers(0, 1500), j] = (1.0 - 2.0 ** -k) * 2.0 ** (j % 7 - 3) * (-1) ** j
+    S = _tc_sketch(A, 4)
+    ref = _oracle_sketch(A, 4)
+    for j in range(120):
+        assert np.linalg.norm(S[:, j] - ref[:, j]) <= 1e-13 * np.linalg.norm(ref[:, j])
