@@ -1,7 +1,8 @@
 // Preconditioner (Algorithm 1 steps 4-5, Algorithm 2 steps 4-5) on the device.
 //
 // Input: the sketch Xs (S x Q, row-major, S > Q): A~ for m >= n, A~^T for m < n.
-// 1. Householder QR of Xs -> R (Q x Q upper triangular); Q is not formed.
+// 1. Householder QR of Xs -> R (Q x Q upper triangular), blocked in panels of
+//    32 columns with the compact WY form; Q is not formed.
 // 2. One-sided (Hestenes) Jacobi on Y = R^T: rotate pairs of columns of Y
 //    (= rows of R, contiguous in memory) until all pairs are orthogonal to
 //    |y_a . y_b| <= tol ||y_a|| ||y_b||; parallel round-robin ordering, one
@@ -19,78 +20,255 @@ namespace lsrn {
 
 namespace {
 
-// Reflector for column k: H = I - tau v v^T, v_k = 1, annihilates X[k+1:, k].
-__global__ void __launch_bounds__(256) hh_reflector_kernel(double* __restrict__ X, int64_t S,
-                                                           int64_t Q, int64_t k,
-                                                           double* __restrict__ tau) {
-  __shared__ double red[8];
-  __shared__ double s_scal;
+// ---- blocked Householder QR --------------------------------------------------
+// Panels of kQrNb columns: one CTA factors the panel in place (reflectors below
+// the diagonal with an implicit unit, R on and above it) and forms T of the
+// compact WY form H_k0 ... H_k0+nb-1 = I - V T V^T (T upper triangular).  The
+// trailing columns C = X[k0:S, k0+nb:Q] then get C <- C - V T^T (V^T C):
+// W = V^T C as per-chunk partial sums (row chunks of kQrChunk, summed in a
+// fixed order, so the result does not depend on scheduling), W2 = T^T W, and
+// the rank-nb update C -= V W2 tile by tile.
+constexpr int kQrNb = 32;
+constexpr int kQrPanelThreads = 512;
+constexpr int kQrChunk = 256;
+
+// V[r][i] of panel k0 (rows r >= k0 of X, i < nb): 1 on the diagonal, 0 above.
+__device__ __forceinline__ double qr_v(const double* X, int64_t Q, int64_t k0, int64_t r, int i) {
+  const int64_t k = k0 + i;
+  if (r < k) return 0.0;
+  if (r == k) return 1.0;
+  return X[r * Q + k];
+}
+
+__global__ void __launch_bounds__(kQrPanelThreads) qr_panel_kernel(double* __restrict__ X, int64_t S,
+                                                                    int64_t Q, int64_t k0, int nb,
+                                                                    double* __restrict__ tau,
+                                                                    double* __restrict__ T) {
+  __shared__ double red[kQrPanelThreads / 32][kQrNb];
+  __shared__ double vals[kQrNb];
+  __shared__ double Ts[kQrNb][kQrNb];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  for (int q = tid; q < kQrNb * kQrNb; q += kQrPanelThreads) Ts[q / kQrNb][q % kQrNb] = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    const int64_t k = k0 + j;
+    // 1. reflector for column k
+    double ss = 0.0;
+    for (int64_t r = k + 1 + tid; r < S; r += kQrPanelThreads) {
+      const double x = X[r * Q + k];
+      ss = fma(x, x, ss);
+    }
+    ss = group_sum<32>(ss);
+    if (lane == 0) red[wp][0] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kQrPanelThreads / 32; ++w) t += red[w][0];
+      const double alpha = X[k * Q + k];
+      double tk = 0.0, scal = 0.0;
+      if (t > 0.0) {
+        const double nrm = sqrt(alpha * alpha + t);
+        const double beta = alpha >= 0.0 ? -nrm : nrm;
+        tk = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+        X[k * Q + k] = beta;
+      }
+      tau[k] = tk;
+      vals[0] = tk;
+      vals[1] = scal;
+    }
+    __syncthreads();
+    const double tk = vals[0], scal = vals[1];
+    if (scal != 0.0)
+      for (int64_t r = k + 1 + tid; r < S; r += kQrPanelThreads) X[r * Q + k] *= scal;
+    __syncthreads();
+    // 2. apply H_k to the panel columns k+1 .. k0+nb-1
+    const int ncol = nb - j - 1;
+    if (ncol > 0 && tk != 0.0) {
+      double part[kQrNb];
+#pragma unroll
+      for (int c = 0; c < kQrNb; ++c) part[c] = 0.0;
+      for (int64_t r = k + tid; r < S; r += kQrPanelThreads) {
+        const double v = (r == k) ? 1.0 : X[r * Q + k];
+#pragma unroll
+        for (int c = 0; c < kQrNb; ++c)
+          if (c < ncol) part[c] = fma(v, X[r * Q + k + 1 + c], part[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < kQrNb; ++c) {
+        if (c < ncol) {
+          const double t = group_sum<32>(part[c]);
+          if (lane == 0) red[wp][c] = t;
+        }
+      }
+      __syncthreads();
+      if (tid < ncol) {
+        double t = 0.0;
+        for (int w = 0; w < kQrPanelThreads / 32; ++w) t += red[w][tid];
+        vals[tid] = tk * t;
+      }
+      __syncthreads();
+      for (int64_t r = k + tid; r < S; r += kQrPanelThreads) {
+        const double v = (r == k) ? 1.0 : X[r * Q + k];
+        for (int c = 0; c < ncol; ++c) X[r * Q + k + 1 + c] = fma(-v, vals[c], X[r * Q + k + 1 + c]);
+      }
+      __syncthreads();
+    }
+  }
+  // 3. T: T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j)
+  for (int j = 0; j < nb; ++j) {
+    double part[kQrNb];
+#pragma unroll
+    for (int c = 0; c < kQrNb; ++c) part[c] = 0.0;
+    for (int64_t r = k0 + j + tid; r < S; r += kQrPanelThreads) {
+      const double vj = qr_v(X, Q, k0, r, j);
+#pragma unroll
+      for (int c = 0; c < kQrNb; ++c)
+        if (c < j) part[c] = fma(qr_v(X, Q, k0, r, c), vj, part[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kQrNb; ++c) {
+      if (c < j) {
+        const double t = group_sum<32>(part[c]);
+        if (lane == 0) red[wp][c] = t;
+      }
+    }
+    __syncthreads();
+    if (tid < j) {
+      double t = 0.0;
+      for (int w = 0; w < kQrPanelThreads / 32; ++w) t += red[w][tid];
+      vals[tid] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double tj = tau[k0 + j];
+      for (int i = 0; i < j; ++i) {
+        double acc = 0.0;
+        for (int l = i; l < j; ++l) acc = fma(Ts[i][l], vals[l], acc);
+        Ts[i][j] = -tj * acc;
+      }
+      Ts[j][j] = tj;
+      for (int i = j + 1; i < kQrNb; ++i) Ts[i][j] = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < kQrNb * kQrNb; q += kQrPanelThreads) T[q] = Ts[q / kQrNb][q % kQrNb];
+}
+
+// Wpart[ch][i][c] = sum over rows r of chunk ch of V[r][i] C[r][c], c = trailing column
+// index (0 .. Q - k0 - nb), 64 columns per CTA, rows [k0 + ch kQrChunk, ...).
+__global__ void __launch_bounds__(256) qr_vtc_kernel(const double* __restrict__ X, int64_t S,
+                                                     int64_t Q, int64_t k0, int nb,
+                                                     double* __restrict__ Wpart) {
+  __shared__ double sv[32][kQrNb + 1];
+  __shared__ double sc[32][64 + 1];
   const int tid = threadIdx.x;
-  double ss = 0.0;
-  for (int64_t i = k + 1 + tid; i < S; i += 256) {
-    const double x = X[i * Q + k];
-    ss = fma(x, x, ss);
+  const int c = tid & 63, ib = tid >> 6;   // 4 blocks of 8 reflectors
+  const int64_t cbase = k0 + nb + (int64_t)blockIdx.x * 64;
+  const int64_t ncol_tr = Q - k0 - nb;
+  const int64_t r0 = k0 + (int64_t)blockIdx.y * kQrChunk;
+  const int64_t r1 = min(S, r0 + kQrChunk);
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (int64_t rs = r0; rs < r1; rs += 32) {
+    for (int q = tid; q < 32 * kQrNb; q += 256) {
+      const int rr = q / kQrNb, i = q % kQrNb;
+      const int64_t r = rs + rr;
+      sv[rr][i] = (r < r1 && i < nb) ? qr_v(X, Q, k0, r, i) : 0.0;
+    }
+    for (int q = tid; q < 32 * 64; q += 256) {
+      const int rr = q / 64, cc = q % 64;
+      const int64_t r = rs + rr, col = cbase + cc;
+      sc[rr][cc] = (r < r1 && col < Q) ? X[r * Q + col] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const double x = sc[rr][c];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = fma(sv[rr][ib * 8 + q], x, acc[q]);
+    }
+    __syncthreads();
   }
-  ss = group_sum<32>(ss);
-  if ((tid & 31) == 0) red[tid >> 5] = ss;
-  __syncthreads();
-  if (tid == 0) {
+  const int64_t col = (int64_t)blockIdx.x * 64 + c;
+  if (col < ncol_tr) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = ib * 8 + q;
+      Wpart[((int64_t)blockIdx.y * kQrNb + i) * ncol_tr + col] = acc[q];
+    }
+  }
+}
+
+// W2[:, c] = T^T (sum over chunks of Wpart[ch][:, c]), one thread per trailing column.
+__global__ void qr_w2_kernel(const double* __restrict__ Wpart, int nchunk, int64_t ncol_tr, int nb,
+                             const double* __restrict__ T, double* __restrict__ W2) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol_tr) return;
+  double w[kQrNb];
+#pragma unroll
+  for (int i = 0; i < kQrNb; ++i) w[i] = 0.0;
+  for (int ch = 0; ch < nchunk; ++ch) {
+#pragma unroll
+    for (int i = 0; i < kQrNb; ++i)
+      if (i < nb) w[i] += Wpart[((int64_t)ch * kQrNb + i) * ncol_tr + c];
+  }
+#pragma unroll
+  for (int j = 0; j < kQrNb; ++j) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    const double alpha = X[k * Q + k];
-    double tk = 0.0, scal = 0.0;
-    if (t > 0.0) {
-      const double nrm = sqrt(alpha * alpha + t);
-      const double beta = alpha >= 0.0 ? -nrm : nrm;
-      tk = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-      X[k * Q + k] = beta;
-    }
-    tau[k] = tk;
-    s_scal = scal;
+#pragma unroll
+    for (int i = 0; i <= j; ++i) t = fma(T[i * kQrNb + j], w[i], t);
+    if (j < nb) W2[(int64_t)j * ncol_tr + c] = t;
+  }
+}
+
+// C[r][c] -= sum_i V[r][i] W2[i][c] on a 64 x 64 tile (4 x 4 outputs per thread).
+__global__ void __launch_bounds__(256) qr_update_kernel(double* __restrict__ X, int64_t S, int64_t Q,
+                                                        int64_t k0, int nb,
+                                                        const double* __restrict__ W2) {
+  __shared__ double sv[64][kQrNb + 1];
+  __shared__ double sw[kQrNb][64 + 1];
+  const int tid = threadIdx.x;
+  const int64_t ncol_tr = Q - k0 - nb;
+  const int64_t ct = (int64_t)blockIdx.x * 64, rt = k0 + (int64_t)blockIdx.y * 64;
+  for (int q = tid; q < 64 * kQrNb; q += 256) {
+    const int rr = q / kQrNb, i = q % kQrNb;
+    const int64_t r = rt + rr;
+    sv[rr][i] = (r < S && i < nb) ? qr_v(X, Q, k0, r, i) : 0.0;
+  }
+  for (int q = tid; q < kQrNb * 64; q += 256) {
+    const int i = q / 64, cc = q % 64;
+    const int64_t col = ct + cc;
+    sw[i][cc] = (i < nb && col < ncol_tr) ? W2[(int64_t)i * ncol_tr + col] : 0.0;
   }
   __syncthreads();
-  const double scal = s_scal;
-  if (scal != 0.0)
-    for (int64_t i = k + 1 + tid; i < S; i += 256) X[i * Q + k] *= scal;
-}
-
-// wpart[rb][c] = sum_{i in row block rb, i >= k} v_i X[i, c] for c in (k, Q)
-__global__ void __launch_bounds__(128) hh_w_kernel(const double* __restrict__ X, int64_t S,
-                                                   int64_t Q, int64_t k, int64_t rpb,
-                                                   double* __restrict__ wpart,
-                                                   const double* __restrict__ tau) {
-  if (tau[k] == 0.0) return;
-  const int64_t c = k + 1 + (int64_t)blockIdx.x * 128 + threadIdx.x;
-  const int64_t r0 = k + (int64_t)blockIdx.y * rpb;
-  const int64_t r1 = min(S, r0 + rpb);
-  double acc = 0.0;
-  if (c < Q) {
-    for (int64_t i = r0; i < r1; ++i) {
-      const double v = (i == k) ? 1.0 : X[i * Q + k];
-      acc = fma(v, X[i * Q + c], acc);
-    }
-    wpart[(int64_t)blockIdx.y * Q + c] = acc;
+  const int tr = tid >> 4, tc = tid & 15;   // 16 x 16 threads, 4 x 4 outputs each
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll 8
+  for (int i = 0; i < kQrNb; ++i) {
+    double va[4], wb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) va[a] = sv[tr + 16 * a][i];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) wb[b] = sw[i][tc + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(va[a], wb[b], acc[a][b]);
   }
-}
-
-// X[i, c] -= tau v_i w_c with w_c = sum_rb wpart[rb][c]
-__global__ void __launch_bounds__(128) hh_update_kernel(double* __restrict__ X, int64_t S, int64_t Q,
-                                                        int64_t k, int64_t rpb, int nrb,
-                                                        const double* __restrict__ wpart,
-                                                        const double* __restrict__ tau) {
-  const double tk = tau[k];
-  if (tk == 0.0) return;
-  const int64_t c = k + 1 + (int64_t)blockIdx.x * 128 + threadIdx.x;
-  if (c >= Q) return;
-  double w = 0.0;
-  for (int b = 0; b < nrb; ++b) w += wpart[(int64_t)b * Q + c];
-  const double t = tk * w;
-  const int64_t r0 = k + (int64_t)blockIdx.y * rpb;
-  const int64_t r1 = min(S, r0 + rpb);
-  for (int64_t i = r0; i < r1; ++i) {
-    const double v = (i == k) ? 1.0 : X[i * Q + k];
-    X[i * Q + c] = fma(-v, t, X[i * Q + c]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t r = rt + tr + 16 * a;
+    if (r >= S) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t col = ct + tc + 16 * b;
+      if (col < ncol_tr) X[r * Q + k0 + nb + col] -= acc[a][b];
+    }
   }
 }
 
@@ -348,25 +526,32 @@ lsrn_status run_precond(Plan* p) {
   cudaStream_t st = p->stream;
   const int64_t S = p->s, Q = p->q;
   double* X = p->Xs;
-  // 1. Householder QR (one column at a time).
-  double* wpart = p->pvec;   // reuse pass partial buffer: needs nrb * Q doubles
-  const int64_t cap_rows = std::max<int64_t>(1, (int64_t)(p->nblk + 1) * p->xcols / std::max<int64_t>(Q, 1));
-  for (int64_t k = 0; k < Q; ++k) {
-    launch(hh_reflector_kernel, 1, 256, 0, st, X, S, Q, k, p->tau);
-    const int64_t ncols = Q - k - 1;
-    if (ncols <= 0) continue;
-    const int64_t cblk = (ncols + 127) / 128;
-    const int64_t rows = S - k;
-    int64_t nrb = std::max<int64_t>(1, (2 * num_sms() + cblk - 1) / cblk);
-    nrb = std::min<int64_t>(nrb, (rows + 63) / 64);
-    nrb = std::min<int64_t>(nrb, cap_rows);
-    const int64_t rpb = (rows + nrb - 1) / nrb;
-    nrb = (rows + rpb - 1) / rpb;
-    dim3 grid((unsigned)cblk, (unsigned)nrb);
-    launch(hh_w_kernel, grid, 128, 0, st, X, S, Q, k, rpb, wpart, p->tau);
-    launch(hh_update_kernel, grid, 128, 0, st, X, S, Q, k, rpb, (int)nrb, wpart, p->tau);
+  // 1. Householder QR, blocked: panels of kQrNb columns.
+  {
+    const int64_t max_chunks = (S + kQrChunk - 1) / kQrChunk;
+    const size_t ws = ((size_t)max_chunks * kQrNb * Q + (size_t)kQrNb * Q + kQrNb * kQrNb) *
+                      sizeof(double);
+    double* qws = nullptr;
+    LSRN_CUDA_TRY(cudaMallocAsync((void**)&qws, ws, st));
+    double* Wpart = qws;
+    double* W2 = Wpart + (size_t)max_chunks * kQrNb * Q;
+    double* Tm = W2 + (size_t)kQrNb * Q;
+    for (int64_t k0 = 0; k0 < Q; k0 += kQrNb) {
+      const int nb = (int)std::min<int64_t>(kQrNb, Q - k0);
+      launch(qr_panel_kernel, 1, kQrPanelThreads, 0, st, X, S, Q, k0, nb, p->tau, Tm);
+      const int64_t ncol_tr = Q - k0 - nb;
+      if (ncol_tr <= 0) continue;
+      const int nchunk = (int)((S - k0 + kQrChunk - 1) / kQrChunk);
+      launch(qr_vtc_kernel, dim3((unsigned)((ncol_tr + 63) / 64), (unsigned)nchunk), 256, 0, st,
+             (const double*)X, S, Q, k0, nb, Wpart);
+      launch(qr_w2_kernel, (unsigned)((ncol_tr + 127) / 128), 128, 0, st, (const double*)Wpart,
+             nchunk, ncol_tr, nb, (const double*)Tm, W2);
+      launch(qr_update_kernel, dim3((unsigned)((ncol_tr + 63) / 64), (unsigned)((S - k0 + 63) / 64)),
+             256, 0, st, X, S, Q, k0, nb, (const double*)W2);
+    }
+    LSRN_CUDA_TRY(cudaGetLastError());
+    cudaFreeAsync(qws, st);
   }
-  LSRN_CUDA_TRY(cudaGetLastError());
   cudaEventRecord(p->ev[8], st);
   // 2. One-sided Jacobi on the rows of R.
   const int64_t QQ = Q * Q;
