@@ -1,8 +1,9 @@
 // Preconditioner (Algorithm 1 steps 4-5, Algorithm 2 steps 4-5) on the device.
 //
 // Input: the sketch Xs (S x Q, row-major, S > Q): A~ for m >= n, A~^T for m < n.
-// 1. Householder QR of Xs -> R (Q x Q upper triangular), blocked in panels of
-//    32 columns with the compact WY form; Q is not formed.
+// 1. Householder QR of Xs -> R (Q x Q upper triangular); Q is not formed.  One
+//    column at a time up to 3000 columns, blocked in panels of 32 columns
+//    with the compact WY form beyond.
 // 2. One-sided (Hestenes) Jacobi on Y = R^T: rotate pairs of columns of Y
 //    (= rows of R, contiguous in memory) until all pairs are orthogonal to
 //    |y_a . y_b| <= tol ||y_a|| ||y_b||; parallel round-robin ordering, one
@@ -20,6 +21,81 @@ namespace lsrn {
 
 namespace {
 
+// Reflector for column k: H = I - tau v v^T, v_k = 1, annihilates X[k+1:, k].
+__global__ void __launch_bounds__(256) hh_reflector_kernel(double* __restrict__ X, int64_t S,
+                                                           int64_t Q, int64_t k,
+                                                           double* __restrict__ tau) {
+  __shared__ double red[8];
+  __shared__ double s_scal;
+  const int tid = threadIdx.x;
+  double ss = 0.0;
+  for (int64_t i = k + 1 + tid; i < S; i += 256) {
+    const double x = X[i * Q + k];
+    ss = fma(x, x, ss);
+  }
+  ss = group_sum<32>(ss);
+  if ((tid & 31) == 0) red[tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    const double alpha = X[k * Q + k];
+    double tk = 0.0, scal = 0.0;
+    if (t > 0.0) {
+      const double nrm = sqrt(alpha * alpha + t);
+      const double beta = alpha >= 0.0 ? -nrm : nrm;
+      tk = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+      X[k * Q + k] = beta;
+    }
+    tau[k] = tk;
+    s_scal = scal;
+  }
+  __syncthreads();
+  const double scal = s_scal;
+  if (scal != 0.0)
+    for (int64_t i = k + 1 + tid; i < S; i += 256) X[i * Q + k] *= scal;
+}
+
+// wpart[rb][c] = sum_{i in row block rb, i >= k} v_i X[i, c] for c in (k, Q)
+__global__ void __launch_bounds__(128) hh_w_kernel(const double* __restrict__ X, int64_t S,
+                                                   int64_t Q, int64_t k, int64_t rpb,
+                                                   double* __restrict__ wpart,
+                                                   const double* __restrict__ tau) {
+  if (tau[k] == 0.0) return;
+  const int64_t c = k + 1 + (int64_t)blockIdx.x * 128 + threadIdx.x;
+  const int64_t r0 = k + (int64_t)blockIdx.y * rpb;
+  const int64_t r1 = min(S, r0 + rpb);
+  double acc = 0.0;
+  if (c < Q) {
+    for (int64_t i = r0; i < r1; ++i) {
+      const double v = (i == k) ? 1.0 : X[i * Q + k];
+      acc = fma(v, X[i * Q + c], acc);
+    }
+    wpart[(int64_t)blockIdx.y * Q + c] = acc;
+  }
+}
+
+// X[i, c] -= tau v_i w_c with w_c = sum_rb wpart[rb][c]
+__global__ void __launch_bounds__(128) hh_update_kernel(double* __restrict__ X, int64_t S, int64_t Q,
+                                                        int64_t k, int64_t rpb, int nrb,
+                                                        const double* __restrict__ wpart,
+                                                        const double* __restrict__ tau) {
+  const double tk = tau[k];
+  if (tk == 0.0) return;
+  const int64_t c = k + 1 + (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (c >= Q) return;
+  double w = 0.0;
+  for (int b = 0; b < nrb; ++b) w += wpart[(int64_t)b * Q + c];
+  const double t = tk * w;
+  const int64_t r0 = k + (int64_t)blockIdx.y * rpb;
+  const int64_t r1 = min(S, r0 + rpb);
+  for (int64_t i = r0; i < r1; ++i) {
+    const double v = (i == k) ? 1.0 : X[i * Q + k];
+    X[i * Q + c] = fma(-v, t, X[i * Q + c]);
+  }
+}
+
 // ---- blocked Householder QR --------------------------------------------------
 // Panels of kQrNb columns: one CTA factors the panel in place (reflectors below
 // the diagonal with an implicit unit, R on and above it) and forms T of the
@@ -31,6 +107,7 @@ namespace {
 constexpr int kQrNb = 32;
 constexpr int kQrPanelThreads = 512;
 constexpr int kQrChunk = 256;
+constexpr int64_t kQrBlockedMin = 3000;   // columns from which the blocked QR is faster
 
 // V[r][i] of panel k0 (rows r >= k0 of X, i < nb): 1 on the diagonal, 0 above.
 __device__ __forceinline__ double qr_v(const double* X, int64_t Q, int64_t k0, int64_t r, int i) {
@@ -526,8 +603,31 @@ lsrn_status run_precond(Plan* p) {
   cudaStream_t st = p->stream;
   const int64_t S = p->s, Q = p->q;
   double* X = p->Xs;
-  // 1. Householder QR, blocked: panels of kQrNb columns.
-  {
+  // 1. Householder QR.  Up to kQrBlockedMin columns one column at a time (three
+  // launches per column, the trailing update spread over the whole GPU); beyond
+  // that in panels of kQrNb columns, where the O(S q^2) trailing work runs as a
+  // blocked rank-32 update and the serial panel factorizations are a small part.
+  if (Q <= kQrBlockedMin) {
+    double* wpart = p->pvec;   // reuse pass partial buffer: needs nrb * Q doubles
+    const int64_t cap_rows =
+        std::max<int64_t>(1, (int64_t)(p->nblk + 1) * p->xcols / std::max<int64_t>(Q, 1));
+    for (int64_t k = 0; k < Q; ++k) {
+      launch(hh_reflector_kernel, 1, 256, 0, st, X, S, Q, k, p->tau);
+      const int64_t ncols = Q - k - 1;
+      if (ncols <= 0) continue;
+      const int64_t cblk = (ncols + 127) / 128;
+      const int64_t rows = S - k;
+      int64_t nrb = std::max<int64_t>(1, (2 * num_sms() + cblk - 1) / cblk);
+      nrb = std::min<int64_t>(nrb, (rows + 63) / 64);
+      nrb = std::min<int64_t>(nrb, cap_rows);
+      const int64_t rpb = (rows + nrb - 1) / nrb;
+      nrb = (rows + rpb - 1) / rpb;
+      dim3 grid((unsigned)cblk, (unsigned)nrb);
+      launch(hh_w_kernel, grid, 128, 0, st, X, S, Q, k, rpb, wpart, p->tau);
+      launch(hh_update_kernel, grid, 128, 0, st, X, S, Q, k, rpb, (int)nrb, wpart, p->tau);
+    }
+    LSRN_CUDA_TRY(cudaGetLastError());
+  } else {
     const int64_t max_chunks = (S + kQrChunk - 1) / kQrChunk;
     const size_t ws = ((size_t)max_chunks * kQrNb * Q + (size_t)kQrNb * Q + kQrNb * kQrNb) *
                       sizeof(double);
