@@ -158,6 +158,35 @@ def oracle_sampled_solve_seconds(A_host: np.ndarray, b_host: np.ndarray, iters: 
     return out
 
 
+def kernel_source_hash(src_file: str, name: str) -> str:
+    """sha256 (first 16 hex digits) of a kernel's definition in a CUDA source file."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1109_5981_gb300", "csrc", src_file)).read()
+    i = src.index(name + "(")
+    t, e = src.rfind("template", 0, i), src.rfind("\n}\n", 0, i)
+    i = t if t > e else src.rfind("\n", 0, i)
+    j = src.index("\n}\n", i)
+    return hashlib.sha256(src[i:j + 3].encode()).hexdigest()[:16]
+
+
+KERNEL_SOURCES = {"row_pass_x2_kernel": "k_iter.cu", "dd_pass_x3_kernel": "k_iter.cu",
+                  "sketch_tc_kernel": "k_sketch_tc.cu", "jacobi_pair_kernel": "k_svd.cu"}
+
+
+def traffic_per_unit(kernel: str):
+    """Bytes per unit from profiles/roofline_traffic.md if the kernel is unchanged, else None."""
+    try:
+        rows = open(os.path.join(ROOT, "profiles", "roofline_traffic.md")).read().splitlines()
+        cur = kernel_source_hash(KERNEL_SOURCES[kernel], kernel)
+    except (OSError, KeyError, ValueError):
+        return None
+    for line in rows:
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == kernel:
+            return float(cells[2]) if cells[1] == cur else None
+    return None
+
+
 def _measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -311,9 +340,11 @@ def main():
             flops = 15 * 2.0 * s * args.m * args.n
             peak = peaks.get("bf16_tflops_sustained", 1779.5)
             achieved = flops / (t_gemm * 1e-3) / 1e12
+            tpu = traffic_per_unit("sketch_tc_kernel")
             roofline = {"kernel": "sketch_tc_kernel (tcgen05, bf16 digit slices)", "bound": "tensor",
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak,
+                        "traffic": None if tpu is None else tpu * args.m,
                         "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)",
                         "work_per_launch": "15 slice products x 2*s*m*n over all segments",
                         "fp64_equivalent_tflops": 2.0 * s * args.m * args.n / (t_gemm * 1e-3) / 1e12}
@@ -339,9 +370,11 @@ def main():
         elif args.iter == "x2":
             gbs = 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
             peak = peaks.get("hbm_gbs", 6669.5)
+            tpu = traffic_per_unit("row_pass_x2_kernel")
             roofline = {"kernel": "row_pass_x2_kernel (fused A(Nv) and A^T u, double-float planes)",
                         "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                        "frac": gbs / peak, "traffic": None,
+                        "frac": gbs / peak,
+                        "traffic": None if tpu is None else tpu * args.m * args.n,
                         "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
                         "work_per_launch": "8*m*n bytes (hi and lo FP32 planes of A read once)"}
         else:
