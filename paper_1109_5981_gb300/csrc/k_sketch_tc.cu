@@ -18,8 +18,11 @@
 // Operands are split into digit planes in global memory one segment of rows at
 // a time (K-major, bf16; the digits of X are cut from its 64-bit fixed-point
 // form with integer shifts), then a 128 x 64 output tile per CTA streams them
-// through a two-stage shared-memory pipeline (cp.async, 128B swizzle) into
-// tcgen05.mma (M=128, N=64, K=16, FP32 accumulators in TMEM, 8 x 64 columns).
+// through a two-stage shared-memory ring filled by TMA (cp.async.bulk.tensor,
+// 128B swizzle, mbarrier transaction counts) into tcgen05.mma (M=128, N=64,
+// K=16, FP32 accumulators in TMEM, 8 x 64 columns).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -71,15 +74,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -139,19 +133,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Copy a (rows x 64) bf16 K-major tile (row stride ld elements) into shared
-// memory in the 128-byte swizzled layout: 16-byte chunk c of row r goes to
-// byte r*128 + ((c ^ (r & 7)) << 4).
-__device__ __forceinline__ void load_tile(uint32_t sdst, const uint16_t* src, int rows,
-                                          int64_t ld, int tid) {
-  const int nchunks = rows * 8;
-  for (int q = tid; q < nchunks; q += TC_THREADS) {
-    const int r = q >> 3, c = q & 7;
-    const uint32_t dst = sdst + (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
-    cp_async16(dst, src + (int64_t)r * ld + c * 8);
-  }
-}
-
 // Per-column exponent of a segment: e_j with max_l |X[l, j]| < 2^e_j.  ecol is
 // first set to kNoExp; a column that stays there is all zero.
 constexpr int kNoExp = -100000;
@@ -181,25 +162,46 @@ __device__ __forceinline__ int col_exponent(const int* ecol, int64_t j) {
   return e == kNoExp ? 0 : e;
 }
 
+// TMA load of a box {64 elements of K, rows} at (x, y) into 128-byte-swizzled
+// shared memory, completing on `bar` (transaction bytes).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // The tensor-core GEMM over one segment: Cseg[i, j] += 2^(e_j - 11) * scale *
-// sum_g 2^(-8 g) * sum_l (group g products).  Gh, Gl: S_pad x Lp; D: 7 planes of
-// Q_pad x Lp; all bf16, K-major.
+// sum_g 2^(-8 g) * sum_l (group g products).  The digit planes are read
+// through two tensor maps: tmG over [Gh; Gl] (2 Sp rows of Lp) and tmD over
+// the 8 planes of D (8 Qp rows of Lp), boxes of 64 x 128 and 64 x 64 with the
+// 128-byte swizzle the MMA descriptors expect.  One thread issues the TMA
+// loads and the MMAs: the K-tile k + 1 is loaded into the stage freed by the
+// MMAs of k - 1 (tracked by mbarriers), so loads overlap the MMAs of k and
+// the TMEM drain at the end of a chunk, which all eight warps share.
+constexpr int TC_STAGE_TX = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;
+
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
-    const uint16_t* __restrict__ Gh, const uint16_t* __restrict__ Gl,
-    const uint16_t* __restrict__ D, int64_t Lp, int64_t Kext, int64_t Qp,
-    const int* __restrict__ ecol, double scale, int64_t S, int64_t Q, double* __restrict__ C,
-    int64_t ldc, int* __restrict__ err) {
+    const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmD, int64_t Sp,
+    int64_t Qp, int64_t Kext, const int* __restrict__ ecol, double scale, int64_t S, int64_t Q,
+    double* __restrict__ C, int64_t ldc, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + 2 * STAGE_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  uint64_t* bars = (uint64_t*)(smem + 2 * STAGE_BYTES);   // full[2], empty[2], done
+  uint64_t* full = bars;
+  uint64_t* empty = bars + 2;
+  uint64_t* done = bars + 4;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 5);
+  int* abort_flag = (int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t j0 = (int64_t)blockIdx.x * TC_N;
-  const int64_t i0 = (int64_t)blockIdx.y * TC_M;
+  const int64_t i0 = (int64_t)blockIdx.x * TC_M;   // row tiles vary fastest
+  const int64_t j0 = (int64_t)blockIdx.y * TC_N;
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int q = 0; q < 5; ++q) mbar_init(&bars[q], 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -224,39 +226,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
 #pragma unroll
   for (int c = 0; c < 32; ++c) a1[c] = a2[c] = 0;
 
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  bool ok = true;
-  const int64_t nkt = Kext / TC_KT;   // K-tiles holding rows of this segment (row stride Lp)
+  const int64_t nkt = Kext / TC_KT;   // K-tiles of this segment
   const int kt_per_chunk = TC_CHUNK / TC_KT;
-  int64_t kt = 0;
-  while (kt < nkt && ok) {
-    const int64_t kt_end = (kt + kt_per_chunk < nkt) ? kt + kt_per_chunk : nkt;
-    for (int64_t k = kt; k < kt_end && ok; ++k) {
-      const int st = (int)(k & 1);
-      if (pending[st]) {
-        ok = mbar_wait(&bars[st], phase[st], err);
-        phase[st] ^= 1u;
-        pending[st] = false;
-        tc_fence_after();
-      }
-      if (!ok) break;
-      unsigned char* sbase = smem + st * STAGE_BYTES;
-      const uint32_t s_ah = smem_addr(sbase);
-      const uint32_t s_al = s_ah + TILE_A_BYTES;
-      const uint32_t s_d = s_al + TILE_A_BYTES;
-      const int64_t l0 = k * TC_KT;
-      load_tile(s_ah, Gh + i0 * Lp + l0, TC_M, Lp, tid);
-      load_tile(s_al, Gl + i0 * Lp + l0, TC_M, Lp, tid);
+  const int64_t nchunk = (nkt + kt_per_chunk - 1) / kt_per_chunk;
+  int64_t issued = 0, consumed = 0;   // thread 0: tiles loaded / whose MMAs were issued
+  auto issue = [&](int64_t k) {
+    const int st = (int)(k & 1);
+    unsigned char* sbase = smem + st * STAGE_BYTES;
+    const uint32_t s_ah = smem_addr(sbase);
+    const uint32_t s_al = s_ah + TILE_A_BYTES;
+    const uint32_t s_d = s_al + TILE_A_BYTES;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[st])),
+                 "r"(TC_STAGE_TX)
+                 : "memory");
+    const int x = (int)(k * TC_KT);
+    tma_load_2d(s_ah, &tmG, x, (int)i0, &full[st]);
+    tma_load_2d(s_al, &tmG, x, (int)(Sp + i0), &full[st]);
 #pragma unroll 1
-      for (int p = 0; p < TC_DIGITS; ++p)
-        load_tile(s_d + p * TILE_B_BYTES, D + ((int64_t)p * Qp + j0) * Lp + l0, TC_N, Lp, tid);
-      cp_async_wait_all();
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
+    for (int p = 0; p < TC_DIGITS; ++p)
+      tma_load_2d(s_d + p * TILE_B_BYTES, &tmD, x, (int)(p * Qp + j0), &full[st]);
+    issued = k + 1;
+  };
+  if (tid == 0) {
+    if (nkt > 0) issue(0);
+    if (nkt > 1) issue(1);
+  }
+  bool ok = true;
+  for (int64_t ch = 0; ch < nchunk; ++ch) {
+    const int64_t kt = ch * kt_per_chunk;
+    const int64_t kt_end = (kt + kt_per_chunk < nkt) ? kt + kt_per_chunk : nkt;
+    if (tid == 0 && ok) {
+      for (int64_t k = kt; k < kt_end; ++k) {
+        const int st = (int)(k & 1);
+        if (!mbar_wait(&full[st], (uint32_t)((k >> 1) & 1), err)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
-        const bool first = (k == kt);
+        const uint32_t s_ah = smem_addr(smem + st * STAGE_BYTES);
+        const uint32_t s_al = s_ah + TILE_A_BYTES;
+        const uint32_t s_d = s_al + TILE_A_BYTES;
 #pragma unroll
         for (int ks = 0; ks < TC_KT / 16; ++ks) {
           const uint64_t ah = smem_desc(s_ah + ks * 32);
@@ -265,28 +274,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
           for (int g = 0; g < TC_GROUPS; ++g) {
             const uint32_t dt = tmem + (uint32_t)(g * TC_N);
             const uint64_t bh = smem_desc(s_d + g * TILE_B_BYTES + ks * 32);
-            mma_bf16(dt, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+            mma_bf16(dt, ah, bh, idesc, (k == kt && ks == 0) ? 0u : 1u);
             if (g >= 1) {
               const uint64_t bl = smem_desc(s_d + (g - 1) * TILE_B_BYTES + ks * 32);
               mma_bf16(dt, al, bl, idesc, 1u);
             }
           }
         }
-        mma_commit(&bars[st]);
+        mma_commit(&empty[st]);
+        consumed = k + 1;
+        if (k + 1 == kt_end) mma_commit(done);
+        // refill the stage of k - 1 with tile k + 1 once the MMAs of k - 1 are done
+        if (k >= 1 && k + 1 < nkt && issued == k + 1) {
+          if (!mbar_wait(&empty[st ^ 1], (uint32_t)(((k - 1) >> 1) & 1), err)) {
+            ok = false;
+            break;
+          }
+          issue(k + 1);
+        }
       }
-      pending[st] = true;
-      __syncthreads();
+      if (!ok) *abort_flag = 1;
     }
-    // all MMAs of this chunk done
-    for (int st = 0; st < 2 && ok; ++st) {
-      if (pending[st]) {
-        ok = mbar_wait(&bars[st], phase[st], err);
-        phase[st] ^= 1u;
-        pending[st] = false;
-      }
-    }
+    // every warp: the chunk's MMAs are complete -> drain TMEM
+    bool have = *abort_flag == 0;
+    if (have && !mbar_wait(done, (uint32_t)(ch & 1), err)) have = false;
     tc_fence_after();
-    if (ok) {
+    if (have) {
       const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
       for (int g = 0; g < 4; ++g) {
@@ -304,10 +317,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
 #pragma unroll
         for (int c = 0; c < 32; ++c) a2[c] += (long long)__float2int_rn(v[c]) * w;
       }
+    } else {
+      ok = false;
     }
     tc_fence_before();
-    __syncthreads();
-    kt = kt_end;
+    __syncthreads();   // TMEM may be overwritten by the next chunk's first MMAs
+    if (*abort_flag != 0) {
+      ok = false;
+      break;
+    }
+  }
+  if (tid == 0 && !ok) {
+    // let issued copies and MMAs finish (bounded) before the CTA releases its memory
+    for (int64_t k = consumed; k < issued; ++k) mbar_wait(&full[k & 1], (uint32_t)((k >> 1) & 1), err);
+    for (int64_t k = consumed >= 2 ? consumed - 2 : 0; k < consumed; ++k)
+      mbar_wait(&empty[k & 1], (uint32_t)((k >> 1) & 1), err);
   }
   // epilogue: row i0 + 32 (warp % 4) + lane, columns j0 + 32 wg .. + 31
   const int64_t i = i0 + (warp & 3) * 32 + (tid & 31);
@@ -446,6 +470,37 @@ int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_by
   return std::min(rows, Lr);
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }();
+  return fn;
+}
+
+// 2-D bf16 map over `rows` rows of `Lp` elements (K-major), box 64 x box_rows,
+// 128-byte swizzle.
+static bool make_digit_map(CUtensorMap* map, const uint16_t* base, int64_t Lp, int64_t rows,
+                           int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Lp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Lp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_KT, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
@@ -461,6 +516,10 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
   uint16_t* Gl = Gh + Sp * Lp;
   uint16_t* D = Gl + Sp * Lp;
   int* ecol = (int*)(D + (int64_t)TC_DIGITS * Qp * Lp);
+  CUtensorMap tmG, tmD;
+  if (!make_digit_map(&tmG, Gh, Lp, 2 * Sp, TC_M) ||
+      !make_digit_map(&tmD, D, Lp, (int64_t)TC_DIGITS * Qp, TC_N))
+    return LSRN_ERR_CUDA;
   const int64_t tot = S * Q;
   launch(zero_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, C, S, Q, ldc);
   for (int64_t l0 = 0; l0 < L; l0 += seg_rows) {
@@ -480,9 +539,11 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
       cudaEventCreate(&e1);
       cudaEventRecord(e0, st);
     }
-    launch(sketch_tc_kernel, dim3((unsigned)(Qp / TC_N), (unsigned)(Sp / TC_M)), dim3(TC_THREADS),
-           (size_t)TC_SMEM, st, (const uint16_t*)Gh, (const uint16_t*)Gl,
-           (const uint16_t*)D, Lp, Lseg, Qp, (const int*)ecol, xscale, S, Q, C, ldc, err);
+    // the column tiles that share an X digit tile run together (y fastest):
+    // the smaller Gamma planes are the ones re-read across waves
+    launch(sketch_tc_kernel, dim3((unsigned)(Sp / TC_M), (unsigned)(Qp / TC_N)), dim3(TC_THREADS),
+           (size_t)TC_SMEM, st, tmG, tmD, Sp, Qp, Lseg, (const int*)ecol, xscale, S, Q, C, ldc,
+           err);
     if (gemm_events) {
       cudaEventRecord(e1, st);
       gemm_events->emplace_back(e0, e1);
