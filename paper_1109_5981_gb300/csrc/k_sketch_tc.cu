@@ -263,23 +263,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
           break;
         }
         tc_fence_after();
-        const uint32_t s_ah = smem_addr(smem + st * STAGE_BYTES);
-        const uint32_t s_al = s_ah + TILE_A_BYTES;
-        const uint32_t s_d = s_al + TILE_A_BYTES;
+        // descriptors differ only in the start address field (address >> 4)
+        const uint64_t d_ah = smem_desc(smem_addr(smem + st * STAGE_BYTES));
+        const uint64_t d_al = d_ah + (TILE_A_BYTES >> 4);
+        const uint64_t d_b = d_al + (TILE_A_BYTES >> 4);
 #pragma unroll
         for (int ks = 0; ks < TC_KT / 16; ++ks) {
-          const uint64_t ah = smem_desc(s_ah + ks * 32);
-          const uint64_t al = smem_desc(s_al + ks * 32);
+          const uint32_t acc0 = (k == kt && ks == 0) ? 0u : 1u;
+          // eight MMAs into eight different accumulators, then seven more:
+          // consecutive MMAs never wait on each other's TMEM result
 #pragma unroll
-          for (int g = 0; g < TC_GROUPS; ++g) {
-            const uint32_t dt = tmem + (uint32_t)(g * TC_N);
-            const uint64_t bh = smem_desc(s_d + g * TILE_B_BYTES + ks * 32);
-            mma_bf16(dt, ah, bh, idesc, (k == kt && ks == 0) ? 0u : 1u);
-            if (g >= 1) {
-              const uint64_t bl = smem_desc(s_d + (g - 1) * TILE_B_BYTES + ks * 32);
-              mma_bf16(dt, al, bl, idesc, 1u);
-            }
-          }
+          for (int g = 0; g < TC_GROUPS; ++g)
+            mma_bf16(tmem + (uint32_t)(g * TC_N), d_ah + 2 * ks,
+                     d_b + (uint64_t)(g * (TILE_B_BYTES >> 4)) + 2 * ks, idesc, acc0);
+#pragma unroll
+          for (int g = 1; g < TC_GROUPS; ++g)
+            mma_bf16(tmem + (uint32_t)(g * TC_N), d_al + 2 * ks,
+                     d_b + (uint64_t)((g - 1) * (TILE_B_BYTES >> 4)) + 2 * ks, idesc, 1u);
         }
         mma_commit(&empty[st]);
         consumed = k + 1;
