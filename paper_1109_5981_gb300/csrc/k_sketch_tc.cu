@@ -18,8 +18,8 @@
 // Operands are split into digit planes in global memory one segment of rows at
 // a time (K-major, bf16; the digits of X are cut from its 64-bit fixed-point
 // form with integer shifts), then a 128 x 64 output tile per CTA streams them
-// through a four-stage shared-memory ring filled by TMA (cp.async.bulk.tensor,
-// 64B swizzle, mbarrier transaction counts) into tcgen05.mma (M=128, N=64,
+// through a two-stage shared-memory ring filled by TMA (cp.async.bulk.tensor,
+// 128B swizzle, mbarrier transaction counts) into tcgen05.mma (M=128, N=64,
 // K=16, FP32 accumulators in TMEM, 8 x 64 columns).
 #include <cudaTypedefs.h>
 
@@ -35,16 +35,15 @@ namespace {
 
 constexpr int TC_M = 128;              // sketch rows per tile
 constexpr int TC_N = 64;               // columns of X per tile
-constexpr int TC_KT = 32;              // K per pipeline stage (one 64-byte swizzle row)
-constexpr int TC_NST = 4;              // pipeline stages
+constexpr int TC_KT = 64;              // K per pipeline stage (one 128-byte swizzle row)
 constexpr int TC_CHUNK = 512;          // rows summed exactly in TMEM before the int64 fold
 constexpr int TC_GROUPS = 8;
 constexpr int TC_DIGITS = 8;
 constexpr int TC_THREADS = 256;              // two warpgroups share the TMEM lane quadrants
-constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 8 KB
-constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 4 KB
-constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 48 KB
-constexpr int TC_SMEM = TC_NST * STAGE_BYTES + 1024 + 128;
+constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 16 KB
+constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 8 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 96 KB
+constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024 + 64;
 constexpr long long kSpinLimit = 1ll << 26;         // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -82,15 +81,15 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16),
-// 8-row groups 512 bytes apart (stride byte offset), descriptor version 1.
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
-  d |= (uint64_t)(512 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
   d |= (uint64_t)1 << 46;                       // descriptor version
-  d |= (uint64_t)4 << 61;                       // 64-byte swizzle
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
   return d;
 }
 
@@ -177,11 +176,11 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 // The tensor-core GEMM over one segment: Cseg[i, j] += 2^(e_j - 11) * scale *
 // sum_g 2^(-8 g) * sum_l (group g products).  The digit planes are read
 // through two tensor maps: tmG over [Gh; Gl] (2 Sp rows of Lp) and tmD over
-// the 8 planes of D (8 Qp rows of Lp), boxes of 32 x 128 and 32 x 64 with the
-// 64-byte swizzle the MMA descriptors expect.  One thread issues the TMA
-// loads and the MMAs: the K-tile k + 3 is loaded into the stage freed by the
-// MMAs of k - 1 (tracked by mbarriers), so three stages stay in flight over
-// the MMAs and the TMEM drain at the end of a chunk, which all eight warps share.
+// the 8 planes of D (8 Qp rows of Lp), boxes of 64 x 128 and 64 x 64 with the
+// 128-byte swizzle the MMA descriptors expect.  One thread issues the TMA
+// loads and the MMAs: the K-tile k + 1 is loaded into the stage freed by the
+// MMAs of k - 1 (tracked by mbarriers), so loads overlap the MMAs of k and
+// the TMEM drain at the end of a chunk, which all eight warps share.
 constexpr int TC_STAGE_TX = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;
 
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
@@ -190,18 +189,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
     double* __restrict__ C, int64_t ldc, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + TC_NST * STAGE_BYTES);   // full[NST], empty[NST], done
+  uint64_t* bars = (uint64_t*)(smem + 2 * STAGE_BYTES);   // full[2], empty[2], done
   uint64_t* full = bars;
-  uint64_t* empty = bars + TC_NST;
-  uint64_t* done = bars + 2 * TC_NST;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TC_NST + 1);
+  uint64_t* empty = bars + 2;
+  uint64_t* done = bars + 4;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 5);
   int* abort_flag = (int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * TC_M;   // row tiles vary fastest
   const int64_t j0 = (int64_t)blockIdx.y * TC_N;
 
   if (tid == 0) {
-    for (int q = 0; q < 2 * TC_NST + 1; ++q) mbar_init(&bars[q], 1);
+    for (int q = 0; q < 5; ++q) mbar_init(&bars[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -232,7 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   const int64_t nchunk = (nkt + kt_per_chunk - 1) / kt_per_chunk;
   int64_t issued = 0, consumed = 0;   // thread 0: tiles loaded / whose MMAs were issued
   auto issue = [&](int64_t k) {
-    const int st = (int)(k % TC_NST);
+    const int st = (int)(k & 1);
     unsigned char* sbase = smem + st * STAGE_BYTES;
     const uint32_t s_ah = smem_addr(sbase);
     const uint32_t s_al = s_ah + TILE_A_BYTES;
@@ -248,16 +247,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
       tma_load_2d(s_d + p * TILE_B_BYTES, &tmD, x, (int)(p * Qp + j0), &full[st]);
     issued = k + 1;
   };
-  if (tid == 0)
-    for (int64_t k = 0; k < TC_NST && k < nkt; ++k) issue(k);
+  if (tid == 0) {
+    if (nkt > 0) issue(0);
+    if (nkt > 1) issue(1);
+  }
   bool ok = true;
   for (int64_t ch = 0; ch < nchunk; ++ch) {
     const int64_t kt = ch * kt_per_chunk;
     const int64_t kt_end = (kt + kt_per_chunk < nkt) ? kt + kt_per_chunk : nkt;
     if (tid == 0 && ok) {
       for (int64_t k = kt; k < kt_end; ++k) {
-        const int st = (int)(k % TC_NST);
-        if (!mbar_wait(&full[st], (uint32_t)((k / TC_NST) & 1), err)) {
+        const int st = (int)(k & 1);
+        if (!mbar_wait(&full[st], (uint32_t)((k >> 1) & 1), err)) {
           ok = false;
           break;
         }
@@ -283,14 +284,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
         mma_commit(&empty[st]);
         consumed = k + 1;
         if (k + 1 == kt_end) mma_commit(done);
-        // refill the stage of k - 1 with tile k - 1 + NST once the MMAs of k - 1 are done
-        if (k >= 1 && k - 1 + TC_NST < nkt && issued == k - 1 + TC_NST) {
-          const int64_t kp = k - 1;
-          if (!mbar_wait(&empty[kp % TC_NST], (uint32_t)((kp / TC_NST) & 1), err)) {
+        // refill the stage of k - 1 with tile k + 1 once the MMAs of k - 1 are done
+        if (k >= 1 && k + 1 < nkt && issued == k + 1) {
+          if (!mbar_wait(&empty[st ^ 1], (uint32_t)(((k - 1) >> 1) & 1), err)) {
             ok = false;
             break;
           }
-          issue(kp + TC_NST);
+          issue(k + 1);
         }
       }
       if (!ok) *abort_flag = 1;
@@ -329,10 +329,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   }
   if (tid == 0 && !ok) {
     // let issued copies and MMAs finish (bounded) before the CTA releases its memory
-    for (int64_t k = consumed; k < issued; ++k)
-      mbar_wait(&full[k % TC_NST], (uint32_t)((k / TC_NST) & 1), err);
-    for (int64_t k = consumed >= TC_NST ? consumed - TC_NST : 0; k < consumed; ++k)
-      mbar_wait(&empty[k % TC_NST], (uint32_t)((k / TC_NST) & 1), err);
+    for (int64_t k = consumed; k < issued; ++k) mbar_wait(&full[k & 1], (uint32_t)((k >> 1) & 1), err);
+    for (int64_t k = consumed >= 2 ? consumed - 2 : 0; k < consumed; ++k)
+      mbar_wait(&empty[k & 1], (uint32_t)((k >> 1) & 1), err);
   }
   // epilogue: row i0 + 32 (warp % 4) + lane, columns j0 + 32 wg .. + 31
   const int64_t i = i0 + (warp & 3) * 32 + (tid & 31);
@@ -487,8 +486,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 2-D bf16 map over `rows` rows of `Lp` elements (K-major), box 32 x box_rows,
-// 64-byte swizzle.
+// 2-D bf16 map over `rows` rows of `Lp` elements (K-major), box 64 x box_rows,
+// 128-byte swizzle.
 static bool make_digit_map(CUtensorMap* map, const uint16_t* base, int64_t Lp, int64_t rows,
                            int box_rows) {
   auto enc = tensor_map_encoder();
@@ -498,7 +497,7 @@ static bool make_digit_map(CUtensorMap* map, const uint16_t* base, int64_t Lp, i
   const cuuint32_t box[2] = {(cuuint32_t)TC_KT, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
