@@ -18,11 +18,10 @@
 // Operands are split into digit planes in global memory one segment of rows at
 // a time (K-major, bf16; the digits of X are cut from its 64-bit fixed-point
 // form with integer shifts), then a 128 x 64 output tile per CTA streams them
-// through a two-stage shared-memory ring filled by TMA (cp.async.bulk.tensor,
-// 128B swizzle, mbarrier transaction counts) into tcgen05.mma (M=128, N=64,
-// K=16, FP32 accumulators in TMEM, 8 x 64 columns).
-#include <cudaTypedefs.h>
-
+// through a two-stage shared-memory ring into tcgen05.mma (M=128, N=64, K=16,
+// FP32 accumulators in TMEM, 8 x 64 columns).  The planes are stored as
+// pre-swizzled tiles, so each stage is ten contiguous bulk copies
+// (cp.async.bulk with mbarrier transaction counts).
 #include <algorithm>
 #include <cmath>
 
@@ -133,6 +132,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// Digit planes are stored as tiles: tile (row / R, k / 64) of a plane is a
+// contiguous block of R x 64 bf16 (R = 128 for Gamma, 64 for X), laid out in
+// 128-byte rows with the 16-byte chunks XOR-swizzled by (row % 8) -- the
+// shared-memory layout the MMA descriptors read -- so one bulk copy moves a
+// tile from HBM/L2 into a pipeline stage unchanged.
+__host__ __device__ __forceinline__ int64_t tiled_off(int64_t row, int64_t k, int R, int64_t nkt) {
+  const int64_t tile = (row / R) * nkt + (k >> 6);
+  const int r = (int)(row % R), kk = (int)(k & 63);
+  return tile * (int64_t)(R * 64) + (int64_t)r * 64 + ((((kk >> 3) ^ (r & 7))) << 3) + (kk & 7);
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // Per-column exponent of a segment: e_j with max_l |X[l, j]| < 2^e_j.  ecol is
 // first set to kNoExp; a column that stays there is all zero.
 constexpr int kNoExp = -100000;
@@ -162,30 +180,18 @@ __device__ __forceinline__ int col_exponent(const int* ecol, int64_t j) {
   return e == kNoExp ? 0 : e;
 }
 
-// TMA load of a box {64 elements of K, rows} at (x, y) into 128-byte-swizzled
-// shared memory, completing on `bar` (transaction bytes).
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
-      "{%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-
 // The tensor-core GEMM over one segment: Cseg[i, j] += 2^(e_j - 11) * scale *
-// sum_g 2^(-8 g) * sum_l (group g products).  The digit planes are read
-// through two tensor maps: tmG over [Gh; Gl] (2 Sp rows of Lp) and tmD over
-// the 8 planes of D (8 Qp rows of Lp), boxes of 64 x 128 and 64 x 64 with the
-// 128-byte swizzle the MMA descriptors expect.  One thread issues the TMA
-// loads and the MMAs: the K-tile k + 1 is loaded into the stage freed by the
-// MMAs of k - 1 (tracked by mbarriers), so loads overlap the MMAs of k and
-// the TMEM drain at the end of a chunk, which all eight warps share.
+// sum_g 2^(-8 g) * sum_l (group g products).  Gt holds [Gh; Gl] and Dt the 8
+// planes of X's digits, both as pre-swizzled tiles (tiled_off).  One thread
+// issues the bulk copies and the MMAs: the K-tile k + 1 is loaded into the
+// stage freed by the MMAs of k - 1 (tracked by mbarriers), so loads overlap
+// the MMAs of k and the TMEM drain at the end of a chunk, which all eight
+// warps share.
 constexpr int TC_STAGE_TX = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;
 
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
-    const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmD, int64_t Sp,
-    int64_t Qp, int64_t Kext, const int* __restrict__ ecol, double scale, int64_t S, int64_t Q,
+    const uint16_t* __restrict__ Gt, const uint16_t* __restrict__ Dt, int64_t Sp, int64_t Qp,
+    int64_t Lp, int64_t Kext, const int* __restrict__ ecol, double scale, int64_t S, int64_t Q,
     double* __restrict__ C, int64_t ldc, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -239,12 +245,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[st])),
                  "r"(TC_STAGE_TX)
                  : "memory");
-    const int x = (int)(k * TC_KT);
-    tma_load_2d(s_ah, &tmG, x, (int)i0, &full[st]);
-    tma_load_2d(s_al, &tmG, x, (int)(Sp + i0), &full[st]);
+    const int64_t nkt_l = Lp / TC_KT;   // K-tiles per tile row of a plane
+    bulk_g2s(s_ah, Gt + tiled_off(i0, k * TC_KT, TC_M, nkt_l), TILE_A_BYTES, &full[st]);
+    bulk_g2s(s_al, Gt + Sp * Lp + tiled_off(i0, k * TC_KT, TC_M, nkt_l), TILE_A_BYTES, &full[st]);
 #pragma unroll 1
     for (int p = 0; p < TC_DIGITS; ++p)
-      tma_load_2d(s_d + p * TILE_B_BYTES, &tmD, x, (int)(p * Qp + j0), &full[st]);
+      bulk_g2s(s_d + p * TILE_B_BYTES, Dt + p * Qp * Lp + tiled_off(j0, k * TC_KT, TC_N, nkt_l),
+               TILE_B_BYTES, &full[st]);
     issued = k + 1;
   };
   if (tid == 0) {
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(256) split_x_kernel(const double* __restrict__
     if (j < Qp && l < Lp) {
 #pragma unroll
       for (int p = 0; p < TC_DIGITS; ++p) {
-        D[((int64_t)p * Qp + j) * Lp + l] = tile[p][tx][r];
+        D[(int64_t)p * Qp * Lp + tiled_off(j, l, TC_N, Lp / TC_KT)] = tile[p][tx][r];
       }
     }
   }
@@ -438,8 +445,8 @@ __global__ void __launch_bounds__(256) gamma_digits_kernel(uint64_t seed, uint32
     const int ii = q >> 5, r = q & 31;
     const int64_t i = ib + ii, l = lb + r;
     if (i < Sp && l < Lp) {
-      Gh[i * Lp + l] = th[r][ii];
-      Gl[i * Lp + l] = tl[r][ii];
+      Gh[tiled_off(i, l, TC_M, Lp / TC_KT)] = th[r][ii];
+      Gl[tiled_off(i, l, TC_M, Lp / TC_KT)] = tl[r][ii];
     }
   }
 }
@@ -470,37 +477,6 @@ int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_by
   return std::min(rows, Lr);
 }
 
-// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }();
-  return fn;
-}
-
-// 2-D bf16 map over `rows` rows of `Lp` elements (K-major), box 64 x box_rows,
-// 128-byte swizzle.
-static bool make_digit_map(CUtensorMap* map, const uint16_t* base, int64_t Lp, int64_t rows,
-                           int box_rows) {
-  auto enc = tensor_map_encoder();
-  if (enc == nullptr) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)Lp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)Lp * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_KT, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
@@ -516,10 +492,6 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
   uint16_t* Gl = Gh + Sp * Lp;
   uint16_t* D = Gl + Sp * Lp;
   int* ecol = (int*)(D + (int64_t)TC_DIGITS * Qp * Lp);
-  CUtensorMap tmG, tmD;
-  if (!make_digit_map(&tmG, Gh, Lp, 2 * Sp, TC_M) ||
-      !make_digit_map(&tmD, D, Lp, (int64_t)TC_DIGITS * Qp, TC_N))
-    return LSRN_ERR_CUDA;
   const int64_t tot = S * Q;
   launch(zero_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, C, S, Q, ldc);
   for (int64_t l0 = 0; l0 < L; l0 += seg_rows) {
@@ -542,8 +514,8 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
     // the column tiles that share an X digit tile run together (y fastest):
     // the smaller Gamma planes are the ones re-read across waves
     launch(sketch_tc_kernel, dim3((unsigned)(Sp / TC_M), (unsigned)(Qp / TC_N)), dim3(TC_THREADS),
-           (size_t)TC_SMEM, st, tmG, tmD, Sp, Qp, Lseg, (const int*)ecol, xscale, S, Q, C, ldc,
-           err);
+           (size_t)TC_SMEM, st, (const uint16_t*)Gh, (const uint16_t*)D, Sp, Qp, Lp, Lseg,
+           (const int*)ecol, xscale, S, Q, C, ldc, err);
     if (gemm_events) {
       cudaEventRecord(e1, st);
       gemm_events->emplace_back(e0, e1);
