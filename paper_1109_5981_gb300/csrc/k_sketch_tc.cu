@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   for (int64_t ch = 0; ch < nchunk; ++ch) {
     const int64_t kt = ch * kt_per_chunk;
     const int64_t kt_end = (kt + kt_per_chunk < nkt) ? kt + kt_per_chunk : nkt;
-    if (tid == 0 && ok) {
+    if (warp == 0) {
+      if (tid == 0 && ok) {
       for (int64_t k = kt; k < kt_end; ++k) {
         const int st = (int)(k & 1);
         if (!mbar_wait(&full[st], (uint32_t)((k >> 1) & 1), err)) {
@@ -300,11 +301,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
           issue(k + 1);
         }
       }
+      // the chunk's MMAs complete before any warp reads TMEM
+      if (ok && !mbar_wait(done, (uint32_t)(ch & 1), err)) ok = false;
       if (!ok) *abort_flag = 1;
+      }
+      __syncwarp();   // the other lanes of warp 0 wait here, not in a spin loop
     }
-    // every warp: the chunk's MMAs are complete -> drain TMEM
-    bool have = *abort_flag == 0;
-    if (have && !mbar_wait(done, (uint32_t)(ch & 1), err)) have = false;
+    // every warp: the chunk's MMAs are complete (thread 0 saw `done`) -> drain TMEM
+    __syncthreads();
+    const bool have = *abort_flag == 0;
     tc_fence_after();
     if (have) {
       const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
