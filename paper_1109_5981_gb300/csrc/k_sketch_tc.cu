@@ -18,7 +18,7 @@
 // Operands are split into digit planes in global memory one segment of rows at
 // a time (K-major, bf16; the digits of X are cut from its 64-bit fixed-point
 // form with integer shifts), then a 128 x 64 output tile per CTA streams them
-// through a four-stage shared-memory ring into tcgen05.mma (M=128, N=64, K=16,
+// through a two-stage shared-memory ring into tcgen05.mma (M=128, N=64, K=16,
 // FP32 accumulators in TMEM, 8 x 64 columns).  The planes are stored as
 // pre-swizzled tiles, so each stage is ten contiguous bulk copies
 // (cp.async.bulk with mbarrier transaction counts).
@@ -34,16 +34,15 @@ namespace {
 
 constexpr int TC_M = 128;              // sketch rows per tile
 constexpr int TC_N = 64;               // columns of X per tile
-constexpr int TC_KT = 32;              // K per pipeline stage (one 64-byte swizzle row)
-constexpr int TC_NST = 4;              // pipeline stages
+constexpr int TC_KT = 64;              // K per pipeline stage (one 128-byte swizzle row)
 constexpr int TC_CHUNK = 512;          // rows summed exactly in TMEM before the int64 fold
 constexpr int TC_GROUPS = 8;
 constexpr int TC_DIGITS = 8;
 constexpr int TC_THREADS = 256;              // two warpgroups share the TMEM lane quadrants
-constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 8 KB
-constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 4 KB
-constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 48 KB
-constexpr int TC_SMEM = TC_NST * STAGE_BYTES + 1024 + 128;
+constexpr int TILE_A_BYTES = TC_M * TC_KT * 2;     // 16 KB
+constexpr int TILE_B_BYTES = TC_N * TC_KT * 2;     // 8 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;   // 96 KB
+constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024 + 64;
 constexpr long long kSpinLimit = 1ll << 26;         // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -81,15 +80,15 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16),
-// 8-row groups 512 bytes apart (stride byte offset), descriptor version 1.
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
-  d |= (uint64_t)(512 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
   d |= (uint64_t)1 << 46;                       // descriptor version
-  d |= (uint64_t)4 << 61;                       // 64-byte swizzle
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
   return d;
 }
 
@@ -133,16 +132,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Digit planes are stored as tiles: tile (row / R, k / 32) of a plane is a
-// contiguous block of R x 32 bf16 (R = 128 for Gamma, 64 for X), laid out in
-// 64-byte rows with the 16-byte chunks XOR-swizzled by ((row / 2) % 4) -- the
-// 64-byte-swizzle layout the MMA descriptors read -- so one bulk copy moves a
+// Digit planes are stored as tiles: tile (row / R, k / 64) of a plane is a
+// contiguous block of R x 64 bf16 (R = 128 for Gamma, 64 for X), laid out in
+// 128-byte rows with the 16-byte chunks XOR-swizzled by (row % 8) -- the
+// shared-memory layout the MMA descriptors read -- so one bulk copy moves a
 // tile from HBM/L2 into a pipeline stage unchanged.
 __host__ __device__ __forceinline__ int64_t tiled_off(int64_t row, int64_t k, int R, int64_t nkt) {
-  const int64_t tile = (row / R) * nkt + (k >> 5);
-  const int r = (int)(row % R), kk = (int)(k & 31);
-  return tile * (int64_t)(R * 32) + (int64_t)r * 32 + ((((kk >> 3) ^ ((r >> 1) & 3))) << 3) +
-         (kk & 7);
+  const int64_t tile = (row / R) * nkt + (k >> 6);
+  const int r = (int)(row % R), kk = (int)(k & 63);
+  return tile * (int64_t)(R * 64) + (int64_t)r * 64 + ((((kk >> 3) ^ (r & 7))) << 3) + (kk & 7);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -185,10 +183,10 @@ __device__ __forceinline__ int col_exponent(const int* ecol, int64_t j) {
 // The tensor-core GEMM over one segment: Cseg[i, j] += 2^(e_j - 11) * scale *
 // sum_g 2^(-8 g) * sum_l (group g products).  Gt holds [Gh; Gl] and Dt the 8
 // planes of X's digits, both as pre-swizzled tiles (tiled_off).  One thread
-// issues the bulk copies and the MMAs: the K-tile k + 3 is loaded into the
-// stage freed by the MMAs of k - 1 (tracked by mbarriers), so three stages
-// are in flight over the MMAs and the TMEM drain at the end of a chunk,
-// which all eight warps share.
+// issues the bulk copies and the MMAs: the K-tile k + 1 is loaded into the
+// stage freed by the MMAs of k - 1 (tracked by mbarriers), so loads overlap
+// the MMAs of k and the TMEM drain at the end of a chunk, which all eight
+// warps share.
 constexpr int TC_STAGE_TX = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;
 
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
@@ -197,18 +195,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
     double* __restrict__ C, int64_t ldc, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + TC_NST * STAGE_BYTES);   // full[NST], empty[NST], done
+  uint64_t* bars = (uint64_t*)(smem + 2 * STAGE_BYTES);   // full[2], empty[2], done
   uint64_t* full = bars;
-  uint64_t* empty = bars + TC_NST;
-  uint64_t* done = bars + 2 * TC_NST;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TC_NST + 1);
+  uint64_t* empty = bars + 2;
+  uint64_t* done = bars + 4;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 5);
   int* abort_flag = (int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * TC_M;   // row tiles vary fastest
   const int64_t j0 = (int64_t)blockIdx.y * TC_N;
 
   if (tid == 0) {
-    for (int q = 0; q < 2 * TC_NST + 1; ++q) mbar_init(&bars[q], 1);
+    for (int q = 0; q < 5; ++q) mbar_init(&bars[q], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -239,7 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   const int64_t nchunk = (nkt + kt_per_chunk - 1) / kt_per_chunk;
   int64_t issued = 0, consumed = 0;   // thread 0: tiles loaded / whose MMAs were issued
   auto issue = [&](int64_t k) {
-    const int st = (int)(k % TC_NST);
+    const int st = (int)(k & 1);
     unsigned char* sbase = smem + st * STAGE_BYTES;
     const uint32_t s_ah = smem_addr(sbase);
     const uint32_t s_al = s_ah + TILE_A_BYTES;
@@ -256,8 +254,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
                TILE_B_BYTES, &full[st]);
     issued = k + 1;
   };
-  if (tid == 0)
-    for (int64_t k = 0; k < TC_NST && k < nkt; ++k) issue(k);
+  if (tid == 0) {
+    if (nkt > 0) issue(0);
+    if (nkt > 1) issue(1);
+  }
   bool ok = true;
   for (int64_t ch = 0; ch < nchunk; ++ch) {
     const int64_t kt = ch * kt_per_chunk;
@@ -265,8 +265,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
     if (warp == 0) {
       if (tid == 0 && ok) {
       for (int64_t k = kt; k < kt_end; ++k) {
-        const int st = (int)(k % TC_NST);
-        if (!mbar_wait(&full[st], (uint32_t)((k / TC_NST) & 1), err)) {
+        const int st = (int)(k & 1);
+        if (!mbar_wait(&full[st], (uint32_t)((k >> 1) & 1), err)) {
           ok = false;
           break;
         }
@@ -292,14 +292,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
         mma_commit(&empty[st]);
         consumed = k + 1;
         if (k + 1 == kt_end) mma_commit(done);
-        // refill the stage of k - 1 with tile k - 1 + NST once the MMAs of k - 1 are done
-        if (k >= 1 && k - 1 + TC_NST < nkt && issued == k - 1 + TC_NST) {
-          const int64_t kp = k - 1;
-          if (!mbar_wait(&empty[kp % TC_NST], (uint32_t)((kp / TC_NST) & 1), err)) {
+        // refill the stage of k - 1 with tile k + 1 once the MMAs of k - 1 are done
+        if (k >= 1 && k + 1 < nkt && issued == k + 1) {
+          if (!mbar_wait(&empty[st ^ 1], (uint32_t)(((k - 1) >> 1) & 1), err)) {
             ok = false;
             break;
           }
-          issue(kp + TC_NST);
+          issue(k + 1);
         }
       }
       // the chunk's MMAs complete before any warp reads TMEM
@@ -342,10 +341,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   }
   if (tid == 0 && !ok) {
     // let issued copies and MMAs finish (bounded) before the CTA releases its memory
-    for (int64_t k = consumed; k < issued; ++k)
-      mbar_wait(&full[k % TC_NST], (uint32_t)((k / TC_NST) & 1), err);
-    for (int64_t k = consumed >= TC_NST ? consumed - TC_NST : 0; k < consumed; ++k)
-      mbar_wait(&empty[k % TC_NST], (uint32_t)((k / TC_NST) & 1), err);
+    for (int64_t k = consumed; k < issued; ++k) mbar_wait(&full[k & 1], (uint32_t)((k >> 1) & 1), err);
+    for (int64_t k = consumed >= 2 ? consumed - 2 : 0; k < consumed; ++k)
+      mbar_wait(&empty[k & 1], (uint32_t)((k >> 1) & 1), err);
   }
   // epilogue: row i0 + 32 (warp % 4) + lane, columns j0 + 32 wg .. + 31
   const int64_t i = i0 + (warp & 3) * 32 + (tid & 31);
