@@ -434,15 +434,7 @@ template <int EPT>
 __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __restrict__ W, int64_t Q,
                                                                   int P, int t, double tol,
                                                                   double* __restrict__ nrm2,
-                                                                  double* __restrict__ scl,
                                                                   int* __restrict__ rot_count) {
-  // Rows are stored scaled: true row a = scl[a] * W[a].  A rotation by
-  // (c, s = c t) multiplies both true rows by c, which goes into the scales,
-  // so the stored rows take one FMA each:
-  //   W[a] <- W[a] - (t scl[b] / scl[a]) W[b],   W[b] <- W[b] + (t scl[a] / scl[b]) W[a],
-  //   scl[a] <- c scl[a],  scl[b] <- c scl[b]
-  // (the rounding error in true units is that of the usual rotation).  A row
-  // whose scale falls below 2^-100 is rescaled to 1 on the spot.
   __shared__ double sh[kJacThreads / 32];
   const int pr = blockIdx.x;
   int a, b;
@@ -461,8 +453,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
   }
   double* wa = W + (int64_t)a * Q;
   double* wb = W + (int64_t)b * Q;
-  const double aa = nrm2[a], bb = nrm2[b];   // true squared norms, issued with the row loads
-  const double sa = scl[a], sbv = scl[b];
+  const double aa = nrm2[a], bb = nrm2[b];   // issued with the row loads
   double x[EPT], y[EPT];
   double ab = 0.0;
 #pragma unroll
@@ -472,10 +463,10 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
     y[e] = c < Q ? wb[c] : 0.0;
     ab = fma(x[e], y[e], ab);
   }
-  ab = jac_block_sum(ab, sh) * (sa * sbv);   // true dot product
+  ab = jac_block_sum(ab, sh);
   if (aa == 0.0 || bb == 0.0) return;
   // the angle (square roots and divisions, ~70 FP64 operations) once per pair
-  __shared__ double rot[5];
+  __shared__ double rot[3];
   if (threadIdx.x == 0) {
     double tt = 0.0, cs = 1.0;
     if (fabs(ab) > tol * sqrt(aa) * sqrt(bb)) {
@@ -488,25 +479,17 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
       cs = 1.0 / sqrt(1.0 + tt * tt);
     }
     rot[0] = tt;
-    rot[1] = -tt * sbv / sa;   // multiplier of W[b] in the new W[a]
-    rot[2] = tt * sa / sbv;    // multiplier of W[a] in the new W[b]
-    rot[3] = cs * sa;          // new scales
-    rot[4] = cs * sbv;
+    rot[1] = cs;
+    rot[2] = cs * tt;
   }
   __syncthreads();
-  const double tt = rot[0];
+  const double tt = rot[0], cs = rot[1], sn = rot[2];
   if (tt == 0.0) return;   // converged pair (uniform)
-  const double ma = rot[1], mb = rot[2];
-  double nsa = rot[3], nsb = rot[4];
-  // rescale a row whose scale became small (uniform decision)
-  const bool fold_a = nsa < 0x1p-100, fold_b = nsb < 0x1p-100;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
-    double xa = fma(ma, y[e], x[e]);
-    double yb = fma(mb, x[e], y[e]);
-    if (fold_a) xa *= nsa;
-    if (fold_b) yb *= nsb;
+    const double xa = cs * x[e] - sn * y[e];
+    const double yb = sn * x[e] + cs * y[e];
     x[e] = xa;
     y[e] = yb;
     if (c < Q) {
@@ -514,54 +497,36 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
       wb[c] = yb;
     }
   }
-  if (fold_a) nsa = 1.0;
-  if (fold_b) nsb = 1.0;
   double na = aa - tt * ab, nb = bb + tt * ab;
   if (na < 0.25 * aa || nb < 0.25 * bb) {   // uniform: every thread has the same values
-    double s2a = 0.0, s2b = 0.0;
+    double sa = 0.0, sb = 0.0;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      s2a = fma(x[e], x[e], s2a);
-      s2b = fma(y[e], y[e], s2b);
+      sa = fma(x[e], x[e], sa);
+      sb = fma(y[e], y[e], sb);
     }
-    na = jac_block_sum(s2a, sh) * (nsa * nsa);
-    nb = jac_block_sum(s2b, sh) * (nsb * nsb);
+    na = jac_block_sum(sa, sh);
+    nb = jac_block_sum(sb, sh);
   }
   if (threadIdx.x == 0) {
     nrm2[a] = na;
     nrm2[b] = nb;
-    scl[a] = nsa;
-    scl[b] = nsb;
     *rot_count = 1;   // "some pair rotated in this sweep" (every writer stores 1)
   }
 }
 
-__global__ void fill_one_kernel(double* __restrict__ v, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = 1.0;
-}
-
-// Fold the row scales into the rows (W[row] *= scl[row], scl = 1) and set the
-// exact squared norms (start of a sweep, and before the singular values).
-__global__ void fold_scales_kernel(double* __restrict__ W, int64_t Q, double* __restrict__ scl,
-                                   double* __restrict__ nrm2) {
+__global__ void row_sqnorms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm2) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= Q) return;
-  const double sc = scl[row];
   double acc = 0.0;
   for (int64_t c = lane; c < Q; c += 32) {
-    const double x = W[row * Q + c] * sc;
-    W[row * Q + c] = x;
+    const double x = W[row * Q + c];
     acc = fma(x, x, acc);
   }
   acc = group_sum<32>(acc);
-  if (lane == 0) {
-    if (nrm2 != nullptr) nrm2[row] = acc;
-    scl[row] = 1.0;
-  }
+  if (lane == 0) nrm2[row] = acc;
 }
-
 
 __global__ void row_norms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -703,21 +668,18 @@ lsrn_status run_precond(Plan* p) {
   // rows in registers when they fit (Q <= 4096), else the streaming warp-per-pair kernel
   const int ept = Q <= 512 ? 4 : Q <= 1024 ? 8 : Q <= 2048 ? 16 : Q <= 4096 ? 32 : 0;
   double* nrm2 = p->tmpq;
-  double* scl = p->sig;   // row scales during the sweeps (sig is written after them)
-  if (ept > 0) launch(fill_one_kernel, (unsigned)((Q + 255) / 256), 256, 0, st, scl, Q);
   if (P > 1) {
     do {
       LSRN_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int), st));
       if (ept > 0)
-        launch(fold_scales_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, scl,
-               nrm2);
+        launch(row_sqnorms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, nrm2);
       for (int t = 0; t < P - 1; ++t) {
         const dim3 pg((unsigned)(P / 2));
         switch (ept) {
-          case 4: launch(jacobi_pair_kernel<4>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, scl, rot); break;
-          case 8: launch(jacobi_pair_kernel<8>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, scl, rot); break;
-          case 16: launch(jacobi_pair_kernel<16>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, scl, rot); break;
-          case 32: launch(jacobi_pair_kernel<32>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, scl, rot); break;
+          case 4: launch(jacobi_pair_kernel<4>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          case 8: launch(jacobi_pair_kernel<8>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          case 16: launch(jacobi_pair_kernel<16>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+          case 32: launch(jacobi_pair_kernel<32>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
           default: launch(jacobi_round_kernel, dim3(rblocks), dim3(256), 0, st, p->Wj, Q, P, t, tol, rot);
         }
       }
@@ -728,9 +690,6 @@ lsrn_status run_precond(Plan* p) {
     } while (host_rot > 0 && sweeps < max_sweeps);
   }
   p->sweeps = sweeps;
-  if (ept > 0 && P > 1)
-    launch(fold_scales_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, scl,
-           (double*)nullptr);
   if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;
   // 3. sigma, order, rank, N.
   launch(row_norms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, p->tmpq);
