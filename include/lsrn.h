@@ -79,8 +79,9 @@ typedef enum {
                                    pipe with error-free products and double-float sums folded
                                    into FP64 every 64 rows (relative error of each product and
                                    sum ~2^-48, against 2^-53 in FP64).  Tall and fat; the
-                                   sweep keeps tol, and refinement stays double-double on the
-                                   FP64 A with at least two steps (early stop as usual).
+                                   sweep stops at max(tol, 1e-8) and at least two refinement
+                                   steps follow (early stop as usual), with the residual
+                                   r = b - Ax and A^T r exact to ~2^-65 (three FP32 planes).
                                    Vectors and row coefficients are rescaled by powers of two
                                    inside the pass, so any finite A, b work. */
 } lsrn_iter_mode;

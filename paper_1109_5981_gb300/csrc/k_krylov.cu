@@ -446,9 +446,13 @@ static lsrn_status iterate(Plan* p, int cap, F body) {
   return LSRN_OK;
 }
 
-// Tolerance of the main sweep: the option, or the FP32 floor when passes run in FP32.
+// Tolerance of the main sweep: the option, or a looser one when refinement
+// (at least two steps, each contracting the error by ~refine_tol) follows
+// anyway: the FP32 floor in FP32 mode, 1e-8 in double-float mode.
 static double sweep_tol(const Plan* p) {
-  return p->X32 != nullptr ? std::max(p->opt.tol, 1e-6) : p->opt.tol;
+  if (p->X32 != nullptr) return std::max(p->opt.tol, 1e-6);
+  if (p->X2h != nullptr && p->opt.refine_max > 0) return std::max(p->opt.tol, 1e-8);
+  return p->opt.tol;
 }
 
 static int lsqr_cap(const Plan* p) {
