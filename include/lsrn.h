@@ -78,9 +78,9 @@ typedef enum {
                                    the exponent of max |A_ij|) and every pass runs on the FP32
                                    pipe with error-free products and double-float sums folded
                                    into FP64 every 64 rows (relative error of each product and
-                                   sum ~2^-48, against 2^-53 in FP64).  Tall and fat; the
-                                   sweep stops at max(tol, 1e-8) and at least two refinement
-                                   steps follow (early stop as usual), with the residual
+                                   sum ~2^-48, against 2^-53 in FP64).  Tall and fat; for
+                                   m >= n the sweep stops at max(tol, 1e-8); at least two
+                                   refinement steps follow (early stop as usual), with the residual
                                    r = b - Ax and A^T r exact to ~2^-65 (three FP32 planes).
                                    Vectors and row coefficients are rescaled by powers of two
                                    inside the pass, so any finite A, b work. */

@@ -448,10 +448,12 @@ static lsrn_status iterate(Plan* p, int cap, F body) {
 
 // Tolerance of the main sweep: the option, or a looser one when refinement
 // (at least two steps, each contracting the error by ~refine_tol) follows
-// anyway: the FP32 floor in FP32 mode, 1e-8 in double-float mode.
+// anyway: the FP32 floor in FP32 mode, 1e-8 in double-float mode for m >= n.
+// (For m < n the correction by CS on M^T B contracts less per step, so the
+// sweep keeps tol.)
 static double sweep_tol(const Plan* p) {
   if (p->X32 != nullptr) return std::max(p->opt.tol, 1e-6);
-  if (p->X2h != nullptr && p->opt.refine_max > 0) return std::max(p->opt.tol, 1e-8);
+  if (p->X2h != nullptr && p->tall && p->opt.refine_max > 0) return std::max(p->opt.tol, 1e-8);
   return p->opt.tol;
 }
 
