@@ -238,3 +238,25 @@ def c3_problem(seed: int = 0, m: int = 10_000, n: int = 1_000_000, nnz_per_row: 
     b = gaussian_vector(m, seed + 7919)
     return A, b
 
+
+
+def serving_mix(count: int, seed: int = 7, device: Optional[str] = None,
+                m_range=(5_000, 200_000), n_range=(32, 512), tall_frac: float = 0.7,
+                log10_cond=(2.0, 6.0)):
+    """Request sizes and problems of the batched / serving mix: m log-uniform in
+    m_range, n log-uniform in n_range, a fraction `tall_frac` stored m x n (the rest
+    as its n x m transpose), rank u * min(m, n) with u ~ U[0.8, 1], condition number
+    10^U[log10_cond], Householder-product factors, noise 1e-4.
+    Returns a list of (DenseProblem, tall) with the problem generated tall
+    (the fat request is its transpose)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        m = int(round(math.exp(rng.uniform(math.log(m_range[0]), math.log(m_range[1])))))
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        tall = bool(rng.random() < tall_frac)
+        rank = max(1, int(math.ceil(rng.uniform(0.8, 1.0) * min(m, n))))
+        cond = 10.0 ** rng.uniform(*log10_cond)
+        P = dense_householder(m, n, rank, cond, 1e-4, seed * 100_003 + k, device=device)
+        out.append((P, tall))
+    return out
