@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) row_pass_staged_kernel(
 // kFoldRows rows, which also bounds the error of their lazy low words.  Only
 // contributions below 2^-126 of the largest vin entry or row coefficient lose
 // bits.
-constexpr int kFoldRows = 128;
+constexpr int kFoldRows = 256;
 constexpr int kNoExp = -100000;
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
@@ -708,6 +708,8 @@ __global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
       for (int r = 0; r < RB; ++r) {
         float h = 0.0f, l = 0.0f;
         if (have && r < nr) {
+          // two independent chains (even and odd columns), joined once
+          float h1 = 0.0f, l1 = 0.0f;
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
             const int c = 2 * tid + 2 * kThreads * s;
@@ -715,9 +717,13 @@ __global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
               const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
               const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
               df_fma(a.x, b.x, vh[s][0], vl[s][0], h, l);
-              df_fma(a.y, b.y, vh[s][1], vl[s][1], h, l);   // vin is 0 past C
+              df_fma(a.y, b.y, vh[s][1], vl[s][1], h1, l1);   // vin is 0 past C
             }
           }
+          float sum, er;
+          two_sum_f(h, h1, sum, er);
+          h = sum;
+          l += l1 + er;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
