@@ -275,7 +275,8 @@ lsrn_status lsrn_sketch_f64_noalloc(const double* A, int64_t m, int64_t n, int64
  *   solver            0 = LSQR, 1 = CS.
  * A request is admitted when a slot is free and its estimated device footprint
  * (the copy of A, the sketch, the factors, the vectors, the tensor-core
- * scratch) fits what the running requests leave of the budget; the oldest
+ * scratch, the FP32 planes of the mixed iteration modes) fits what the running
+ * requests leave of the budget; the oldest
  * queued request that fits goes first.  Each slot has its own worker thread
  * and non-blocking stream on the device current at lsrn_server_create.
  * QUEUE_FULL when a single request alone exceeds the budget; INVALID_ARG for
