@@ -282,7 +282,7 @@ lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host) {
   const int64_t m = A->m, n = A->n, nnz = A->nnz;
   auto alloc = [&](void** ptr, size_t bytes) -> lsrn_status {
     *ptr = nullptr;
-    cudaError_t e = cudaMallocAsync(ptr, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = lsrn_malloc_async(ptr, std::max<size_t>(bytes, 16), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? LSRN_ERR_OOM : LSRN_ERR_CUDA;
@@ -302,7 +302,7 @@ lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host) {
     if (nnz) LSRN_CUDA_TRY(cudaMemcpyAsync(cv, A->values, nnz * sizeof(double), cudaMemcpyDefault, st));
   } else if (nnz) {
     float* tmp = nullptr;
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&tmp, nnz * sizeof(float), st));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&tmp, nnz * sizeof(float), st));
     LSRN_CUDA_TRY(cudaMemcpyAsync(tmp, A->values, nnz * sizeof(float), cudaMemcpyDefault, st));
     launch(widen_kernel, dim3((unsigned)((nnz + 255) / 256)), dim3(256), 0, st, (const float*)tmp, nnz, cv);
     cudaFreeAsync(tmp, st);
@@ -310,7 +310,7 @@ lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host) {
   (void)host;
   // validate structure
   int* bad = nullptr;
-  LSRN_CUDA_TRY(cudaMallocAsync((void**)&bad, sizeof(int), st));
+  LSRN_CUDA_TRY(lsrn_malloc_async((void**)&bad, sizeof(int), st));
   LSRN_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
   launch(csr_validate_kernel, dim3((unsigned)((m + 255) / 256)), dim3(256), 0, st,
          (const int64_t*)rp, (const int32_t*)ci, m, n, nnz, bad);
@@ -328,10 +328,10 @@ lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host) {
   LSRN_TRY(alloc((void**)&cvT, nnz * sizeof(double)));
   if (nnz > 0) {
     int32_t *row = nullptr, *idx = nullptr, *keys_out = nullptr, *perm = nullptr;
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&row, nnz * sizeof(int32_t), st));
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&idx, nnz * sizeof(int32_t), st));
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&keys_out, nnz * sizeof(int32_t), st));
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&perm, nnz * sizeof(int32_t), st));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&row, nnz * sizeof(int32_t), st));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&idx, nnz * sizeof(int32_t), st));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&keys_out, nnz * sizeof(int32_t), st));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&perm, nnz * sizeof(int32_t), st));
     launch(expand_rows_kernel, dim3((unsigned)((m + 255) / 256)), dim3(256), 0, st,
            (const int64_t*)rp, m, row, idx);
     int end_bit = 1;
@@ -340,7 +340,7 @@ lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host) {
     cub::DeviceRadixSort::SortPairs(nullptr, temp, (const int32_t*)ci, keys_out, (const int32_t*)idx,
                                     perm, (int)nnz, 0, end_bit, st);
     void* tbuf = nullptr;
-    LSRN_CUDA_TRY(cudaMallocAsync(&tbuf, std::max<size_t>(temp, 16), st));
+    LSRN_CUDA_TRY(lsrn_malloc_async(&tbuf, std::max<size_t>(temp, 16), st));
     LSRN_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tbuf, temp, (const int32_t*)ci, keys_out,
                                                   (const int32_t*)idx, perm, (int)nnz, 0, end_bit,
                                                   st));

@@ -508,7 +508,7 @@ static lsrn_status upload_coefs(Plan* p, const std::vector<double>& t) {
   if ((int64_t)t.size() > p->ncoef) {
     if (p->coefs) cudaFreeAsync(p->coefs, p->stream);
     p->coefs = nullptr;
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&p->coefs, t.size() * sizeof(double), p->stream));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&p->coefs, t.size() * sizeof(double), p->stream));
     p->ncoef = (int64_t)t.size();
   }
   LSRN_CUDA_TRY(cudaMemcpyAsync(p->coefs, t.data(), t.size() * sizeof(double),

@@ -632,7 +632,7 @@ lsrn_status run_precond(Plan* p) {
     const size_t ws = ((size_t)max_chunks * kQrNb * Q + (size_t)kQrNb * Q + kQrNb * kQrNb) *
                       sizeof(double);
     double* qws = nullptr;
-    LSRN_CUDA_TRY(cudaMallocAsync((void**)&qws, ws, st));
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&qws, ws, st));
     double* Wpart = qws;
     double* W2 = Wpart + (size_t)max_chunks * kQrNb * Q;
     double* Tm = W2 + (size_t)kQrNb * Q;

@@ -27,6 +27,42 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
   if (getenv("LSRN_VERBOSE")) fprintf(stderr, "lsrn: %s\n", g_last_error);
 }
 
+// Stream-ordered allocations of the library come from one memory pool per
+// device that keeps up to a quarter of the device memory reserved after frees,
+// so repeated plans (each holding tens of GB of planes and scratch) reuse
+// mapped memory instead of returning it to the driver at every synchronisation.
+// The process-wide default pool is left as it is.
+cudaError_t lsrn_malloc_async(void** ptr, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaMallocAsync(ptr, bytes, st);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (pools[dev] == nullptr) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t p = nullptr;
+      if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaMallocAsync(ptr, bytes, st);
+      }
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      uint64_t keep = total_b / 4;
+      cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+      pools[dev] = p;
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
 int num_sms() {
   static std::atomic<int> cached[64];
   int dev = 0;
@@ -96,7 +132,7 @@ lsrn_status gather_matrix(const void* src, int dtype, int64_t ld_row, int64_t ld
 static lsrn_status dalloc(Plan* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(ptr, bytes, p->stream);
+  cudaError_t e = lsrn_malloc_async(ptr, bytes, p->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     record_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -386,7 +422,7 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
     }
     const size_t scratch = sketch_tc_scratch_bytes(seg, p->q, p->s);
     void* buf = nullptr;
-    LSRN_CUDA_TRY(cudaMallocAsync(&buf, scratch, p->stream));
+    LSRN_CUDA_TRY(lsrn_malloc_async(&buf, scratch, p->stream));
     LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), p->stream));
     lsrn_status st = launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
                                       tag, p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR,
@@ -396,7 +432,7 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
   } else {
     const size_t scratch = sketch_f64_scratch_bytes(p->xrows, p->q, p->s);
     double* buf = nullptr;
-    if (scratch) LSRN_CUDA_TRY(cudaMallocAsync((void**)&buf, scratch, p->stream));
+    if (scratch) LSRN_CUDA_TRY(lsrn_malloc_async((void**)&buf, scratch, p->stream));
     lsrn_status st = launch_sketch_f64(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
                                        tag, p->Xs, p->q, buf, scratch, p->stream);
     if (buf) cudaFreeAsync(buf, p->stream);
@@ -578,8 +614,8 @@ lsrn_status lsrn_generate_sketch_block(uint64_t seed, uint32_t tag, int64_t i0, 
   double* gd = g;
   float* zd = z;
   const size_t tot = (size_t)(rows * cols);
-  if (g && !gdev) LSRN_CUDA_TRY(cudaMallocAsync((void**)&gd, tot * sizeof(double), st));
-  if (z && !zdev) LSRN_CUDA_TRY(cudaMallocAsync((void**)&zd, tot * sizeof(float), st));
+  if (g && !gdev) LSRN_CUDA_TRY(lsrn_malloc_async((void**)&gd, tot * sizeof(double), st));
+  if (z && !zdev) LSRN_CUDA_TRY(lsrn_malloc_async((void**)&zd, tot * sizeof(float), st));
   lsrn_status res = launch_gamma_block(seed, tag, i0, j0, rows, cols, gd, zd, st);
   if (g && !gdev) {
     cudaMemcpyAsync(g, gd, tot * sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -28,6 +28,8 @@ namespace lsrn {
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 int num_sms();
+// Stream-ordered allocation from the library's memory pool of the current device.
+cudaError_t lsrn_malloc_async(void** ptr, size_t bytes, cudaStream_t st);
 
 // ---- device scalar block (one per plan) -----------------------------------
 enum ScalarSlot : int {
