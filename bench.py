@@ -57,9 +57,10 @@ def parse(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "serving"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "serving", "c1"],
                     help="dense: the 1e6 x 2000 solve; serving: a Poisson stream of mixed-size "
-                         "requests through lsrn_submit/lsrn_poll")
+                         "requests through lsrn_submit/lsrn_poll; c1: latency of the 2000 x 100 "
+                         "rank-80 FP64 solve")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: all at once)")
     ap.add_argument("--slots", type=int, default=8)
@@ -354,12 +355,77 @@ def run_serving(args):
     return 0
 
 
+def run_small(args):
+    """The 2000 x 100 rank-80 problem (sigma 1 -> 1e-6, Haar factors, noise 1e-3,
+    gamma 2, LSQR tol 1e-14, FP64 sketch and passes): latency of one solve,
+    plan to destroy, with A and b resident on the device.  A is 1.6 MB and stays
+    in L2, so the solve is bound by launch and synchronisation latency, not by
+    a roofline."""
+    import torch
+    import paper_1109_5981_gb300 as L
+    import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.load_library()
+    P = W.c1_problem(seed=0)
+    A = torch.from_numpy(np.ascontiguousarray(P.A)).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.empty(P.A.shape[1], dtype=torch.float64, device="cuda")
+    xstar = P.apply_V(P.apply_Ut(P.b) / P.sigma)
+    opts = L.default_options(seed=3, sketch_mode=L.LSRN_SKETCH_F64, iter_mode=L.LSRN_ITER_F64)
+    solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
+
+    def step():
+        plan = L.lsrn_plan(A, opts)
+        try:
+            _, info = solve_fn(plan, b, x)
+        finally:
+            plan.close()
+        return info
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(args.steps, 50)
+    lat = []
+    launches0 = L.kernel_launches()
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        info = step()
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t0) * 1e3)
+    launches = L.kernel_launches() - launches0
+    lat = np.array(lat)
+    err = rel_error(x.cpu().numpy(), xstar)
+    line = {
+        "metric": "LS solve latency (dense 2000x100 rank 80, FP64 plain LSRN, plan to destroy)",
+        "value": float(np.median(lat)) * 1e3, "unit": "us", "higher_is_better": False,
+        "n_gpus": 1, "steps": steps, "warmup": max(args.warmup, 3),
+        "latency_us": {"p50": float(np.percentile(lat, 50)) * 1e3,
+                       "p99": float(np.percentile(lat, 99)) * 1e3},
+        "solves_per_s": float(steps / (lat.sum() * 1e-3)),
+        "rel_err": err, "within_1e-10": bool(err <= 1e-10),
+        "phases_ms": {"sketch": info["t_sketch_ms"], "precond": info["t_precond_ms"],
+                      "iterations": info["t_iter_ms"], "refinement": info["t_refine_ms"]},
+        "iterations": info["iterations"], "jacobi_sweeps": info["jacobi_sweeps"],
+        "gpu_launches": launches, "dtype": "f64", "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": "dense 2000x100, rank 80, sigma log-spaced 1 -> 1e-6, Haar factors, "
+                               "noise 1e-3, gamma 2 (s = 200); A resident in HBM (and L2)",
+                   "solver": args.solver, "sketch": "f64", "passes": "f64"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "c1":
+        return run_small(args)
     import torch
     import paper_1109_5981_gb300 as L
     import workloads as W

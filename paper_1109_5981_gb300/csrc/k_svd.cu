@@ -668,26 +668,42 @@ lsrn_status run_precond(Plan* p) {
   // rows in registers when they fit (Q <= 4096), else the streaming warp-per-pair kernel
   const int ept = Q <= 512 ? 4 : Q <= 1024 ? 8 : Q <= 2048 ? 16 : Q <= 4096 ? 32 : 0;
   double* nrm2 = p->tmpq;
+  // One sweep: reset the rotation flag, exact squared norms, P - 1 rounds.
+  auto issue_sweep = [&]() {
+    cudaMemsetAsync(rot, 0, sizeof(int), st);
+    if (ept > 0)
+      launch(row_sqnorms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, nrm2);
+    for (int t = 0; t < P - 1; ++t) {
+      const dim3 pg((unsigned)(P / 2));
+      switch (ept) {
+        case 4: launch(jacobi_pair_kernel<4>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+        case 8: launch(jacobi_pair_kernel<8>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+        case 16: launch(jacobi_pair_kernel<16>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+        case 32: launch(jacobi_pair_kernel<32>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
+        default: launch(jacobi_round_kernel, dim3(rblocks), dim3(256), 0, st, p->Wj, Q, P, t, tol, rot);
+      }
+    }
+  };
   if (P > 1) {
+    // The sweep is captured once into a CUDA graph and replayed for every
+    // sweep: the same kernels with the same arguments, without the host
+    // launch overhead of P - 1 rounds (about 2 us a round).  If the capture
+    // fails the sweeps are launched one kernel at a time.
+    unsigned long long nodes = 0;
+    cudaGraphExec_t sweep_graph = capture_graph(st, issue_sweep, &nodes);
     do {
-      LSRN_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int), st));
-      if (ept > 0)
-        launch(row_sqnorms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, nrm2);
-      for (int t = 0; t < P - 1; ++t) {
-        const dim3 pg((unsigned)(P / 2));
-        switch (ept) {
-          case 4: launch(jacobi_pair_kernel<4>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
-          case 8: launch(jacobi_pair_kernel<8>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
-          case 16: launch(jacobi_pair_kernel<16>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
-          case 32: launch(jacobi_pair_kernel<32>, pg, kJacThreads, 0, st, p->Wj, Q, P, t, tol, nrm2, rot); break;
-          default: launch(jacobi_round_kernel, dim3(rblocks), dim3(256), 0, st, p->Wj, Q, P, t, tol, rot);
-        }
+      if (sweep_graph != nullptr) {
+        LSRN_CUDA_TRY(cudaGraphLaunch(sweep_graph, st));
+        g_kernel_launches.fetch_add(nodes, std::memory_order_relaxed);
+      } else {
+        issue_sweep();
       }
       LSRN_CUDA_TRY(cudaGetLastError());
       LSRN_CUDA_TRY(cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st));
       LSRN_CUDA_TRY(cudaStreamSynchronize(st));
       ++sweeps;
     } while (host_rot > 0 && sweeps < max_sweeps);
+    if (sweep_graph != nullptr) cudaGraphExecDestroy(sweep_graph);
   }
   p->sweeps = sweeps;
   if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;

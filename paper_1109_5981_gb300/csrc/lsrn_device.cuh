@@ -29,6 +29,38 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+// Capture the stream work that `issue` enqueues on `st` into an executable
+// CUDA graph (capture mode local to the calling thread, so other threads'
+// plans and servers are unaffected).  Returns nullptr, with the stream back in
+// normal mode and the error cleared, if capture or instantiation fails; the
+// caller then issues the work directly.  *kernels receives the number of
+// kernel launches in the graph; they are not counted as launched until the
+// graph is.
+template <class F>
+inline cudaGraphExec_t capture_graph(cudaStream_t st, F issue, unsigned long long* kernels) {
+  *kernels = 0;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const unsigned long long before = g_kernel_launches.load(std::memory_order_relaxed);
+  issue();
+  const unsigned long long after = g_kernel_launches.load(std::memory_order_relaxed);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess && g != nullptr) e = cudaGraphInstantiate(&ex, g, 0);
+  if (g != nullptr) cudaGraphDestroy(g);
+  g_kernel_launches.fetch_sub(after - before, std::memory_order_relaxed);
+  if (e != cudaSuccess || ex == nullptr) {
+    if (ex != nullptr) cudaGraphExecDestroy(ex);
+    cudaGetLastError();
+    return nullptr;
+  }
+  *kernels = after - before;
+  return ex;
+}
+
 struct U4 {
   uint32_t x, y, z, w;
 };
