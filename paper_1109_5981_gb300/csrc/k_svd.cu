@@ -690,7 +690,7 @@ lsrn_status run_precond(Plan* p) {
     // launch overhead of P - 1 rounds (about 2 us a round).  If the capture
     // fails the sweeps are launched one kernel at a time.
     unsigned long long nodes = 0;
-    cudaGraphExec_t sweep_graph = capture_graph(st, issue_sweep, &nodes);
+    cudaGraphExec_t sweep_graph = p->graph_sweeps ? capture_graph(st, issue_sweep, &nodes) : nullptr;
     do {
       if (sweep_graph != nullptr) {
         LSRN_CUDA_TRY(cudaGraphLaunch(sweep_graph, st));

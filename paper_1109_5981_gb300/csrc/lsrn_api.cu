@@ -276,6 +276,12 @@ using namespace lsrn;
 
 struct lsrn_plan_s : Plan {};
 
+namespace lsrn {
+void plan_disable_sweep_graphs(lsrn_plan_t p) {
+  if (p != nullptr) p->graph_sweeps = false;
+}
+}  // namespace lsrn
+
 extern "C" {
 
 const char* lsrn_status_string(lsrn_status s) {

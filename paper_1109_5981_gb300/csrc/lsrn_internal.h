@@ -129,6 +129,10 @@ struct Plan {
   double sigma_max = 0.0, sigma_min = 0.0;
   int sweeps = 0;
   int state = 0;                    // 0 planned, 1 sketched, 2 preconditioned
+  // Replay each Jacobi sweep from a captured CUDA graph.  Off for plans run by
+  // the server: there several streams share the GPU and fill one another's
+  // launch gaps, and the per-plan capture only adds host work.
+  bool graph_sweeps = true;
 
   // iteration workspace
   double* scal = nullptr;           // SC_COUNT doubles
@@ -192,6 +196,8 @@ bool is_device_pointer(const void* ptr);
 
 // SVD / preconditioner: Xs (S x Q) -> N (Q x r), NT, sig; returns rank
 lsrn_status run_precond(Plan* p);
+// Server-owned plans launch the Jacobi rounds directly (see Plan::graph_sweeps).
+void plan_disable_sweep_graphs(lsrn_plan_t p);
 
 // fused passes
 lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "lsrn.h"
+#include "lsrn_internal.h"
 
 namespace {
 
@@ -102,6 +103,7 @@ struct lsrn_server_s {
       res.x.assign((size_t)req->A.n, 0.0);
       lsrn_status s = lsrn_plan(&req->A, &req->opt, st, &plan);
       if (s == LSRN_OK) {
+        lsrn::plan_disable_sweep_graphs(plan);
         s = req->solver == 1 ? lsrn_solve_cs(plan, req->b.data(), res.x.data(), &res.info)
                              : lsrn_solve_lsqr(plan, req->b.data(), res.x.data(), &res.info);
         lsrn_plan_destroy(plan);
