@@ -6,8 +6,9 @@
 //    with the compact WY form beyond.
 // 2. One-sided (Hestenes) Jacobi on Y = R^T: rotate pairs of columns of Y
 //    (= rows of R, contiguous in memory) until all pairs are orthogonal to
-//    |y_a . y_b| <= tol ||y_a|| ||y_b||; parallel round-robin ordering, one
-//    kernel per round.  With Y J = W (orthogonal columns, norms sigma_j),
+//    |y_a . y_b| <= tol ||y_a|| ||y_b||; parallel round-robin ordering.  For
+//    q > 1024 one persistent kernel per sweep runs the rounds as a dataflow
+//    (each pair waits for its two rows); otherwise one kernel per round.  With Y J = W (orthogonal columns, norms sigma_j),
 //    R = J Sigma U_W^T, so the right singular vectors of Xs are W Sigma^-1.
 // 3. sigma sorted descending, rank r = #{sigma_j > rcond * sigma_1},
 //    N = V~ Sigma~^-1 = W_r Sigma_r^-2 (Q x r), also stored transposed.
@@ -515,6 +516,158 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
   }
 }
 
+// ---- dataflow sweep: one persistent launch per sweep (q > 1024) ----
+// Work item i = t * (P/2) + k is pair k of round t of the round-robin order.
+// CTAs take items in increasing order from an atomic counter.  An item waits
+// until both of its rows have finished round t - 1 (per-row counters ver[row]),
+// rotates them exactly as jacobi_pair_kernel does and publishes ver = t + 1.
+// Every dependency of an item has a smaller index, and all smaller items were
+// taken by running CTAs, so the smallest unfinished item can always proceed:
+// no barrier between rounds, no tail of a partial wave, one launch per sweep.
+// Each row sees the same rotations in the same order as with one launch per
+// round, so the result is the same bit for bit.
+// ws[0]: next item, ws[1]: error flag (a wait gave up), ws[2 + row]: ver[row].
+// A wait polls at most kJacSpinLimit times (well under a second); then the
+// CTA raises the flag, every CTA stops at its next item or poll, and the
+// preconditioner returns LSRN_ERR_TIMEOUT.
+constexpr int kJacSpinLimit = 1 << 20;
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// EPT = 16 is held to 95 registers (5 CTAs per SM) without spills.
+template <int EPT>
+__global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
+    jacobi_flow_kernel(double* __restrict__ W, int64_t Q, int P, double tol,
+                       double* __restrict__ nrm2, int* __restrict__ rot_count,
+                       int* __restrict__ ws) {
+  __shared__ double sh[kJacThreads / 32];
+  __shared__ double rot[3];
+  __shared__ int s_item, s_ok;
+  int* next = ws;
+  int* err = ws + 1;
+  int* ver = ws + 2;
+  const int npairs = P / 2;
+  const int total = (P - 1) * npairs;
+  for (;;) {
+    __syncthreads();   // the previous item is done with s_item, rot and sh
+    if (threadIdx.x == 0) {
+      const int item = atomicAdd(next, 1);
+      int ok = 0;
+      if (item < total && ld_acquire_gpu(err) == 0) {
+        const int t = item / npairs, k = item % npairs;
+        const int a = k == 0 ? P - 1 : (t + k) % (P - 1);
+        const int b = k == 0 ? t : (t - k + P - 1) % (P - 1);
+        ok = 1;
+        for (int it = 0;; ++it) {
+          const bool ra = a >= Q || ld_acquire_gpu(ver + a) >= t;
+          const bool rb = b >= Q || ld_acquire_gpu(ver + b) >= t;
+          if (ra && rb) break;
+          if (it >= kJacSpinLimit || ((it & 63) == 63 && ld_acquire_gpu(err) != 0)) {
+            atomicExch(err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+        __threadfence();   // the rows published with ver are read after this point
+      }
+      s_item = item;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total || s_ok == 0) return;   // uniform
+    const int t = item / npairs, k = item % npairs;
+    int a = k == 0 ? P - 1 : (t + k) % (P - 1);
+    int b = k == 0 ? t : (t - k + P - 1) % (P - 1);
+    if (a >= Q || b >= Q) {   // the row without a partner this round only advances
+      if (threadIdx.x == 0) {
+        const int r = a < Q ? a : b;
+        if (r < Q) st_release_gpu(ver + r, t + 1);
+      }
+      continue;
+    }
+    if (a > b) {
+      const int tmp = a;
+      a = b;
+      b = tmp;
+    }
+    double* wa = W + (int64_t)a * Q;
+    double* wb = W + (int64_t)b * Q;
+    const double aa = __ldcg(nrm2 + a), bb = __ldcg(nrm2 + b);
+    double x[EPT], y[EPT];
+    double ab = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
+      x[e] = c < Q ? __ldcg(wa + c) : 0.0;
+      y[e] = c < Q ? __ldcg(wb + c) : 0.0;
+      ab = fma(x[e], y[e], ab);
+    }
+    ab = jac_block_sum(ab, sh);
+    if (threadIdx.x == 0) {
+      double tt = 0.0, cs = 1.0;
+      if (aa != 0.0 && bb != 0.0 && fabs(ab) > tol * sqrt(aa) * sqrt(bb)) {
+        const double zeta = (bb - aa) / (2.0 * ab);
+        if (fabs(zeta) > 1e150) {
+          tt = 0.5 / zeta;
+        } else {
+          tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        }
+        cs = 1.0 / sqrt(1.0 + tt * tt);
+      }
+      rot[0] = tt;
+      rot[1] = cs;
+      rot[2] = cs * tt;
+    }
+    __syncthreads();
+    const double tt = rot[0], cs = rot[1], sn = rot[2];
+    if (tt != 0.0) {   // uniform
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
+        const double xa = cs * x[e] - sn * y[e];
+        const double yb = sn * x[e] + cs * y[e];
+        x[e] = xa;
+        y[e] = yb;
+        if (c < Q) {
+          wa[c] = xa;
+          wb[c] = yb;
+        }
+      }
+      double na = aa - tt * ab, nb = bb + tt * ab;
+      if (na < 0.25 * aa || nb < 0.25 * bb) {   // uniform
+        double sa = 0.0, sb = 0.0;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          sa = fma(x[e], x[e], sa);
+          sb = fma(y[e], y[e], sb);
+        }
+        na = jac_block_sum(sa, sh);
+        nb = jac_block_sum(sb, sh);
+      }
+      if (threadIdx.x == 0) {
+        nrm2[a] = na;
+        nrm2[b] = nb;
+        *rot_count = 1;
+      }
+      __threadfence();   // this thread's row (and norm) stores before the release below
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st_release_gpu(ver + a, t + 1);
+      st_release_gpu(ver + b, t + 1);
+    }
+  }
+}
+
 __global__ void row_sqnorms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm2) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -668,11 +821,38 @@ lsrn_status run_precond(Plan* p) {
   // rows in registers when they fit (Q <= 4096), else the streaming warp-per-pair kernel
   const int ept = Q <= 512 ? 4 : Q <= 1024 ? 8 : Q <= 2048 ? 16 : Q <= 4096 ? 32 : 0;
   double* nrm2 = p->tmpq;
+  // q > 1024 (16 or 32 elements of a row per thread): the dataflow sweep.  At
+  // smaller q the rows are short and the chain of rounds bounds it, so the
+  // rounds are launched one by one (from a graph).
+  const bool flow = ept >= 16;
+  int* jws = nullptr;
+  int flow_grid = 0;
+  if (flow) {
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&jws, (Q + 2) * sizeof(int), st));
+    int per_sm = 0;
+    if (ept == 16)
+      LSRN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_flow_kernel<16>,
+                                                                  kJacThreads, 0));
+    else
+      LSRN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_flow_kernel<32>,
+                                                                  kJacThreads, 0));
+    const int64_t items = (int64_t)(P - 1) * (P / 2);
+    flow_grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * num_sms(), items));
+  }
   // One sweep: reset the rotation flag, exact squared norms, P - 1 rounds.
   auto issue_sweep = [&]() {
     cudaMemsetAsync(rot, 0, sizeof(int), st);
     if (ept > 0)
       launch(row_sqnorms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, nrm2);
+    if (flow) {
+      cudaMemsetAsync(jws, 0, (Q + 2) * sizeof(int), st);
+      if (ept == 16)
+        launch(jacobi_flow_kernel<16>, flow_grid, kJacThreads, 0, st, p->Wj, Q, P, tol, nrm2, rot, jws);
+      else
+        launch(jacobi_flow_kernel<32>, flow_grid, kJacThreads, 0, st, p->Wj, Q, P, tol, nrm2, rot, jws);
+      return;
+    }
     for (int t = 0; t < P - 1; ++t) {
       const dim3 pg((unsigned)(P / 2));
       switch (ept) {
@@ -700,11 +880,20 @@ lsrn_status run_precond(Plan* p) {
       }
       LSRN_CUDA_TRY(cudaGetLastError());
       LSRN_CUDA_TRY(cudaMemcpyAsync(&host_rot, rot, sizeof(int), cudaMemcpyDeviceToHost, st));
+      int flow_err = 0;
+      if (flow)
+        LSRN_CUDA_TRY(cudaMemcpyAsync(&flow_err, jws + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
       LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+      if (flow_err != 0) {   // a dependency wait of the dataflow sweep gave up
+        if (sweep_graph != nullptr) cudaGraphExecDestroy(sweep_graph);
+        cudaFreeAsync(jws, st);
+        return LSRN_ERR_TIMEOUT;
+      }
       ++sweeps;
     } while (host_rot > 0 && sweeps < max_sweeps);
     if (sweep_graph != nullptr) cudaGraphExecDestroy(sweep_graph);
   }
+  if (jws != nullptr) cudaFreeAsync(jws, st);
   p->sweeps = sweeps;
   if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;
   // 3. sigma, order, rank, N.
