@@ -197,7 +197,10 @@ lsrn_status lsrn_sketch(lsrn_plan_t p);
 /* Algorithm 1 steps 4-5 / Algorithm 2 steps 4-5: SVD of A~ on the device
  * (Householder QR, then one-sided Jacobi), numerical rank r, and N = V~
  * Sigma~^-1 (n x r) or M = U~ Sigma~^-1 (m x r).  Requires lsrn_sketch first
- * (LSRN_ERR_STATE otherwise).  Synchronises; writes r to *rank_out if non-NULL. */
+ * (LSRN_ERR_STATE otherwise).  Synchronises; writes r to *rank_out if non-NULL.
+ * Returns LSRN_ERR_NOT_CONVERGED if the Jacobi sweeps have not converged after
+ * 40 sweeps, and LSRN_ERR_TIMEOUT if a bounded wait of the dataflow sweep
+ * (min(m, n) > 1024) gave up. */
 lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out);
 
 /* Algorithm 1 steps 6-7 / Algorithm 2 steps 6-7 with LSQR (Paige and Saunders
