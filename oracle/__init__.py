@@ -25,7 +25,7 @@ Sections of the paper followed here:
   * LSQR is the algorithm of Paige and Saunders (ACM TOMS 8(1), 1982), which the
     paper cites and uses but does not print              -> ``lsqr``
 
-Readings of the paper that the oracle takes (each also listed in the design doc):
+Readings of the paper that the oracle takes:
   * Algorithm 3, k = 1: alpha = 1 / (d - c^2 / (2 d)) (the printed formula lacks
     the reciprocal; only this reading reproduces the Chebyshev polynomial
     residual, which a test pins).
