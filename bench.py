@@ -4,21 +4,26 @@
 Workload (N = 1): the dense tall problem A (10^6 x 2000, rank 1800, singular
 values log-spaced 1 -> 1e-6, random orthogonal factors from 8 seeded
 Householder reflectors), b = A x0 + 1e-4 N(0,1), gamma = 2 (s = 4000), LSQR to
-tol 1e-14 plus one refinement step.  One step = one complete solve through the
-C ABI: lsrn_plan + lsrn_sketch + lsrn_precond + lsrn_solve_lsqr (+ destroy),
-i.e. Algorithm 1 steps 1-7, on inputs already resident in HBM.  A (16 GB) is
-larger than L2, so no L2 flush is needed between steps.
+tol 1e-14 plus refinement.  One step = one complete solve through the C ABI:
+lsrn_plan + lsrn_sketch + lsrn_precond + lsrn_solve_lsqr (+ destroy), i.e.
+Algorithm 1 steps 1-7, on inputs already resident in HBM, in the mixed-precision
+configuration (exact tensor-core sketch, double-float passes, FP64 SVD,
+recurrences and refinement).  A (16 GB) is larger than L2, so no L2 flush is
+needed between steps.  The same problem is solved once more in the FP64-plain
+configuration (FP64 sketch and passes) for the "mixed vs FP64 plain" comparison
+of the metric, and per-solve latencies give p50/p99.
 
-Each step's x is checked against the planted-factor closed form
-x* = V Sigma^-1 U^T b computed by the oracle on the host; the line reports the
-worst relative error seen.
+Each solve's x is checked against the planted-factor closed form
+x* = V Sigma^-1 U^T b (computed on the host from the generator's factors, no
+oracle call on the GPU leg); the line reports the worst relative error seen.
 
 Under torchrun (N > 1) every rank solves its own independently seeded problem
 (no collective on the data path; weak scaling) and value = all solves / max
 rank time.
 
 --impl reference times the oracle (plain FP64 CPU LSRN) on bounded samples of
-the same workload on this host's cores and extrapolates to one solve.
+the same workload on this host's cores and extrapolates to one solve with the
+paper's cost model (section 4.3); the factors are printed in the line.
 """
 from __future__ import annotations
 
@@ -37,7 +42,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "LS solves/s at <=1e-10 rel err (dense 1e6x2000 rank 1800, FP64, LSQR + refinement)"
+METRIC = ("LS solves/s at <=1e-10 rel err: mixed precision vs FP64 plain; p50/p99 latency "
+          "(dense 1e6x2000 rank 1800)")
 UNIT = "solves/s"
 M, N, RANK = 1_000_000, 2000, 1800
 
@@ -57,6 +63,8 @@ def parse(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true",
+                    help="skip the FP64-plain comparison solve after the timed region")
     ap.add_argument("--workload", default="dense", choices=["dense", "serving", "c1"],
                     help="dense: the 1e6 x 2000 solve; serving: a Poisson stream of mixed-size "
                          "requests through lsrn_submit/lsrn_poll; c1: latency of the 2000 x 100 "
@@ -126,42 +134,64 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # CPU baseline: the oracle on bounded samples                                  #
 # --------------------------------------------------------------------------- #
+SAMPLE_ROWS = 10_000          # rows of A in the timed sketch sample
+SAMPLE_SVD_N = 240            # columns of the timed Jacobi SVD sample
+
+
 def oracle_sampled_solve_seconds(A_host: np.ndarray, b_host: np.ndarray, iters: int,
                                  refine_passes: int, seed: int = 0) -> dict:
-    """Time the oracle's LSRN stages on samples of the workload and extrapolate
-    to one full solve with the paper's cost model (section 4.3, eq. lsrn_flops):
-    sketch ~ s*m*randn + 2smn (linear in the rows sampled), SVD ~ n^3, each
-    iteration = one application of A and one of A^T."""
+    """Time the oracle's LSRN stages on bounded samples of the workload and
+    extrapolate to one full solve with the paper's cost model (section 4.3, eq.
+    lsrn_flops): the sketch (s*m normals + 2smn) is linear in the rows, the SVD
+    of the s x n sketch cubic in n, and each iteration one product with A and
+    one with A^T.  The stages are the calls oracle.lsrn makes (G from the
+    oracle's generator times A with numpy, the oracle's one-sided Jacobi SVD,
+    A v and A^T u with numpy).  Returns measured seconds, factors and the
+    extrapolated total."""
     import oracle as O
     m, n = A_host.shape
     s = math.ceil(2.0 * n)
     out = {}
     # sketch: G (s x m_s) drawn by the oracle, times A[:m_s]
-    m_s = min(m, 8000)
+    m_s = min(m, SAMPLE_ROWS)
     t = time.perf_counter()
     G = O.sketch_block(seed, 0, 0, m_s, s).T
     At_part = G @ A_host[:m_s]
-    out["sketch_s"] = (time.perf_counter() - t) * (m / m_s)
+    t_sk = time.perf_counter() - t
     del G, At_part
-    # SVD of a (2 n_s) x n_s sketch by the oracle's one-sided Jacobi, scaled by n^3
-    n_s = min(n, 160)
+    # SVD of a (2 n_s) x n_s matrix with the workload's spectrum shape (log-spaced
+    # 1 -> 1e-6 on 90% of the columns) by the oracle's one-sided Jacobi
+    n_s = min(n, SAMPLE_SVD_N)
     rng = np.random.Generator(np.random.PCG64(1))
-    X = rng.standard_normal((2 * n_s, n_s)) @ np.diag(np.logspace(0, -6, n_s))
+    r_s = max(1, int(0.9 * n_s))
+    sig = np.zeros(n_s)
+    sig[:r_s] = np.logspace(0, -6, r_s)
+    U, _ = np.linalg.qr(rng.standard_normal((2 * n_s, n_s)))
+    V, _ = np.linalg.qr(rng.standard_normal((n_s, n_s)))
+    X = (U * sig) @ V.T
     t = time.perf_counter()
     O.jacobi_svd(X)
-    out["svd_s"] = (time.perf_counter() - t) * (n / n_s) ** 3
+    t_svd = time.perf_counter() - t
     # one oracle LSQR-style application of A and A^T on the full matrix
     v = rng.standard_normal(n)
     t = time.perf_counter()
     u = A_host @ v
     w = A_host.T @ u
-    per_pass = time.perf_counter() - t
-    out["iter_s"] = per_pass * (iters + refine_passes)
-    out["total_s"] = out["sketch_s"] + out["svd_s"] + out["iter_s"]
-    out["sample"] = (f"sketch on {m_s} of {m} rows (x{m / m_s:.0f}), Jacobi SVD at "
-                     f"{2 * n_s}x{n_s} (x(n/{n_s})^3), one A and A^T product on the full "
-                     f"matrix (x{iters + refine_passes} passes)")
+    t_pass = time.perf_counter() - t
     del u, w
+    passes = iters + refine_passes
+    f_sk, f_svd = m / m_s, (n / n_s) ** 3
+    out["measured_s"] = {"sketch": t_sk, "svd": t_svd, "pass": t_pass}
+    out["factors"] = {"sketch": f_sk, "svd": f_svd, "pass": passes}
+    out["sketch_s"] = t_sk * f_sk
+    out["svd_s"] = t_svd * f_svd
+    out["iter_s"] = t_pass * passes
+    out["total_s"] = out["sketch_s"] + out["svd_s"] + out["iter_s"]
+    out["sample_s"] = t_sk + t_svd + t_pass
+    out["sample"] = (f"sketch on {m_s} of {m} rows (x{f_sk:.0f}), Jacobi SVD at "
+                     f"{2 * n_s}x{n_s} with the workload's spectrum shape (x(n/{n_s})^3 = "
+                     f"x{f_svd:.0f}), one A and one A^T product on the full matrix "
+                     f"(x{passes} passes)")
     return out
 
 
@@ -177,7 +207,8 @@ def kernel_source_hash(src_file: str, name: str) -> str:
 
 
 KERNEL_SOURCES = {"row_pass_x2_kernel": "k_iter.cu", "dd_pass_x3_kernel": "k_iter.cu",
-                  "sketch_tc_kernel": "k_sketch_tc.cu", "jacobi_pair_kernel": "k_svd.cu"}
+                  "sketch_tc_kernel": "k_sketch_tc.cu", "jacobi_pair_kernel": "k_svd.cu",
+                  "jacobi_flow_kernel": "k_svd.cu"}
 
 
 def traffic_per_unit(kernel: str):
@@ -237,17 +268,20 @@ def run_reference(args):
     t0 = time.perf_counter()
     P = W.c2_problem(seed=0, m=args.m, n=args.n, rank=args.rank)
     gen_s = time.perf_counter() - t0
-    iters = 83
+    iters, refine = 50, 45          # the GPU solve's sweep and refinement passes at this size
     steps = []
     for k in range(args.warmup + args.steps):
-        r = oracle_sampled_solve_seconds(P.A, P.b, iters, 24)
+        r = oracle_sampled_solve_seconds(P.A, P.b, iters, refine)
         if k >= args.warmup:
             steps.append(r)
     tot = float(np.mean([r["total_s"] for r in steps]))
+    sample_ms = float(np.mean([r["sample_s"] for r in steps])) * 1e3
     value = 1.0 / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        # each step times a bounded sample; value extrapolates it to one solve
+        "ms_per_step": sample_ms, "extrapolated_ms_per_solve": tot * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, cond 1e6, "
@@ -257,6 +291,7 @@ def run_reference(args):
                          "sample": steps[-1]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "stages_s": {k: steps[-1][k] for k in ("sketch_s", "svd_s", "iter_s")},
+        "measured_s": steps[-1]["measured_s"], "factors": steps[-1]["factors"],
         "generator_s": gen_s,
     }
     print(json.dumps(line), flush=True)
@@ -418,14 +453,86 @@ def run_small(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "serving":
-        return run_serving(args)
-    if args.workload == "c1":
-        return run_small(args)
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor) nominal rate
+
+
+def phase_rooflines(info_list, args, peaks: dict, fp64_peak: float) -> dict:
+    """Roofline of every large phase of a solve, from the library's per-phase
+    CUDA-event times averaged over the timed solves.  Work is the method's
+    algorithmic work (section 4.3 and the unit counts of the path): the sketch
+    2 s m n flop, the QR 2 s n^2 - 2 n^3 / 3 flop, the SVD of the n x n
+    triangle 11 n^3 flop, each fused pass 8 m n bytes (A streamed once as its
+    two FP32 planes, or once in FP64)."""
+    m, n = args.m, args.n
+    s = info_list[-1]["s"]
+    mean = lambda k: float(np.mean([i[k] for i in info_list]))
+    bf16 = peaks.get("bf16_tflops_sustained", 1707.9)
+    hbm = peaks.get("hbm_gbs", 6785.5)
+    out = {}
+    t_gemm = mean("t_sketch_gemm_ms") if args.sketch == "tc" else mean("t_sketch_ms")
+    flops = 2.0 * s * m * n
+    if args.sketch == "tc":
+        ach = flops / (t_gemm * 1e-3) / 1e12
+        out["sketch"] = {"kernel": "sketch_tc_kernel (tcgen05, exact bf16 digit slices)",
+                         "ms": t_gemm, "bound": "tensor", "achieved": ach, "peak": bf16,
+                         "unit": "TFLOP/s", "frac": ach / bf16,
+                         "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)",
+                         "work": f"2*s*m*n = {flops:.3e} flop (the method's count)",
+                         "slice_products_tflops": 15 * ach,
+                         "slice_products_frac": 15 * ach / bf16}
+    else:
+        ach = flops / (t_gemm * 1e-3) / 1e12
+        out["sketch"] = {"kernel": "sketch_f64_kernel", "ms": t_gemm, "bound": "alu",
+                         "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": ach / fp64_peak, "work": f"2*s*m*n = {flops:.3e} flop",
+                         "peak_source": "FP64 FMA rate probed in this run (lsrn_probe_fp64_fma)"}
+    t_qr = mean("t_qr_ms")
+    qflops = 2.0 * s * n * n - 2.0 * n ** 3 / 3.0
+    ach = qflops / (t_qr * 1e-3) / 1e12 if t_qr > 0 else 0.0
+    out["qr"] = {"kernel": "hh_reflector/hh_w/hh_update (Householder QR of the sketch)", "ms": t_qr,
+                 "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                 "frac": ach / fp64_peak, "work": f"2 s n^2 - 2 n^3/3 = {qflops:.3e} flop",
+                 "peak_source": "FP64 FMA rate probed in this run (lsrn_probe_fp64_fma)"}
+    t_jac = mean("t_jacobi_ms")
+    jflops = 11.0 * n ** 3
+    ach = jflops / (t_jac * 1e-3) / 1e12 if t_jac > 0 else 0.0
+    out["svd"] = {"kernel": "jacobi_flow_kernel (one-sided Jacobi sweeps)", "ms": t_jac,
+                  "sweeps": info_list[-1]["jacobi_sweeps"], "bound": "alu", "achieved": ach,
+                  "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                  "work": f"11 n^3 = {jflops:.3e} flop (the SVD count of section 4.3)",
+                  "peak_source": "FP64 FMA rate probed in this run (lsrn_probe_fp64_fma)"}
+    t_pass_tot = mean("t_pass_ms")
+    n_pass = max(1, int(round(mean("n_pass"))))
+    t_pass = t_pass_tot / n_pass
+    kname = {"x2": "row_pass_x2_kernel (fused A(Nv) and A^T u on two FP32 planes)",
+             "f32": "row_pass_kernel<float> (fused A(Nv) and A^T u on FP32 A)",
+             "f64": "row_pass_staged_kernel<double> (fused A(Nv) and A^T u, FP64)"}[args.iter]
+    streamed = {"x2": 8.0, "f32": 4.0, "f64": 8.0}[args.iter] * m * n
+    gbs = 8.0 * m * n / (t_pass * 1e-3) / 1e9
+    out["passes"] = {"kernel": kname, "ms": t_pass_tot, "launches": n_pass, "ms_each": t_pass,
+                     "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
+                     "work": "8*m*n bytes per pass (A read once, FP64-equivalent)",
+                     "bytes_streamed_per_pass": streamed}
+    return out
+
+
+def traffic_for(phase: str, args):
+    """DRAM bytes per launch of the phase's kernel from profiles/roofline_traffic.md
+    (null once the kernel changed since the capture)."""
+    if phase == "passes" and args.iter == "x2":
+        tpu = traffic_per_unit("row_pass_x2_kernel")
+        return None if tpu is None else tpu * args.m * args.n
+    if phase == "sketch" and args.sketch == "tc":
+        tpu = traffic_per_unit("sketch_tc_kernel")
+        return None if tpu is None else tpu * args.m
+    if phase == "svd":
+        tpu = traffic_per_unit("jacobi_flow_kernel")
+        return None if tpu is None else tpu
+    return None
+
+
+def run_dense(args):
     import torch
     import paper_1109_5981_gb300 as L
     import workloads as W
@@ -454,8 +561,8 @@ def main():
                                  args.iter, L.LSRN_ITER_F64))
     solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
 
-    def step():
-        plan = L.lsrn_plan(A, opts)
+    def step(o=opts):
+        plan = L.lsrn_plan(A, o)
         try:
             _, info = solve_fn(plan, b, x)
         finally:
@@ -470,87 +577,53 @@ def main():
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     launches0 = L.kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.synchronize()
-    ev0.record()
+    evs[0].record()
     infos = []
-    for _ in range(args.steps):
+    for k in range(args.steps):
         infos.append(step())
-    ev1.record()
+        evs[k + 1].record()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = evs[0].elapsed_time(evs[-1])
+    per_step = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
     launches = L.kernel_launches() - launches0
     clk = clocks.stop()
     errs = [rel_error(x.cpu().numpy(), xstar)]   # every step solves the same problem
     elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     value = job_throughput(world, args.steps, elapsed_ms)
     info = infos[-1]
-    s = info["s"]
-    t_sketch = float(np.mean([i["t_sketch_ms"] for i in infos]))
     fp64_peak = L.probe_fp64_fma()
     peaks = _measured_peaks()
-    # dominant kernel: the sketch GEMM or the fused pass over A (total per step)
-    t_gemm = float(np.mean([i["t_sketch_gemm_ms"] for i in infos])) if args.sketch == "tc" else t_sketch
-    t_pass_tot = float(np.mean([i["t_pass_ms"] for i in infos]))
-    n_pass = max(1, int(np.mean([i["n_pass"] for i in infos])))
-    t_pass = t_pass_tot / n_pass
-    if t_gemm >= t_pass_tot:
-        if args.sketch == "tc":
-            # 15 exact bf16 slice products of the s x m x n contraction per solve
-            flops = 15 * 2.0 * s * args.m * args.n
-            peak = peaks.get("bf16_tflops_sustained", 1779.5)
-            achieved = flops / (t_gemm * 1e-3) / 1e12
-            tpu = traffic_per_unit("sketch_tc_kernel")
-            roofline = {"kernel": "sketch_tc_kernel (tcgen05, bf16 digit slices)", "bound": "tensor",
-                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak,
-                        "traffic": None if tpu is None else tpu * args.m,
-                        "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)",
-                        "work_per_launch": "15 slice products x 2*s*m*n over all segments",
-                        "fp64_equivalent_tflops": 2.0 * s * args.m * args.n / (t_gemm * 1e-3) / 1e12}
-        else:
-            flops = 2.0 * s * args.m * args.n
-            achieved = flops / (t_gemm * 1e-3) / 1e12
-            roofline = {"kernel": "sketch_f64_kernel", "bound": "alu", "achieved": achieved,
-                        "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                        "traffic": None,
-                        "peak_source": "FP64 FMA throughput measured in this run (lsrn_probe_fp64_fma)",
-                        "work_per_launch": f"2*s*m*n = {flops:.3e} flop"}
-    else:
-        flops = 4.0 * args.m * args.n          # one dot + one axpy per element of A
-        achieved = flops / (t_pass * 1e-3) / 1e12
-        if args.iter == "f32":
-            gbs = 4.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
-            peak = peaks.get("hbm_gbs", 6669.5)
-            roofline = {"kernel": "row_pass_kernel<float> (fused A(Nv) and A^T u on FP32 A)",
-                        "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                        "frac": gbs / peak, "traffic": None,
-                        "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
-                        "work_per_launch": "4*m*n bytes (FP32 copy of A read once)"}
-        elif args.iter == "x2":
-            gbs = 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
-            peak = peaks.get("hbm_gbs", 6669.5)
-            tpu = traffic_per_unit("row_pass_x2_kernel")
-            roofline = {"kernel": "row_pass_x2_kernel (fused A(Nv) and A^T u, double-float planes)",
-                        "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                        "frac": gbs / peak,
-                        "traffic": None if tpu is None else tpu * args.m * args.n,
-                        "peak_source": "hbm_gbs of measured (MEASURED_PEAKS.json)",
-                        "work_per_launch": "8*m*n bytes (hi and lo FP32 planes of A read once)"}
-        else:
-            roofline = {"kernel": "row_pass_kernel (fused A(Nv) and A^T u, FP64)", "bound": "alu",
-                      "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                      "frac": achieved / fp64_peak, "traffic": None,
-                      "peak_source": "FP64 FMA throughput measured in this run (lsrn_probe_fp64_fma)",
-                      "work_per_launch": "4*m*n flop (8*m*n bytes of A)",
-                      "hbm_gbs": 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9,
-                      "hbm_frac_of_measured": 8.0 * args.m * args.n / (t_pass * 1e-3) / 1e9
-                      / peaks.get("hbm_gbs", 6669.5)}
-    kernel_ms = {"sketch_gemm_total": t_gemm, "pass_each": t_pass, "pass_total": t_pass_tot,
-                 "passes": n_pass}
+    phases = phase_rooflines(infos, args, peaks, fp64_peak)
+    dominant = max(phases, key=lambda k: phases[k]["ms"])
+    roofline = dict(phases[dominant])
+    roofline["phase"] = dominant
+    roofline["traffic"] = traffic_for(dominant, args)
+    roofline["selection"] = "largest device time per solve among sketch, qr, svd, passes"
+
+    # FP64 plain: the same problem with the FP64 sketch and FP64 passes (one solve,
+    # outside the timed region) -- the comparison point of the metric
+    fp64_plain = None
+    if not args.no_fp64_plain:
+        o64 = L.default_options(seed=1234 + rank, sketch_mode=L.LSRN_SKETCH_F64,
+                                iter_mode=L.LSRN_ITER_F64)
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        inf64 = step(o64)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        err64 = rel_error(x.cpu().numpy(), xstar)
+        fp64_plain = {"value": job_throughput(world, 1, ms64), "unit": UNIT, "ms_per_solve": ms64,
+                      "steps": 1, "rel_err": err64, "within_1e-10": bool(err64 <= 1e-10),
+                      "phases_ms": {"sketch": inf64["t_sketch_ms"], "precond": inf64["t_precond_ms"],
+                                    "iter": inf64["t_iter_ms"], "refine": inf64["t_refine_ms"]},
+                      "config": "FP64 sketch (DFMA), FP64 passes, FP64 SVD and refinement"}
 
     # end to end through the C ABI with host buffers (pinned A, b in; x out)
     e2e = None
@@ -580,7 +653,9 @@ def main():
         r = oracle_sampled_solve_seconds(A_np, b.cpu().numpy(), info["iterations"],
                                          info["refine_iterations"] + 1)
         cpu = {"value": 1.0 / r["total_s"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": r["sample"], "stages_s": {k: r[k] for k in ("sketch_s", "svd_s", "iter_s")}}
+               "sample": r["sample"], "sample_s": r["sample_s"],
+               "stages_s": {k: r[k] for k in ("sketch_s", "svd_s", "iter_s")},
+               "measured_s": r["measured_s"], "factors": r["factors"]}
         del A_np
 
     if rank == 0:
@@ -589,8 +664,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"x2": "f32x2 passes, f32x3 residual, f64 SVD/recurrences",
-                      "f32": "f32 passes, f64 SVD/recurrences/residual",
+            "dtype": {"x2": "mixed: bf16 exact-slice sketch, f32x2 passes, f32x3 residual, "
+                            "f64 SVD/recurrences/refinement",
+                      "f32": "mixed: f32 passes, f64 SVD/recurrences/residual",
                       "f64": "f64"}[args.iter],
             "data": "synthetic (seeded generator, no dataset)",
             "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, cond 1e6, "
@@ -598,19 +674,26 @@ def main():
                                    f"refinement, sketch {args.sketch}, passes {args.iter}",
                        "l2": "inputs larger than L2 (A is 16 GB)",
                        "parallelism": "independent problem per GPU"},
+            "latency_ms": {"p50": float(np.percentile(per_step, 50)),
+                           "p99": float(np.percentile(per_step, 99)),
+                           "max": float(per_step.max())},
+            "fp64_plain": fp64_plain,
+            "mixed_over_fp64_plain": (value / fp64_plain["value"]) if fp64_plain else None,
             "accuracy": {"max_rel_err_vs_planted_xstar": max(errs), "target": 1e-10,
                          "ok": bool(max(errs) <= 1e-10)},
-            "phases_ms": {"sketch": t_sketch,
+            "phases_ms": {"sketch": float(np.mean([i["t_sketch_ms"] for i in infos])),
                           "precond": float(np.mean([i["t_precond_ms"] for i in infos])),
                           "precond_qr": float(np.mean([i["t_qr_ms"] for i in infos])),
+                          "precond_jacobi": float(np.mean([i["t_jacobi_ms"] for i in infos])),
                           "iter": float(np.mean([i["t_iter_ms"] for i in infos])),
                           "refine": float(np.mean([i["t_refine_ms"] for i in infos]))},
             "iterations": info["iterations"], "refine_iterations": info["refine_iterations"],
             "jacobi_sweeps": info["jacobi_sweeps"],
             "refine_steps": info["refine_steps"],
-            "rank": info["rank"], "s": s,
+            "rank": info["rank"], "s": info["s"],
             "roofline": roofline,
-            "kernel_ms": kernel_ms,
+            "roofline_phases": phases,
+            "fp64_peak_tflops": {"probed": fp64_peak, "nominal": FP64_NOMINAL_TFLOPS},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
@@ -620,6 +703,17 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload == "c1":
+        return run_small(args)
+    return run_dense(args)
 
 
 if __name__ == "__main__":

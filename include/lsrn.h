@@ -140,10 +140,14 @@ typedef struct {
   double anorm_est;               /* LSQR estimate of ||AN||_F */
   float t_sketch_ms, t_precond_ms, t_iter_ms, t_refine_ms;  /* device time per phase */
   float t_sketch_gemm_ms;         /* tensor-core GEMM kernels inside the sketch (0 otherwise) */
-  float t_pass_ms;                /* fused HBM passes over A in the main sweep (sum) */
-  int32_t n_pass;                 /* number of those passes */
+  float t_pass_ms;                /* fused passes over dense A in the solve, main sweep and
+                                     refinement corrections (sum of their device times) */
+  int32_t n_pass;                 /* those passes that streamed A: passes launched after the
+                                     sweep converged return at once and are not counted
+                                     (duration below a quarter of the longest pass) */
   float t_qr_ms;                  /* Householder QR of the sketch inside t_precond_ms */
   int32_t jacobi_sweeps;          /* one-sided Jacobi sweeps of the preconditioner */
+  float t_jacobi_ms;              /* the Jacobi sweeps inside t_precond_ms */
 } lsrn_info;
 
 typedef struct lsrn_plan_s* lsrn_plan_t;
@@ -267,6 +271,28 @@ lsrn_status lsrn_generate_sketch_block(uint64_t seed, uint32_t tag, int64_t i0, 
  * memory is allocated or freed. */
 lsrn_status lsrn_sketch_f64_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
                                     double gamma, uint64_t seed, double* out, void* stream);
+
+/* Test knobs (no counterpart in the paper): process-wide settings that let a
+ * test drive a failure path on purpose without faulting the GPU.  Every knob
+ * is 0 (off) by default and is read when a preconditioner starts.
+ *   LSRN_KNOB_JACOBI_WAIT_NS          > 0: time limit, in nanoseconds of the
+ *                                     GPU's global timer, of each dependency
+ *                                     wait of the dataflow Jacobi sweep
+ *                                     (min(m, n) > 1024); 0: one second.
+ *   LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND != 0: the dataflow sweep starts after the
+ *                                     first round's pairs, so every later pair
+ *                                     waits on rows that are never published
+ *                                     and the sweep's bounded wait runs out:
+ *                                     lsrn_precond returns LSRN_ERR_TIMEOUT.
+ * A preconditioner that fails leaves the plan needing a new sketch (the QR
+ * overwrites the sketch in place); lsrn_solve_* redoes it by itself.
+ * INVALID_ARG for an unknown knob or a negative value. */
+typedef enum {
+  LSRN_KNOB_JACOBI_WAIT_NS = 0,
+  LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 1,
+  LSRN_KNOB_COUNT = 2
+} lsrn_test_knob;
+lsrn_status lsrn_set_test_knob(int32_t knob, int64_t value);
 
 /* ---- serving: a request queue with admission by device-memory budget ----
  * lsrn_submit copies the request (A, b, options) and returns a ticket at once;

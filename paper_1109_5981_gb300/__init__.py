@@ -37,6 +37,7 @@ LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
 LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED = 0, 1
 LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2 = 0, 1, 2
+LSRN_KNOB_JACOBI_WAIT_NS, LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 0, 1
 
 
 class lsrn_matrix(ctypes.Structure):
@@ -66,7 +67,8 @@ class lsrn_info(ctypes.Structure):
                 ("t_precond_ms", ctypes.c_float), ("t_iter_ms", ctypes.c_float),
                 ("t_refine_ms", ctypes.c_float), ("t_sketch_gemm_ms", ctypes.c_float),
                 ("t_pass_ms", ctypes.c_float), ("n_pass", ctypes.c_int32),
-                ("t_qr_ms", ctypes.c_float), ("jacobi_sweeps", ctypes.c_int32)]
+                ("t_qr_ms", ctypes.c_float), ("jacobi_sweeps", ctypes.c_int32),
+                ("t_jacobi_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -89,6 +91,7 @@ _SIGS = {
     "lsrn_kernel_launches": ([], ctypes.c_uint64),
     "lsrn_probe_fp64_fma": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lsrn_default_options": ([ctypes.POINTER(lsrn_options)], ctypes.c_int),
+    "lsrn_set_test_knob": ([ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
     "lsrn_plan": ([ctypes.POINTER(lsrn_matrix), ctypes.POINTER(lsrn_options), ctypes.c_void_p,
                    ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "lsrn_sketch": ([ctypes.c_void_p], ctypes.c_int),
@@ -151,6 +154,11 @@ def probe_fp64_fma() -> float:
     v = ctypes.c_double()
     _check(load_library().lsrn_probe_fp64_fma(ctypes.byref(v)), "lsrn_probe_fp64_fma")
     return v.value
+
+
+def lsrn_set_test_knob(knob: int, value: int) -> None:
+    """Set a process-wide test knob (0 turns it off)."""
+    _check(load_library().lsrn_set_test_knob(knob, value), "lsrn_set_test_knob")
 
 
 def status_string(status: int) -> str:

@@ -9,6 +9,8 @@
 // workspace.  The array (kNoAllocScratchDoubles doubles, 32 MiB) is part of the
 // library's device image: every GPU that loads the library holds it until the
 // process exits.
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "lsrn_device.cuh"
@@ -53,11 +55,12 @@ extern "C" lsrn_status lsrn_sketch_f64_noalloc(const double* A, int64_t m, int64
                                                double gamma, uint64_t seed, double* out,
                                                void* stream) {
   if (A == nullptr || out == nullptr || m < 1 || n < 1 || m < n || lda < n) return LSRN_ERR_INVALID_ARG;
-  if (!(gamma > 1.0)) return LSRN_ERR_INVALID_ARG;
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return LSRN_ERR_INVALID_ARG;
   if (!lsrn::is_device_pointer(A) || !lsrn::is_device_pointer(out)) return LSRN_ERR_INVALID_ARG;
-  int64_t s = (int64_t)std::ceil(gamma * (double)n);
-  if (s <= n) s = n + 1;
-  if ((size_t)(s * n) > kNoAllocScratchDoubles) return LSRN_ERR_INVALID_ARG;   // over the fixed scratch
+  // size check in double arithmetic first, so a huge gamma cannot overflow s or s * n
+  const double sd = std::max(std::ceil(gamma * (double)n), (double)n + 1.0);
+  if (!(sd * (double)n <= (double)kNoAllocScratchDoubles)) return LSRN_ERR_INVALID_ARG;
+  const int64_t s = (int64_t)sd;
   double* scratch = nullptr;
   lsrn_status st = noalloc_scratch(&scratch);
   if (st != LSRN_OK) return st;

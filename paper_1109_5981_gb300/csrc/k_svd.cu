@@ -527,10 +527,16 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __rest
 // Each row sees the same rotations in the same order as with one launch per
 // round, so the result is the same bit for bit.
 // ws[0]: next item, ws[1]: error flag (a wait gave up), ws[2 + row]: ver[row].
-// A wait polls at most kJacSpinLimit times (well under a second); then the
-// CTA raises the flag, every CTA stops at its next item or poll, and the
-// preconditioner returns LSRN_ERR_TIMEOUT.
-constexpr int kJacSpinLimit = 1 << 20;
+// A wait is bounded by elapsed time on the GPU's global timer (wait_ns, one
+// second by default); then the CTA raises the flag, every CTA stops at its
+// next item or poll, and the preconditioner returns LSRN_ERR_TIMEOUT.
+constexpr uint64_t kJacWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
@@ -546,7 +552,7 @@ template <int EPT>
 __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
     jacobi_flow_kernel(double* __restrict__ W, int64_t Q, int P, double tol,
                        double* __restrict__ nrm2, int* __restrict__ rot_count,
-                       int* __restrict__ ws) {
+                       int* __restrict__ ws, uint64_t wait_ns) {
   __shared__ double sh[kJacThreads / 32];
   __shared__ double rot[3];
   __shared__ int s_item, s_ok;
@@ -565,11 +571,13 @@ __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
         const int a = k == 0 ? P - 1 : (t + k) % (P - 1);
         const int b = k == 0 ? t : (t - k + P - 1) % (P - 1);
         ok = 1;
+        const uint64_t t0 = globaltimer_ns();
         for (int it = 0;; ++it) {
           const bool ra = a >= Q || ld_acquire_gpu(ver + a) >= t;
           const bool rb = b >= Q || ld_acquire_gpu(ver + b) >= t;
           if (ra && rb) break;
-          if (it >= kJacSpinLimit || ((it & 63) == 63 && ld_acquire_gpu(err) != 0)) {
+          if ((it & 15) == 15 &&
+              (globaltimer_ns() - t0 > wait_ns || ld_acquire_gpu(err) != 0)) {
             atomicExch(err, 1);
             ok = 0;
             break;
@@ -667,6 +675,8 @@ __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
     }
   }
 }
+
+__global__ void set_int_kernel(int* __restrict__ p, int v) { *p = v; }
 
 __global__ void row_sqnorms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm2) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -827,6 +837,12 @@ lsrn_status run_precond(Plan* p) {
   const bool flow = ept >= 16;
   int* jws = nullptr;
   int flow_grid = 0;
+  // Test knobs (lsrn_set_test_knob): a shorter wait limit, and items of the
+  // first round skipped so that every later item waits on rows that are never
+  // published -- the only way to make the bounded wait run out on purpose.
+  const int64_t knob_wait = test_knob(LSRN_KNOB_JACOBI_WAIT_NS);
+  const uint64_t wait_ns = knob_wait > 0 ? (uint64_t)knob_wait : kJacWaitNs;
+  const int skip_items = test_knob(LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND) != 0 ? P / 2 : 0;
   if (flow) {
     LSRN_CUDA_TRY(lsrn_malloc_async((void**)&jws, (Q + 2) * sizeof(int), st));
     int per_sm = 0;
@@ -847,10 +863,13 @@ lsrn_status run_precond(Plan* p) {
       launch(row_sqnorms_kernel, (unsigned)((Q * 32 + 255) / 256), 256, 0, st, p->Wj, Q, nrm2);
     if (flow) {
       cudaMemsetAsync(jws, 0, (Q + 2) * sizeof(int), st);
+      if (skip_items > 0) launch(set_int_kernel, 1, 1, 0, st, jws, skip_items);
       if (ept == 16)
-        launch(jacobi_flow_kernel<16>, flow_grid, kJacThreads, 0, st, p->Wj, Q, P, tol, nrm2, rot, jws);
+        launch(jacobi_flow_kernel<16>, flow_grid, kJacThreads, 0, st, p->Wj, Q, P, tol, nrm2, rot, jws,
+               wait_ns);
       else
-        launch(jacobi_flow_kernel<32>, flow_grid, kJacThreads, 0, st, p->Wj, Q, P, tol, nrm2, rot, jws);
+        launch(jacobi_flow_kernel<32>, flow_grid, kJacThreads, 0, st, p->Wj, Q, P, tol, nrm2, rot, jws,
+               wait_ns);
       return;
     }
     for (int t = 0; t < P - 1; ++t) {
@@ -893,6 +912,7 @@ lsrn_status run_precond(Plan* p) {
     } while (host_rot > 0 && sweeps < max_sweeps);
     if (sweep_graph != nullptr) cudaGraphExecDestroy(sweep_graph);
   }
+  cudaEventRecord(p->ev[9], st);
   if (jws != nullptr) cudaFreeAsync(jws, st);
   p->sweeps = sweeps;
   if (host_rot > 0) return LSRN_ERR_NOT_CONVERGED;

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "lsrn_device.cuh"
 #include "lsrn_internal.h"
@@ -20,6 +21,12 @@ lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host);
 
 static thread_local char g_last_error[512];
 std::atomic<unsigned long long> g_kernel_launches{0};
+static std::atomic<long long> g_test_knobs[LSRN_KNOB_COUNT];
+
+int64_t test_knob(int knob) {
+  if (knob < 0 || knob >= LSRN_KNOB_COUNT) return 0;
+  return (int64_t)g_test_knobs[knob].load(std::memory_order_relaxed);
+}
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s -> %s", file, line, what,
@@ -305,6 +312,12 @@ const char* lsrn_last_error_message(void) { return g_last_error; }
 
 uint64_t lsrn_kernel_launches(void) { return (uint64_t)g_kernel_launches.load(); }
 
+lsrn_status lsrn_set_test_knob(int32_t knob, int64_t value) {
+  if (knob < 0 || knob >= LSRN_KNOB_COUNT || value < 0) return LSRN_ERR_INVALID_ARG;
+  g_test_knobs[knob].store((long long)value, std::memory_order_relaxed);
+  return LSRN_OK;
+}
+
 lsrn_status lsrn_default_options(lsrn_options* opt) {
   if (opt == nullptr) return LSRN_ERR_INVALID_ARG;
   memset(opt, 0, sizeof(*opt));
@@ -418,10 +431,7 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
     LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, p->xscale, p->s,
                                p->opt.seed, tag, p->Xs, p->q, p->stream));
   } else if (p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED) {
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
-    int64_t seg = sketch_tc_segment_rows(p->xrows, p->q, p->s, budget);
+    int64_t seg = sketch_tc_plan_segment_rows(p->xrows, p->q, p->s);
     if (const char* env = getenv("LSRN_TC_SEGMENT_ROWS")) {   // testing: force small segments
       const long long v = atoll(env);
       if (v >= 64) seg = std::min<int64_t>(seg, (int64_t)(v / 64 * 64));
@@ -464,7 +474,13 @@ lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
     if (tcerr) return LSRN_ERR_TIMEOUT;
   }
   cudaEventRecord(p->ev[2], p->stream);
-  LSRN_TRY(run_precond(p));
+  {
+    const lsrn_status st = run_precond(p);
+    if (st != LSRN_OK) {
+      p->state = 0;   // the QR has overwritten the sketch: a retry must sketch again
+      return st;
+    }
+  }
   cudaEventRecord(p->ev[3], p->stream);
   LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[3]));
   cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
@@ -472,6 +488,10 @@ lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
   if (cudaEventElapsedTime(&p->t_qr_ms, p->ev[2], p->ev[8]) != cudaSuccess) {
     cudaGetLastError();
     p->t_qr_ms = 0.f;
+  }
+  if (cudaEventElapsedTime(&p->t_jacobi_ms, p->ev[8], p->ev[9]) != cudaSuccess) {
+    cudaGetLastError();
+    p->t_jacobi_ms = 0.f;
   }
   p->t_sketch_gemm_ms = 0.f;
   for (auto& pr : p->gemm_events) {
@@ -506,6 +526,7 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   inf.t_precond_ms = p->t_precond_ms;
   inf.t_qr_ms = p->t_qr_ms;
   inf.jacobi_sweeps = p->sweeps;
+  inf.t_jacobi_ms = p->t_jacobi_ms;
   inf.t_sketch_gemm_ms = p->t_sketch_gemm_ms;
   lsrn_status result = LSRN_OK;
   const bool xdev = is_device_pointer(x);
@@ -529,25 +550,30 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
       inf.arnorm_est = sc[SC_ARNORM];
       inf.anorm_est = sc[SC_ANORM];
     }
-    p->time_passes = false;
     cudaEventRecord(p->ev[5], p->stream);
     if (result == LSRN_OK) {
       LSRN_TRY(run_refine(p, p->opt.refine_max, &inf.refine_iterations, &inf.refine_steps));
     }
+    p->time_passes = false;
     cudaEventRecord(p->ev[6], p->stream);
     LSRN_TRY(finish_x(p, xout));
     LSRN_CUDA_TRY(cudaEventSynchronize(p->ev[6]));
     cudaEventElapsedTime(&inf.t_iter_ms, p->ev[4], p->ev[5]);
+    std::vector<float> pass_ms;
     for (auto& pr : p->pass_events) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
-        inf.t_pass_ms += ms;
-        inf.n_pass += 1;
-      }
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) pass_ms.push_back(ms);
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
     }
     p->pass_events.clear();
+    // passes launched after the sweep converged return at once: count only
+    // those that streamed A (at least a quarter of the longest pass)
+    const float longest = pass_ms.empty() ? 0.f : *std::max_element(pass_ms.begin(), pass_ms.end());
+    for (float ms : pass_ms) {
+      inf.t_pass_ms += ms;
+      if (ms >= 0.25f * longest) inf.n_pass += 1;
+    }
     cudaEventElapsedTime(&inf.t_refine_ms, p->ev[5], p->ev[6]);
   }
   if (!xdev)

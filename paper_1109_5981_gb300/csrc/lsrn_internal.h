@@ -27,6 +27,8 @@ namespace lsrn {
   } while (0)
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+// Current value of a test knob (lsrn_set_test_knob); 0 when unset.
+int64_t test_knob(int knob);
 int num_sms();
 // Stream-ordered allocation from the library's memory pool of the current device.
 cudaError_t lsrn_malloc_async(void** ptr, size_t bytes, cudaStream_t st);
@@ -151,11 +153,11 @@ struct Plan {
   double* pvec2 = nullptr;          // second partial buffer (double-double low parts)
   double* pscal = nullptr;          // (nblk + 1) scalar partials
   int nblk = 0;                     // CTAs of the fused pass
-  cudaEvent_t ev[9] = {nullptr};   // [8]: end of the QR inside the preconditioner
+  cudaEvent_t ev[10] = {nullptr};  // [8]: end of the QR, [9]: end of the Jacobi sweeps
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gemm_events;   // tensor-core GEMM launches
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;   // fused passes of the main sweep
   bool time_passes = false;
-  float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0, t_qr_ms = 0;
+  float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0, t_qr_ms = 0, t_jacobi_ms = 0;
 };
 
 // ---- kernels (launchers) -------------------------------------------------
@@ -175,6 +177,13 @@ lsrn_status launch_sketch_f64_splitk_into(const double* X, int64_t L, int64_t Q,
 // sketch_tc_scratch_bytes(seg_rows, Q, S) of scratch; *err is set on a timed-out wait.
 size_t sketch_tc_scratch_bytes(int64_t Ls, int64_t Q, int64_t S);
 int64_t sketch_tc_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_bytes);
+// Segment length the plan uses: a function of (L, Q, S) and a fixed scratch
+// budget only, never of the memory free at the time, so the sketch (whose
+// per-column exponents and final roundings are per segment) is reproducible.
+constexpr size_t kTcScratchBudget = (size_t)8 << 30;
+inline int64_t sketch_tc_plan_segment_rows(int64_t L, int64_t Q, int64_t S) {
+  return sketch_tc_segment_rows(L, Q, S, kTcScratchBudget);
+}
 lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,

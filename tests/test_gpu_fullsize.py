@@ -61,6 +61,25 @@ def test_dense_tall_full_size(c2, iter_mode):
     assert np.linalg.norm(O.dd_atr(A_host, r)) / np.linalg.norm(r) <= 1e-12
 
 
+def test_dense_tall_full_size_cs(c2):
+    """Algorithm 3 (Chebyshev semi-iterative) at full size in the benchmark's
+    double-float mode: x against the planted x* and the normal equations."""
+    P, A_host, b = c2
+    opt = L.default_options(seed=1234, sketch_mode=L.LSRN_SKETCH_TC_SLICED,
+                            iter_mode=L.LSRN_ITER_F32X2)
+    plan = L.lsrn_plan(P.A, opt)
+    try:
+        x, info = L.lsrn_solve_cs(plan, P.b)
+    finally:
+        plan.close()
+    assert info["rank"] == 1800 and info["sigma_L"] > 0.0
+    xs = O.minlen_from_factors(P.apply_Ut, P.sigma, P.apply_V, b)
+    xh = x.cpu().numpy()
+    assert O.rel_err(xh, xs) <= 1e-10
+    r = O.dd_residual(A_host, b, xh)
+    assert np.linalg.norm(O.dd_atr(A_host, r)) / np.linalg.norm(r) <= 1e-12
+
+
 @pytest.fixture(scope="module")
 def c3():
     A, b = W.c3_problem(seed=0)
@@ -85,3 +104,22 @@ def test_sparse_fat_ridge_full_size(c3):
     ref = O.ridge_closed_form(As, b, lam)
     assert O.rel_err(x_lsqr.cpu().numpy(), ref) <= 1e-10
     assert O.rel_err(x_cs.cpu().numpy(), ref) <= 1e-10
+
+
+def test_sparse_fat_ridge_full_size_f32_values():
+    """The same 10^4 x 10^6 shape with FP32 values (the oracle uses the rounded
+    values): LSQR against the ridge closed form."""
+    import scipy.sparse as sp
+    A, b = W.c3_problem(seed=1, dtype=np.float32)
+    lam = 1e-3
+    csr = (A.m, A.n, torch.from_numpy(A.row_ptr).to("cuda"), torch.from_numpy(A.col_idx).to("cuda"),
+           torch.from_numpy(A.values).to("cuda"))
+    plan = L.lsrn_plan(None, L.default_options(seed=4, lambda_=lam), csr=csr)
+    try:
+        x, info = L.lsrn_solve_lsqr(plan, torch.from_numpy(b).to("cuda"))
+    finally:
+        plan.close()
+    assert info["tall"] == 0 and info["rank"] == A.m
+    As = sp.csr_matrix((A.values.astype(np.float64), A.col_idx, A.row_ptr), shape=(A.m, A.n))
+    ref = O.ridge_closed_form(As, b, lam)
+    assert O.rel_err(x.cpu().numpy(), ref) <= 1e-10

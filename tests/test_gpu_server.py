@@ -176,3 +176,31 @@ def test_destroy_with_queued_requests_returns():
     t0 = time.monotonic()
     L.lsrn_server_destroy(srv)
     assert time.monotonic() - t0 < 60
+
+
+def test_tc_sketch_result_does_not_depend_on_free_memory():
+    """The tensor-core sketch cuts X into row segments (per-column exponents and
+    the final FP64 rounding are per segment).  The segment length depends on
+    the problem's shape only, so a request gives the same x bit for bit when it
+    runs alone and when a neighbour holds nearly all free device memory."""
+    P = W.dense_householder(200_000, 512, rank=500, cond=1e4, noise=1e-3, seed=61)
+    A = torch.from_numpy(P.A).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    opt = L.default_options(seed=5, sketch_mode=L.LSRN_SKETCH_TC_SLICED)
+    srv = L.lsrn_server_create(64 * GiB, max_slots=1)
+    try:
+        x_alone = np.zeros(512)
+        st, _ = _wait(srv, L.lsrn_submit(srv, A, b, opt, 0), x_alone)
+        assert st == L.LSRN_OK
+        free, _ = torch.cuda.mem_get_info()
+        hog = torch.empty(max(0, free - 8 * GiB), dtype=torch.uint8, device="cuda")
+        try:
+            x_crowded = np.zeros(512)
+            st, _ = _wait(srv, L.lsrn_submit(srv, A, b, opt, 0), x_crowded)
+            assert st == L.LSRN_OK
+        finally:
+            del hog
+            torch.cuda.empty_cache()
+    finally:
+        L.lsrn_server_destroy(srv)
+    assert np.array_equal(x_alone, x_crowded)
