@@ -65,6 +65,9 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true",
                     help="skip the FP64-plain comparison solve after the timed region")
+    ap.add_argument("--parallel", default="shard", choices=["shard", "replica"],
+                    help="N > 1: shard = one problem split by rows over the ranks (section 4.4, "
+                         "strong scaling); replica = an independent problem per rank (weak)")
     ap.add_argument("--workload", default="dense", choices=["dense", "serving", "c1"],
                     help="dense: the 1e6 x 2000 solve; serving: a Poisson stream of mixed-size "
                          "requests through lsrn_submit/lsrn_poll; c1: latency of the 2000 x 100 "
@@ -456,14 +459,14 @@ def run_small(args):
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor) nominal rate
 
 
-def phase_rooflines(info_list, args, peaks: dict, fp64_peak: float) -> dict:
+def phase_rooflines(info_list, args, peaks: dict, fp64_peak: float, m_local: int = 0) -> dict:
     """Roofline of every large phase of a solve, from the library's per-phase
     CUDA-event times averaged over the timed solves.  Work is the method's
     algorithmic work (section 4.3 and the unit counts of the path): the sketch
     2 s m n flop, the QR 2 s n^2 - 2 n^3 / 3 flop, the SVD of the n x n
     triangle 11 n^3 flop, each fused pass 8 m n bytes (A streamed once as its
     two FP32 planes, or once in FP64)."""
-    m, n = args.m, args.n
+    m, n = (m_local or args.m), args.n        # a shard streams its own rows
     s = info_list[-1]["s"]
     mean = lambda k: float(np.mean([i[k] for i in info_list]))
     bf16 = peaks.get("bf16_tflops_sustained", 1707.9)
@@ -517,15 +520,15 @@ def phase_rooflines(info_list, args, peaks: dict, fp64_peak: float) -> dict:
     return out
 
 
-def traffic_for(phase: str, args):
+def traffic_for(phase: str, args, m_local: int):
     """DRAM bytes per launch of the phase's kernel from profiles/roofline_traffic.md
     (null once the kernel changed since the capture)."""
     if phase == "passes" and args.iter == "x2":
         tpu = traffic_per_unit("row_pass_x2_kernel")
-        return None if tpu is None else tpu * args.m * args.n
+        return None if tpu is None else tpu * m_local * args.n
     if phase == "sketch" and args.sketch == "tc":
         tpu = traffic_per_unit("sketch_tc_kernel")
-        return None if tpu is None else tpu * args.m
+        return None if tpu is None else tpu * m_local
     if phase == "svd":
         tpu = traffic_per_unit("jacobi_flow_kernel")
         return None if tpu is None else tpu
@@ -548,21 +551,41 @@ def run_dense(args):
         dist = dist_
     L.load_library()
     dev = f"cuda:{local}"
+    sharded = world > 1 and args.parallel == "shard"
 
-    P = W.c2_problem(seed=rank, device=dev, m=args.m, n=args.n, rank=args.rank)
+    if sharded:
+        # one problem, rows split over the ranks; every rank ends with the whole x
+        off, cnt = L.shard_rows(args.m, world, rank)
+        P = W.c2_problem(seed=0, device=dev, m=args.m, n=args.n, rank=args.rank,
+                         rows=(off, off + cnt))
+        gather = L.torch_allgather()
+        sizes = [L.shard_rows(args.m, world, r)[1] for r in range(world)]
+        bpad = torch.zeros(max(sizes), dtype=torch.float64, device=dev)
+        bpad[:cnt] = P.b
+        ball = [torch.empty_like(bpad) for _ in range(world)]
+        dist.all_gather(ball, bpad)
+        b_full = torch.cat([t[:c] for t, c in zip(ball, sizes)]).cpu().numpy()
+    else:
+        P = W.c2_problem(seed=rank, device=dev, m=args.m, n=args.n, rank=args.rank)
+        b_full = P.b.cpu().numpy()
     A, b = P.A, P.b
     x = torch.empty(args.n, dtype=torch.float64, device=dev)
     # x* = V Sigma^-1 U^T b from the generator's planted factors
-    xstar = P.apply_V(P.apply_Ut(b.cpu().numpy()) / P.sigma)
-    opts = L.default_options(seed=1234 + rank,
+    xstar = P.apply_V(P.apply_Ut(b_full) / P.sigma)
+    opts = L.default_options(seed=1234 + (0 if sharded else rank),
                              sketch_mode=L.LSRN_SKETCH_TC_SLICED if args.sketch == "tc"
                              else L.LSRN_SKETCH_F64,
                              iter_mode={"f32": L.LSRN_ITER_F32, "x2": L.LSRN_ITER_F32X2}.get(
                                  args.iter, L.LSRN_ITER_F64))
     solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
 
+    def make_plan(Amat, o):
+        if sharded:
+            return L.lsrn_plan_sharded(Amat, o, rank, world, off, args.m, gather)
+        return L.lsrn_plan(Amat, o)
+
     def step(o=opts):
-        plan = L.lsrn_plan(A, o)
+        plan = make_plan(A, o)
         try:
             _, info = solve_fn(plan, b, x)
         finally:
@@ -593,15 +616,16 @@ def run_dense(args):
     clk = clocks.stop()
     errs = [rel_error(x.cpu().numpy(), xstar)]   # every step solves the same problem
     elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
-    value = job_throughput(world, args.steps, elapsed_ms)
+    # sharded: all ranks together solve one problem per step
+    value = job_throughput(1 if sharded else world, args.steps, elapsed_ms)
     info = infos[-1]
     fp64_peak = L.probe_fp64_fma()
     peaks = _measured_peaks()
-    phases = phase_rooflines(infos, args, peaks, fp64_peak)
+    phases = phase_rooflines(infos, args, peaks, fp64_peak, int(A.shape[0]))
     dominant = max(phases, key=lambda k: phases[k]["ms"])
     roofline = dict(phases[dominant])
     roofline["phase"] = dominant
-    roofline["traffic"] = traffic_for(dominant, args)
+    roofline["traffic"] = traffic_for(dominant, args, int(A.shape[0]))
     roofline["selection"] = "largest device time per solve among sketch, qr, svd, passes"
 
     # FP64 plain: the same problem with the FP64 sketch and FP64 passes (one solve,
@@ -619,7 +643,8 @@ def run_dense(args):
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         err64 = rel_error(x.cpu().numpy(), xstar)
-        fp64_plain = {"value": job_throughput(world, 1, ms64), "unit": UNIT, "ms_per_solve": ms64,
+        fp64_plain = {"value": job_throughput(1 if sharded else world, 1, ms64), "unit": UNIT,
+                      "ms_per_solve": ms64,
                       "steps": 1, "rel_err": err64, "within_1e-10": bool(err64 <= 1e-10),
                       "phases_ms": {"sketch": inf64["t_sketch_ms"], "precond": inf64["t_precond_ms"],
                                     "iter": inf64["t_iter_ms"], "refine": inf64["t_refine_ms"]},
@@ -628,27 +653,28 @@ def run_dense(args):
     # end to end through the C ABI with host buffers (pinned A, b in; x out)
     e2e = None
     if not args.no_e2e:
-        A_h = torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True)
+        rows_here = A.shape[0]
+        A_h = torch.empty((rows_here, args.n), dtype=torch.float64, pin_memory=True)
         A_h.copy_(A)
         b_h = b.cpu().numpy().copy()
         x_h = np.empty(args.n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            plan = L.lsrn_plan(A_h, opts)
+            plan = make_plan(A_h, opts)
             solve_fn(plan, b_h, x_h)
             plan.close()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e_s = max_over_ranks(e2e_s * 1e3, dist, dev) / 1e3
         errs.append(rel_error(x_h, xstar))
-        e2e = {"value": job_throughput(world, 1, e2e_s * 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(args.m * args.n * 8 + args.m * 8),
+        e2e = {"value": job_throughput(1 if sharded else world, 1, e2e_s * 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(rows_here * args.n * 8 + rows_here * 8),
                "d2h_bytes_per_step": int(args.n * 8)}
         del A_h
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         A_np = A.cpu().numpy()
         r = oracle_sampled_solve_seconds(A_np, b.cpu().numpy(), info["iterations"],
                                          info["refine_iterations"] + 1)
@@ -663,7 +689,7 @@ def run_dense(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None,
             "dtype": {"x2": "mixed: bf16 exact-slice sketch, f32x2 passes, f32x3 residual, "
                             "f64 SVD/recurrences/refinement",
                       "f32": "mixed: f32 passes, f64 SVD/recurrences/residual",
@@ -673,7 +699,9 @@ def run_dense(args):
                                    f"noise 1e-4, gamma 2, {args.solver.upper()} tol 1e-14 + "
                                    f"refinement, sketch {args.sketch}, passes {args.iter}",
                        "l2": "inputs larger than L2 (A is 16 GB)",
-                       "parallelism": "independent problem per GPU"},
+                       "parallelism": (f"one problem row-sharded over {world} GPUs (allgather of "
+                                       "n + 1 values per pass)" if sharded
+                                       else "independent problem per GPU")},
             "latency_ms": {"p50": float(np.percentile(per_step, 50)),
                            "p99": float(np.percentile(per_step, 99)),
                            "max": float(per_step.max())},

@@ -53,7 +53,8 @@ typedef enum {
   LSRN_ERR_TIMEOUT = -6,        /* a bounded device wait gave up */
   LSRN_ERR_QUEUE_FULL = -7,     /* server: no slot or memory budget for the request */
   LSRN_ERR_STATE = -8,          /* calls out of order (e.g. precond before sketch) */
-  LSRN_ERR_UNSUPPORTED = -9     /* valid request this build does not implement */
+  LSRN_ERR_UNSUPPORTED = -9,    /* valid request this build does not implement */
+  LSRN_ERR_COMM = -10           /* the allgather callback of a sharded plan reported failure */
 } lsrn_status;
 
 typedef enum {
@@ -225,6 +226,48 @@ lsrn_status lsrn_solve_lsqr(lsrn_plan_t p, const double* b, double* x, lsrn_info
  * (the bounds did not hold); x then holds the last iterate.  INVALID_ARG if
  * (1 - alpha) sqrt(s) <= sqrt(r) (no valid upper bound). */
 lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* info);
+
+/* ---- row-sharded solve (section 4.4: A partitioned by rows over processes) ----
+ * One plan per shard (a GPU, a process or a host thread), each holding a block
+ * of consecutive rows of the tall A (m_total >= n).  The shards exchange data
+ * only through the caller's allgather callback:
+ *   - the sketch: each shard computes G_p A_p with G's columns drawn at the
+ *     block's global row indices (row_offset + i), the s x n partial sketches
+ *     are gathered once and summed in rank order, so every shard holds the same
+ *     A~ = G A and computes the same N (redundantly, no broadcast);
+ *   - each fused pass over A: the partial A_p^T u_p (n values) and ||u_p||^2
+ *     are gathered and summed in rank order (one exchange of n + 1 values per
+ *     iteration, LSQR's scalar packed with the vector; CS uses the same);
+ *   - ||b||^2 once per solve, and each refinement step's residual product
+ *     A^T r (gathered as double-double and summed in double-double).
+ * Every shard thus runs identical scalar recurrences and reaches the same x.
+ *   allgather(ctx, send, recv, count): send holds `count` doubles in device
+ *     memory; the callback must write world * count doubles to recv (device
+ *     memory, rank-major: shard p's values at recv[p * count]) before it
+ *     returns, and return 0 (nonzero: the solve stops with LSRN_ERR_COMM).  The
+ *     library synchronises its stream before the call and reads recv after it.
+ *     The callback runs on the thread that called into the library.
+ * Ridge (lambda > 0): the rows lambda I belong to shard 0. */
+typedef int32_t (*lsrn_allgather_fn)(void* ctx, const double* send, double* recv, int64_t count);
+typedef struct {
+  int32_t rank, world;        /* this shard, number of shards (>= 1) */
+  int64_t row_offset;         /* global index of this shard's first row */
+  int64_t m_total;            /* rows of the whole matrix (m_total >= n) */
+  lsrn_allgather_fn allgather;
+  void* ctx;
+} lsrn_shard;
+
+/* Plan for one shard: A_local is the shard's block (rows row_offset ..
+ * row_offset + A_local.m - 1 of A, all n columns; dense or CSR, host or device
+ * data as for lsrn_plan).  Every shard must pass the same options (seed
+ * included) and call lsrn_sketch / lsrn_precond / lsrn_solve_* in the same
+ * order: each exchange is a collective over the shards.  b given to a solve is
+ * the shard's block of b (A_local.m values); x (n values) is the whole solution
+ * on every shard.  UNSUPPORTED for m_total < n (Algorithm 2 partitions columns,
+ * which this entry point does not build); INVALID_ARG for inconsistent shard
+ * fields or a missing callback with world > 1. */
+lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* opt,
+                              const lsrn_shard* shard, void* stream, lsrn_plan_t* out);
 
 /* Release everything the plan owns.  NULL is accepted.  Synchronises. */
 lsrn_status lsrn_plan_destroy(lsrn_plan_t p);

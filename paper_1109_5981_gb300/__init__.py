@@ -32,6 +32,7 @@ LSRN_ERR_TIMEOUT = -6
 LSRN_ERR_QUEUE_FULL = -7
 LSRN_ERR_STATE = -8
 LSRN_ERR_UNSUPPORTED = -9
+LSRN_ERR_COMM = -10
 
 LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
@@ -74,6 +75,16 @@ class lsrn_info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+lsrn_allgather_fn = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int64)
+
+
+class lsrn_shard(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("world", ctypes.c_int32),
+                ("row_offset", ctypes.c_int64), ("m_total", ctypes.c_int64),
+                ("allgather", lsrn_allgather_fn), ("ctx", ctypes.c_void_p)]
+
+
 class LsrnError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -94,6 +105,9 @@ _SIGS = {
     "lsrn_set_test_knob": ([ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
     "lsrn_plan": ([ctypes.POINTER(lsrn_matrix), ctypes.POINTER(lsrn_options), ctypes.c_void_p,
                    ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "lsrn_plan_sharded": ([ctypes.POINTER(lsrn_matrix), ctypes.POINTER(lsrn_options),
+                           ctypes.POINTER(lsrn_shard), ctypes.c_void_p,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "lsrn_sketch": ([ctypes.c_void_p], ctypes.c_int),
     "lsrn_precond": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "lsrn_solve_lsqr": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -281,6 +295,84 @@ def lsrn_plan(A, opt: Optional[lsrn_options] = None, stream: int = 0, layout: st
     _check(lib.lsrn_plan(ctypes.byref(mat), ctypes.byref(o), ctypes.c_void_p(stream),
                          ctypes.byref(h)), "lsrn_plan")
     return Plan(h.value, keep, mat.m, mat.n)
+
+
+def shard_rows(m_total: int, world: int, rank: int) -> tuple:
+    """Rows of shard `rank` in a partition of m_total rows into `world` blocks
+    of consecutive rows whose sizes differ by at most one: (offset, count)."""
+    if not (world >= 1 and 0 <= rank < world and m_total >= world):
+        raise ValueError("need world >= 1, 0 <= rank < world and m_total >= world")
+    base, extra = divmod(m_total, world)
+    offset = rank * base + min(rank, extra)
+    return offset, base + (1 if rank < extra else 0)
+
+
+class _DeviceArray:
+    """A device buffer the library owns, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f8",
+                                         "data": (ptr, False), "version": 3}
+
+
+def device_view(ptr: int, count: int):
+    """torch view (float64, CUDA) of `count` doubles at a library device pointer."""
+    import torch
+    return torch.as_tensor(_DeviceArray(ptr, count), device="cuda")
+
+
+def torch_allgather(group=None):
+    """allgather callback over a torch.distributed process group: NCCL gathers
+    the device buffers in place; other backends (gloo) go through host copies."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(send_ptr: int, recv_ptr: int, count: int) -> None:
+        send = device_view(send_ptr, count)
+        recv = device_view(recv_ptr, count * dist.get_world_size(group))
+        if dist.get_backend(group) == "nccl":
+            dist.all_gather_into_tensor(recv, send, group=group)
+            torch.cuda.current_stream().synchronize()
+        else:
+            out = torch.empty(recv.shape, dtype=torch.float64)
+            dist.all_gather_into_tensor(out, send.cpu(), group=group)
+            recv.copy_(out)
+            torch.cuda.synchronize()
+    return fn
+
+
+def lsrn_plan_sharded(A_local, opt: Optional[lsrn_options], rank: int, world: int,
+                      row_offset: int, m_total: int, allgather, stream: int = 0,
+                      csr: Optional[tuple] = None) -> Plan:
+    """lsrn_plan_sharded(): one shard (rows row_offset .. of the tall A).
+    allgather(send_ptr, recv_ptr, count) fills recv (world * count doubles,
+    rank-major) from every shard's send; exceptions become LSRN_ERR_COMM."""
+    lib = load_library()
+    if csr is not None:
+        m, n, rp, ci, vals = csr
+        mat = csr_matrix(m, n, rp, ci, vals)
+        keep = [rp, ci, vals]
+    else:
+        mat = dense_matrix(A_local, "row")
+        keep = [A_local]
+
+    def _cb(ctx, send, recv, count):
+        try:
+            allgather(int(send), int(recv), int(count))
+            return 0
+        except Exception:        # reported to the library as a failed exchange
+            import traceback
+            traceback.print_exc()
+            return 1
+    cb = lsrn_allgather_fn(_cb)
+    sh = lsrn_shard(rank=rank, world=world, row_offset=row_offset, m_total=m_total,
+                    allgather=cb, ctx=None)
+    keep += [cb, sh]
+    h = ctypes.c_void_p()
+    o = opt if opt is not None else default_options()
+    _check(lib.lsrn_plan_sharded(ctypes.byref(mat), ctypes.byref(o), ctypes.byref(sh),
+                                 ctypes.c_void_p(stream), ctypes.byref(h)), "lsrn_plan_sharded")
+    return Plan(h.value, tuple(keep), mat.m, mat.n)
 
 
 def lsrn_sketch(plan: Plan) -> None:

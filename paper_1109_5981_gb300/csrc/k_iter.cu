@@ -475,6 +475,55 @@ __device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, f
   h = s;
   l += er + e;
 }
+// Packed pairs: two FP32 lanes in one 64-bit register, operated on by the
+// f32x2 instructions (one issue slot for both lanes, each lane rounded as the
+// scalar IEEE operation).  The pass handles columns in (even, odd) pairs, so
+// the error-free transformations above run on both columns of a pair at once.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float x, float y) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(f32x2 r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// (h, l) += (ah + al) * (bh + bl) lane by lane, as df_fma; bhn = -bh (so the
+// negated product comes from one multiply and the TwoSum uses it directly).
+__device__ __forceinline__ void df_fma2(f32x2 ah, f32x2 al, f32x2 bh, f32x2 bhn, f32x2 bl,
+                                        f32x2& h, f32x2& l) {
+  const f32x2 np = mul2(ah, bhn);                       // -p, p = ah bh rounded
+  f32x2 e = fma2(ah, bh, np);                           // ah bh - p, exact
+  e = fma2(ah, bl, fma2(al, bh, e));
+  const f32x2 s = sub2(h, np);                          // TwoSum(h, p)
+  const f32x2 bb = sub2(s, h);
+  const f32x2 er = sub2(sub2(h, sub2(s, bb)), add2(np, bb));
+  h = s;
+  l = add2(l, add2(er, e));
+}
+
 __device__ __forceinline__ void split_df(double x, float& h, float& l) {
   h = __double2float_rn(x);
   l = __double2float_rn(x - (double)h);
@@ -634,27 +683,32 @@ __global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
   }
 
   // ---- compute warps ----
-  float vh[SLOTS][2], vl[SLOTS][2], wh[SLOTS][2], wl[SLOTS][2];
+  // (even, odd) column pairs: vin as packed (hi, lo) and -hi, the column
+  // accumulators as packed (hi, lo), folded into FP64 wd
+  f32x2 vh[SLOTS], vhn[SLOTS], vl[SLOTS], wh[SLOTS], wl[SLOTS];
   double wd[SLOTS][2];
 #pragma unroll
-  for (int s = 0; s < SLOTS; ++s)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      split_df(ldexp(vv[s][e], -ve), vh[s][e], vl[s][e]);
-      wh[s][e] = wl[s][e] = 0.0f;
-      wd[s][e] = 0.0;
-    }
+  for (int s = 0; s < SLOTS; ++s) {
+    float h0, l0, h1, l1;
+    split_df(ldexp(vv[s][0], -ve), h0, l0);
+    split_df(ldexp(vv[s][1], -ve), h1, l1);
+    vh[s] = pk2(h0, h1);
+    vhn[s] = pk2(-h0, -h1);
+    vl[s] = pk2(l0, l1);
+    wh[s] = wl[s] = 0ull;   // +0.0f in both lanes
+    wd[s][0] = wd[s][1] = 0.0;
+  }
   double escale = 0.0;
   int since_fold = 0;
   auto fold = [&]() {
     if (E != kNoExp) {
 #pragma unroll
-      for (int s = 0; s < SLOTS; ++s)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          wd[s][e] += escale * ((double)wh[s][e] + (double)wl[s][e]);
-          wh[s][e] = wl[s][e] = 0.0f;
-        }
+      for (int s = 0; s < SLOTS; ++s) {
+        const float2 h = upk2(wh[s]), l = upk2(wl[s]);
+        wd[s][0] += escale * ((double)h.x + (double)l.x);
+        wd[s][1] += escale * ((double)h.y + (double)l.y);
+        wh[s] = wl[s] = 0ull;
+      }
     }
     since_fold = 0;
   };
@@ -675,14 +729,14 @@ __global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
     for (int r = 0; r < RB; ++r) {
       if (r >= nr) break;
       const float th = tch[par][r], tl = tcl[par][r];
+      const f32x2 th2 = pk2(th, th), thn2 = pk2(-th, -th), tl2 = pk2(tl, tl);
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int c = 2 * tid + 2 * kThreads * s;
         if (c < C) {
-          const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
-          const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
-          df_fma(th, tl, a.x, b.x, wh[s][0], wl[s][0]);
-          df_fma(th, tl, a.y, b.y, wh[s][1], wl[s][1]);
+          const f32x2 a = *reinterpret_cast<const f32x2*>(hp + (size_t)r * rstride + c);
+          const f32x2 b = *reinterpret_cast<const f32x2*>(lp + (size_t)r * rstride + c);
+          df_fma2(a, b, th2, thn2, tl2, wh[s], wl[s]);
         }
       }
     }
@@ -708,22 +762,22 @@ __global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
       for (int r = 0; r < RB; ++r) {
         float h = 0.0f, l = 0.0f;
         if (have && r < nr) {
-          // two independent chains (even and odd columns), joined once
-          float h1 = 0.0f, l1 = 0.0f;
+          // one packed chain: even columns in one lane, odd columns in the other
+          f32x2 h2 = 0ull, l2 = 0ull;
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
             const int c = 2 * tid + 2 * kThreads * s;
             if (c < C) {
-              const float2 a = *reinterpret_cast<const float2*>(hp + (size_t)r * rstride + c);
-              const float2 b = *reinterpret_cast<const float2*>(lp + (size_t)r * rstride + c);
-              df_fma(a.x, b.x, vh[s][0], vl[s][0], h, l);
-              df_fma(a.y, b.y, vh[s][1], vl[s][1], h1, l1);   // vin is 0 past C
+              const f32x2 a = *reinterpret_cast<const f32x2*>(hp + (size_t)r * rstride + c);
+              const f32x2 b = *reinterpret_cast<const f32x2*>(lp + (size_t)r * rstride + c);
+              df_fma2(a, b, vh[s], vhn[s], vl[s], h2, l2);   // vin is 0 past C
             }
           }
+          const float2 hh = upk2(h2), ll = upk2(l2);
           float sum, er;
-          two_sum_f(h, h1, sum, er);
+          two_sum_f(hh.x, hh.y, sum, er);
           h = sum;
-          l += l1 + er;
+          l = ll.x + (ll.y + er);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

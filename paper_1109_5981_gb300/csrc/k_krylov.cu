@@ -407,8 +407,8 @@ static lsrn_status fill(Plan* p, double* v, int64_t n, double val) {
 }
 
 // One fused pass (+ ridge rows) and its reduction into out (C) and scal[SC_SS].
-static lsrn_status fused_pass(Plan* p, const double* vin, const RowArgs& a, double* out,
-                              const int* done) {
+static lsrn_status fused_pass_local(Plan* p, const double* vin, const RowArgs& a, double* out,
+                                    const int* done) {
   if (p->csr) return csr_fused_pass(p, vin, a, out, p->tcsr, p->scal + SC_SS, done);
   if (p->time_passes) {
     cudaEvent_t e0, e1;
@@ -424,6 +424,33 @@ static lsrn_status fused_pass(Plan* p, const double* vin, const RowArgs& a, doub
   LSRN_TRY(launch_extra_rows(p, vin, a, p->pvec, p->pscal, done));
   const int nslots = p->nblk + (p->extra_rows > 0 ? 1 : 0);
   return launch_reduce(p->pvec, nslots, p->xcols, out, p->pscal, p->scal + SC_SS, done, p->stream);
+}
+
+// The pass, and for a shard the sum over shards of its column vector and its
+// sum of squares (one exchange of q + 1 values; out has room for q + 2).
+static lsrn_status fused_pass(Plan* p, const double* vin, const RowArgs& a, double* out,
+                              const int* done) {
+  LSRN_TRY(fused_pass_local(p, vin, a, out, done));
+  if (!p->sharded) return LSRN_OK;
+  if (done != nullptr) {   // after convergence the pass wrote nothing: nothing to exchange
+    int d = 0;             // (the flag is the same on every shard: identical recurrences)
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&d, done, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (d != 0) return LSRN_OK;
+  }
+  const int64_t C = p->xcols;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(out + C, p->scal + SC_SS, sizeof(double), cudaMemcpyDeviceToDevice,
+                                p->stream));
+  LSRN_TRY(shard_sum(p, out, C + 1));
+  LSRN_CUDA_TRY(cudaMemcpyAsync(p->scal + SC_SS, out + C, sizeof(double), cudaMemcpyDeviceToDevice,
+                                p->stream));
+  return LSRN_OK;
+}
+
+// ||v||^2 of a vector over the long side (b): summed over the shards.
+static lsrn_status sumsq_long(Plan* p, const double* v, int64_t n, double* out) {
+  LSRN_TRY(sumsq(p, v, n, out));
+  return shard_sum(p, out, 1);
 }
 
 static const double* c100(Plan* p) { return p->scal + SC_ONE; }   // (1, 0, 0)
@@ -536,10 +563,9 @@ lsrn_status run_lsqr(Plan* p, int* iters, int* istop) {
     // u state = b (rows m) and zeros for the ridge rows; ||b||^2.
     LSRN_CUDA_TRY(cudaMemcpyAsync(p->st0, p->bdev, p->m * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
     LSRN_TRY(fill(p, p->st0 + p->m, p->nstate - p->m, 0.0));
-    LSRN_TRY(sumsq(p, p->bdev, p->m, p->scal + SC_SS));
     RowArgs a0{RM_ACC_STATE, p->st0, nullptr, nullptr, 1.0};
     LSRN_TRY(fused_pass(p, nullptr, a0, p->vq, nullptr));
-    LSRN_TRY(sumsq(p, p->bdev, p->m, p->scal + SC_SS));   // the pass overwrote SC_SS
+    LSRN_TRY(sumsq_long(p, p->bdev, p->m, p->scal + SC_SS));   // the pass overwrote SC_SS
     LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, tmpr, nullptr, nullptr, c100(p), nullptr, p->stream));
     launch(lsqr_tall_init_kernel, 1, kCtl, 0, p->stream, p->scal, p->iscal, tmpr, v, w, y, r);
     LSRN_CUDA_TRY(cudaGetLastError());
@@ -609,7 +635,7 @@ lsrn_status run_cs(Plan* p, int* iters, double* sL_out, double* sU_out, bool* di
     double* y = p->vr[2];
     LSRN_CUDA_TRY(cudaMemcpyAsync(p->st0, p->bdev, p->m * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
     LSRN_TRY(fill(p, p->st0 + p->m, p->nstate - p->m, 0.0));
-    LSRN_TRY(sumsq(p, p->bdev, p->m, p->scal + SC_SS0));
+    LSRN_TRY(sumsq_long(p, p->bdev, p->m, p->scal + SC_SS0));
     RowArgs a0{RM_ACC_STATE, p->st0, nullptr, nullptr, 1.0};
     LSRN_TRY(fused_pass(p, nullptr, a0, p->vq, nullptr));
     LSRN_TRY(fill(p, v, r, 0.0));
@@ -679,6 +705,7 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
       LSRN_TRY(launch_gemv_dd(p->Nm, q, r, y, x, p->stream));
       LSRN_TRY(launch_dd_pass(p, x, p->bdev, p->st1, p->pvec, p->pvec2, nullptr));
       LSRN_TRY(launch_reduce_dd(p->pvec, p->pvec2, nslots, q, p->vq, p->vq2, p->stream));
+      LSRN_TRY(shard_sum_dd(p, p->vq, p->vq2, q));
       // g = hi + lo
       launch(axpy_kernel, grid_for(q), 256, 0, p->stream, p->vq, p->vq2, q, 1.0);
       LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, h, nullptr, nullptr, c100(p), nullptr, p->stream));

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) sketch_f64_kernel(const double* __restric
                                                          int64_t Q, int64_t ldx, double xscale,
                                                          int64_t S, uint64_t seed, uint32_t tag,
                                                          int64_t lchunk, double* __restrict__ out,
-                                                         int64_t ldo, int64_t out_stride_z) {
+                                                         int64_t ldo, int64_t out_stride_z,
+                                                         int64_t lbase) {
   __shared__ double Gs[SK_BK][SK_BM];
   __shared__ double Xs[SK_BK][SK_BN];
   const int tid = threadIdx.x;
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(256) sketch_f64_kernel(const double* __restric
       const int64_t l = l0 + lr;
       const int64_t i = i0 + 4 * g4;
       float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (l < lend && i < S) z = normal4(seed, tag, (uint64_t)l, (uint64_t)(i >> 2));
+      if (l < lend && i < S) z = normal4(seed, tag, (uint64_t)(lbase + l), (uint64_t)(i >> 2));
       Gs[lr][4 * g4 + 0] = (l < lend && i + 0 < S) ? (double)quantize_g(z.x) : 0.0;
       Gs[lr][4 * g4 + 1] = (l < lend && i + 1 < S) ? (double)quantize_g(z.y) : 0.0;
       Gs[lr][4 * g4 + 2] = (l < lend && i + 2 < S) ? (double)quantize_g(z.z) : 0.0;
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(256) sketch_csr_kernel(const int64_t* __restri
                                                          const double* __restrict__ vals,
                                                          int64_t Q, double xscale, int64_t S,
                                                          uint64_t seed, uint32_t tag,
-                                                         double* __restrict__ C, int64_t ldc) {
+                                                         double* __restrict__ C, int64_t ldc,
+                                                         int64_t lbase) {
   const int64_t j = blockIdx.x;
   const int64_t ib = (int64_t)blockIdx.y * 1024;
   const int tid = threadIdx.x;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(256) sketch_csr_kernel(const int64_t* __restri
     const int64_t l = rowidx[e];
     const double a = vals[e] * xscale;
     if (i < S) {
-      const float4 z = normal4(seed, tag, (uint64_t)l, (uint64_t)(i >> 2));
+      const float4 z = normal4(seed, tag, (uint64_t)(lbase + l), (uint64_t)(i >> 2));
       acc[0] = fma(a, (double)quantize_g(z.x), acc[0]);
       acc[1] = fma(a, (double)quantize_g(z.y), acc[1]);
       acc[2] = fma(a, (double)quantize_g(z.z), acc[2]);
@@ -197,18 +199,20 @@ size_t sketch_f64_scratch_bytes(int64_t L, int64_t Q, int64_t S) {
 
 lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                               int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
-                              double* scratch, size_t scratch_bytes, cudaStream_t st) {
+                              double* scratch, size_t scratch_bytes, cudaStream_t st,
+                              int64_t lbase) {
   const int64_t z = splitk_factor(L, Q, S);
   const int64_t lchunk = ((L + z - 1) / z + SK_BK - 1) / SK_BK * SK_BK;
   const int64_t nz = (L + lchunk - 1) / lchunk;
   dim3 grid((unsigned)((Q + SK_BN - 1) / SK_BN), (unsigned)((S + SK_BM - 1) / SK_BM), (unsigned)nz);
   if (nz == 1) {
-    launch(sketch_f64_kernel, grid, 256, 0, st, X, L, Q, ldx, xscale, S, seed, tag, lchunk, C, ldc, 0);
+    launch(sketch_f64_kernel, grid, 256, 0, st, X, L, Q, ldx, xscale, S, seed, tag, lchunk, C, ldc,
+           (int64_t)0, lbase);
   } else {
     if (scratch == nullptr || scratch_bytes < (size_t)nz * S * Q * sizeof(double))
       return LSRN_ERR_INVALID_ARG;
     launch(sketch_f64_kernel, grid, 256, 0, st, X, L, Q, ldx, xscale, S, seed, tag, lchunk, scratch, Q,
-                                            S * Q);
+           S * Q, lbase);
     const int64_t tot = S * Q;
     launch(splitk_reduce_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, scratch, (int)nz, S, Q, C,
                                                                           ldc);
@@ -229,7 +233,7 @@ lsrn_status launch_sketch_f64_splitk_into(const double* X, int64_t L, int64_t Q,
   if ((size_t)(nz * S * Q) > scratch_doubles) return LSRN_ERR_INVALID_ARG;
   dim3 grid((unsigned)((Q + SK_BN - 1) / SK_BN), (unsigned)((S + SK_BM - 1) / SK_BM), (unsigned)nz);
   launch(sketch_f64_kernel, grid, dim3(256), 0, st, X, L, Q, ldx, 1.0, S, seed, tag, lchunk,
-         scratch, Q, S * Q);
+         scratch, Q, S * Q, (int64_t)0);
   const int64_t tot = S * Q;
   launch(splitk_reduce_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st,
          (const double*)scratch, (int)nz, S, Q, C, ldc);
@@ -259,11 +263,13 @@ lsrn_status launch_gamma_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t 
 
 lsrn_status launch_sketch_csr(const int64_t* colptr, const int32_t* rowidx, const double* vals,
                               int64_t L, int64_t Q, double xscale, int64_t S, uint64_t seed,
-                              uint32_t tag, double* C, int64_t ldc, cudaStream_t st) {
+                              uint32_t tag, double* C, int64_t ldc, cudaStream_t st,
+                              int64_t lbase) {
   (void)L;
   if (Q == 0 || S == 0) return LSRN_OK;
   dim3 grid((unsigned)Q, (unsigned)((S + 1023) / 1024));
-  launch(sketch_csr_kernel, grid, 256, 0, st, colptr, rowidx, vals, Q, xscale, S, seed, tag, C, ldc);
+  launch(sketch_csr_kernel, grid, 256, 0, st, colptr, rowidx, vals, Q, xscale, S, seed, tag, C, ldc,
+         lbase);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }

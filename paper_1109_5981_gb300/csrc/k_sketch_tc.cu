@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256) gamma_digits_kernel(uint64_t seed, uint32
                                                            int64_t l1, int64_t S, int64_t Sp,
                                                            int64_t Lp,
                                                            uint16_t* __restrict__ Gh,
-                                                           uint16_t* __restrict__ Gl) {
+                                                           uint16_t* __restrict__ Gl, int64_t lbase) {
   __shared__ unsigned short th[32][129], tl[32][129];
   const int64_t ib = (int64_t)blockIdx.x * 128, lb = (int64_t)blockIdx.y * 32;
   // generate: thread -> (row r of 32, group of four sketch indices g4 of 32)
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256) gamma_digits_kernel(uint64_t seed, uint32
     const int64_t l = l0 + lb + r;
     const int64_t i = ib + 4 * g4;
     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (l < l1 && i < S) z = normal4(seed, tag, (uint64_t)l, (uint64_t)(i >> 2));
+    if (l < l1 && i < S) z = normal4(seed, tag, (uint64_t)(lbase + l), (uint64_t)(i >> 2));
     const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -486,7 +486,8 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
                              cudaStream_t st,
-                             std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events) {
+                             std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events,
+                             int64_t lbase) {
   const int64_t Qp = (Q + TC_N - 1) / TC_N * TC_N;
   const int64_t Sp = (S + TC_M - 1) / TC_M * TC_M;
   const int64_t Lp = (seg_rows + TC_KT - 1) / TC_KT * TC_KT;
@@ -509,7 +510,7 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
     launch(split_x_kernel, dim3((unsigned)(Qp / 32), (unsigned)(Lp / 32)), dim3(256), 0, st, X, l0,
            l1, Q, ldx, (const int*)ecol, Qp, Lp, D);
     launch(gamma_digits_kernel, dim3((unsigned)(Sp / 128), (unsigned)(Lp / 32)), dim3(256), 0, st,
-           seed, tag, l0, l1, S, Sp, Lp, Gh, Gl);
+           seed, tag, l0, l1, S, Sp, Lp, Gh, Gl, lbase);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (gemm_events) {
       cudaEventCreate(&e0);

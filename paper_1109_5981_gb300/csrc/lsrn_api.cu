@@ -159,6 +159,8 @@ static void release(Plan* p) {
   if (p->stream) {
     for (void* ptr : p->owned) cudaFreeAsync(ptr, p->stream);
     if (p->coefs) cudaFreeAsync(p->coefs, p->stream);
+    if (p->shard.send) cudaFreeAsync(p->shard.send, p->stream);
+    if (p->shard.recv) cudaFreeAsync(p->shard.recv, p->stream);
     cudaStreamSynchronize(p->stream);
   }
   for (auto& e : p->ev)
@@ -202,7 +204,7 @@ static lsrn_status plan_workspace(Plan* p) {
   // +2: the staged pass copies row state in 16-byte units
   LSRN_TRY(dalloc_n(p, &p->st0, p->nstate + 2));
   LSRN_TRY(dalloc_n(p, &p->st1, p->nstate + 2));
-  LSRN_TRY(dalloc_n(p, &p->vq, q));
+  LSRN_TRY(dalloc_n(p, &p->vq, q + 2));   // + 2: a sharded pass appends its sum of squares
   LSRN_TRY(dalloc_n(p, &p->vq2, q));
   LSRN_TRY(dalloc_n(p, &p->tmpq, q));
   for (auto& v : p->vr) LSRN_TRY(dalloc_n(p, &v, q));
@@ -304,6 +306,7 @@ const char* lsrn_status_string(lsrn_status s) {
     case LSRN_ERR_QUEUE_FULL: return "LSRN_ERR_QUEUE_FULL";
     case LSRN_ERR_STATE: return "LSRN_ERR_STATE";
     case LSRN_ERR_UNSUPPORTED: return "LSRN_ERR_UNSUPPORTED";
+    case LSRN_ERR_COMM: return "LSRN_ERR_COMM";
   }
   return "LSRN_UNKNOWN_STATUS";
 }
@@ -334,8 +337,8 @@ lsrn_status lsrn_default_options(lsrn_options* opt) {
   return LSRN_OK;
 }
 
-lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
-                      lsrn_plan_t* out) {
+static lsrn_status plan_create(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
+                               const lsrn_shard* sh, lsrn_plan_t* out) {
   if (out == nullptr || A == nullptr) return LSRN_ERR_INVALID_ARG;
   *out = nullptr;
   if (A->m < 1 || A->n < 1 || A->values == nullptr) return LSRN_ERR_INVALID_ARG;
@@ -369,6 +372,16 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   p->m = A->m;
   p->n = A->n;
   p->tall = A->m >= A->n;
+  if (sh != nullptr) {   // a shard: orientation from the whole matrix; exchanges when world > 1
+    p->sharded = sh->world > 1;
+    p->tall = true;
+    p->shard.rank = sh->rank;
+    p->shard.world = sh->world;
+    p->shard.lbase = sh->row_offset;
+    p->shard.long_total = sh->m_total;
+    p->shard.fn = sh->allgather;
+    p->shard.ctx = sh->ctx;
+  }
   p->lam = o.lambda;
   p->ridge = o.lambda > 0.0;
   p->csr = A->format == LSRN_CSR;
@@ -377,7 +390,7 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   p->q = p->xcols;
   p->s = (int64_t)std::ceil(o.gamma * (double)p->q);
   if (p->s <= p->q) p->s = p->q + 1;
-  if (p->ridge) {
+  if (p->ridge && !(p->sharded && p->shard.rank != 0)) {   // shard 0 holds the rows lambda I
     p->extra_rows = p->tall ? A->n : A->m;
     p->extra_coef = p->tall ? o.lambda : 1.0;
     p->xscale = p->tall ? 1.0 : 1.0 / o.lambda;
@@ -422,6 +435,25 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   return LSRN_OK;
 }
 
+lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
+                      lsrn_plan_t* out) {
+  return plan_create(A, opt, stream, nullptr, out);
+}
+
+lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* opt,
+                              const lsrn_shard* shard, void* stream, lsrn_plan_t* out) {
+  if (out == nullptr || A_local == nullptr || shard == nullptr) return LSRN_ERR_INVALID_ARG;
+  *out = nullptr;
+  const lsrn_shard& sh = *shard;
+  if (sh.world < 1 || sh.rank < 0 || sh.rank >= sh.world) return LSRN_ERR_INVALID_ARG;
+  if (sh.world > 1 && sh.allgather == nullptr) return LSRN_ERR_INVALID_ARG;
+  if (sh.row_offset < 0 || A_local->m < 1 || sh.m_total < sh.row_offset + A_local->m)
+    return LSRN_ERR_INVALID_ARG;
+  if (sh.m_total > (int64_t)0xFFFFFFFFll) return LSRN_ERR_INVALID_ARG;   // G's row counter word
+  if (sh.m_total < A_local->n) return LSRN_ERR_UNSUPPORTED;               // Algorithm 2 is not sharded
+  return plan_create(A_local, opt, stream, &sh, out);
+}
+
 lsrn_status lsrn_sketch(lsrn_plan_t p) {
   if (p == nullptr) return LSRN_ERR_INVALID_ARG;
   cudaSetDevice(p->device);
@@ -429,7 +461,7 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
   const uint32_t tag = 0;
   if (p->csr) {
     LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, p->xscale, p->s,
-                               p->opt.seed, tag, p->Xs, p->q, p->stream));
+                               p->opt.seed, tag, p->Xs, p->q, p->stream, p->shard.lbase));
   } else if (p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED) {
     int64_t seg = sketch_tc_plan_segment_rows(p->xrows, p->q, p->s);
     if (const char* env = getenv("LSRN_TC_SEGMENT_ROWS")) {   // testing: force small segments
@@ -442,7 +474,7 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
     LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), p->stream));
     lsrn_status st = launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
                                       tag, p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR,
-                                      p->stream, &p->gemm_events);
+                                      p->stream, &p->gemm_events, p->shard.lbase);
     cudaFreeAsync(buf, p->stream);
     LSRN_TRY(st);
   } else {
@@ -450,13 +482,16 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
     double* buf = nullptr;
     if (scratch) LSRN_CUDA_TRY(lsrn_malloc_async((void**)&buf, scratch, p->stream));
     lsrn_status st = launch_sketch_f64(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
-                                       tag, p->Xs, p->q, buf, scratch, p->stream);
+                                       tag, p->Xs, p->q, buf, scratch, p->stream, p->shard.lbase);
     if (buf) cudaFreeAsync(buf, p->stream);
     LSRN_TRY(st);
   }
-  if (p->ridge)
-    LSRN_TRY(launch_sketch_add_gamma(p->Xs, p->q, p->s, p->q, p->opt.seed, tag, p->xrows,
-                                     p->extra_coef, p->stream));
+  if (p->ridge && p->extra_rows > 0)   // the rows lambda I (or I_m) follow the last row of X
+    LSRN_TRY(launch_sketch_add_gamma(p->Xs, p->q, p->s, p->q, p->opt.seed, tag,
+                                     p->shard.long_total > 0 ? p->shard.long_total : p->xrows,
+                                     p->extra_coef,
+                                     p->stream));
+  LSRN_TRY(shard_sum(p, p->Xs, p->s * p->q));   // A~ = sum over shards of G_p A_p
   cudaEventRecord(p->ev[1], p->stream);
   p->state = 1;   // a new sketch invalidates an earlier preconditioner
   return LSRN_OK;
@@ -515,7 +550,7 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   if (p->state < 2) LSRN_TRY(lsrn_precond(p, nullptr));
   lsrn_info inf;
   memset(&inf, 0, sizeof(inf));
-  inf.m = p->m;
+  inf.m = p->shard.long_total > 0 ? p->shard.long_total : p->m;
   inf.n = p->n;
   inf.s = p->s;
   inf.rank = p->rank;

@@ -81,6 +81,18 @@ struct RowArgs {
   double sx;            // constant scale of every X row
 };
 
+// ---- row sharding (lsrn_plan_sharded) ----------------------------------------
+struct Shard {
+  int rank = 0, world = 1;
+  int64_t lbase = 0;              // global long-side index of this shard's first row
+  int64_t long_total = 0;         // long side of the whole matrix
+  lsrn_allgather_fn fn = nullptr;
+  void* ctx = nullptr;
+  double* send = nullptr;         // plan-owned staging: cap doubles
+  double* recv = nullptr;         // world * cap doubles
+  int64_t cap = 0;
+};
+
 // ---- the plan -----------------------------------------------------------
 struct Plan {
   int device = 0;
@@ -158,13 +170,25 @@ struct Plan {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;   // fused passes of the main sweep
   bool time_passes = false;
   float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0, t_qr_ms = 0, t_jacobi_ms = 0;
+  bool sharded = false;             // a shard of a row-partitioned matrix (lsrn_plan_sharded)
+  Shard shard;
 };
+
+// Sum `count` doubles at `buf` (device) over the shards of a sharded plan:
+// allgather through the caller's callback, then a fixed rank-order sum on the
+// device, identical on every shard.  No-op for an unsharded plan.
+lsrn_status shard_sum(Plan* p, double* buf, int64_t count);
+// The same for a double-double vector (hi, lo), summed in double-double.
+lsrn_status shard_sum_dd(Plan* p, double* hi, double* lo, int64_t count);
 
 // ---- kernels (launchers) -------------------------------------------------
 // sketch: C (S x Q, ldc) = xscale * Gamma[lrow0 : lrow0+L]^T X   (X: L x Q row-major)
+// lbase: long-side index of X's first row in the whole matrix (G is drawn at
+// rows lbase + l; nonzero for a shard of a row-partitioned matrix).
 lsrn_status launch_sketch_f64(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
                               int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
-                              double* scratch, size_t scratch_bytes, cudaStream_t st);
+                              double* scratch, size_t scratch_bytes, cudaStream_t st,
+                              int64_t lbase = 0);
 size_t sketch_f64_scratch_bytes(int64_t L, int64_t Q, int64_t S);
 // Same sketch, always through split-K partial sums held in caller-provided
 // scratch (scratch_doubles >= nz * S * Q for the split nz it picks, nz >= 1).
@@ -188,7 +212,8 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
                              int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
                              void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
                              cudaStream_t st,
-                             std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events);
+                             std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events,
+                             int64_t lbase = 0);
 // C[i, j] = scale_c * C[i, j] + coef * Gamma[lrow0 + j, i], i < S, j < Q
 lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st);
@@ -197,7 +222,8 @@ lsrn_status launch_gamma_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t 
 // CSR sketch: C (S x Q) = xscale * Gamma^T X with X given by its columns (CSC of X)
 lsrn_status launch_sketch_csr(const int64_t* colptr, const int32_t* rowidx, const double* vals,
                               int64_t L, int64_t Q, double xscale, int64_t S, uint64_t seed,
-                              uint32_t tag, double* C, int64_t ldc, cudaStream_t st);
+                              uint32_t tag, double* C, int64_t ldc, cudaStream_t st,
+                              int64_t lbase = 0);
 
 // Theorem 4.5 bounds (sigma_L, sigma_U) for the plan's r and s and alpha option
 lsrn_status thm45_bounds(const Plan* p, double* sL, double* sU);

@@ -97,13 +97,16 @@ class _Reflectors:
 
 def dense_householder(m: int, n: int, rank: int, cond: float, noise: float, seed: int,
                       n_reflectors: int = 8, device: Optional[str] = None,
-                      row_block: int = 65536) -> DenseProblem:
+                      row_block: int = 65536, rows: Optional[tuple] = None) -> DenseProblem:
     """Dense A = U diag(sigma) V^T with U, V products of seeded Householder reflectors.
 
     A = Q [W; 0] with W = diag(sigma) V^T (rank x n) and Q = I - Y T Y^T, so
     A = [W; 0] - Y (T Y[:rank]^T W): a rank-k update written row block by row
     block.  With ``device`` set (a torch device string) A and b are built there
-    with torch, otherwise with numpy on the host.
+    with torch, otherwise with numpy on the host.  With ``rows = (r0, r1)``
+    (device path) only rows r0 .. r1 - 1 of A and b are built -- one shard of a
+    row-partitioned problem; the factors (apply_Ut, ...) stay those of the
+    whole matrix.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     k = n_reflectors
@@ -130,18 +133,19 @@ def dense_householder(m: int, n: int, rank: int, cond: float, noise: float, seed
     else:
         import torch
         dev = torch.device(device)
-        A = torch.empty((m, n), dtype=torch.float64, device=dev)
+        lo, hi = rows if rows is not None else (0, m)
+        A = torch.empty((hi - lo, n), dtype=torch.float64, device=dev)
         Zt = torch.from_numpy(Z).to(dev)
         Wt = torch.from_numpy(W).to(dev)
         Yt = torch.from_numpy(QU.Y).to(dev)
-        for r0 in range(0, m, row_block):
-            r1 = min(m, r0 + row_block)
+        for r0 in range(lo, hi, row_block):
+            r1 = min(hi, r0 + row_block)
             blk = -(Yt[r0:r1] @ Zt)
             if r0 < rank:
                 t = min(r1, rank)
                 blk[: t - r0] += Wt[r0:t]
-            A[r0:r1] = blk
-        b = A @ torch.from_numpy(x0).to(dev) + noise * torch.from_numpy(e).to(dev)
+            A[r0 - lo:r1 - lo] = blk
+        b = A @ torch.from_numpy(x0).to(dev) + noise * torch.from_numpy(e[lo:hi]).to(dev)
 
     def apply_Ut(v: np.ndarray) -> np.ndarray:
         return QU.apply_t(np.asarray(v, dtype=np.float64).reshape(m, 1))[:rank, 0]
@@ -226,9 +230,9 @@ def c1_problem(seed: int = 0) -> DenseProblem:
 
 
 def c2_problem(seed: int = 0, device: Optional[str] = None, m: int = 1_000_000,
-               n: int = 2000, rank: int = 1800) -> DenseProblem:
+               n: int = 2000, rank: int = 1800, rows: Optional[tuple] = None) -> DenseProblem:
     """10^6 x 2000, rank 1800, sigma 1 -> 1e-6, 8 Householder reflectors, noise 1e-4."""
-    return dense_householder(m, n, rank, 1e6, 1e-4, seed, device=device)
+    return dense_householder(m, n, rank, 1e6, 1e-4, seed, device=device, rows=rows)
 
 
 def c3_problem(seed: int = 0, m: int = 10_000, n: int = 1_000_000, nnz_per_row: int = 2000,
