@@ -55,7 +55,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solver", default="lsqr", choices=["lsqr", "cs"])
-    ap.add_argument("--sketch", default="tc", choices=["f64", "tc"])
+    ap.add_argument("--sketch", default="tc", choices=["f64", "tc", "bf16", "auto"])
     ap.add_argument("--iter", default="x2", choices=["f64", "f32", "x2"])
     ap.add_argument("--m", type=int, default=M)
     ap.add_argument("--n", type=int, default=N)
@@ -68,7 +68,7 @@ def parse(argv=None):
     ap.add_argument("--parallel", default="shard", choices=["shard", "replica"],
                     help="N > 1: shard = one problem split by rows over the ranks (section 4.4, "
                          "strong scaling); replica = an independent problem per rank (weak)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "serving", "c1"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "serving", "c1", "sketch"],
                     help="dense: the 1e6 x 2000 solve; serving: a Poisson stream of mixed-size "
                          "requests through lsrn_submit/lsrn_poll; c1: latency of the 2000 x 100 "
                          "rank-80 FP64 solve")
@@ -535,6 +535,85 @@ def traffic_for(phase: str, args, m_local: int):
     return None
 
 
+def sketch_mode_of(L, name: str) -> int:
+    return {"f64": L.LSRN_SKETCH_F64, "tc": L.LSRN_SKETCH_TC_SLICED, "bf16": L.LSRN_SKETCH_BF16,
+            "auto": L.LSRN_SKETCH_AUTO}[name]
+
+
+def run_sketch(args):
+    """Algorithm 1 steps 2-3 alone on the 10^6 x 2000 matrix: one step = one
+    lsrn_sketch (G drawn on the fly and A~ = G A) on a plan made before the
+    timed region; the tensor-core GEMM is timed by the library's CUDA events."""
+    import torch
+    import paper_1109_5981_gb300 as L
+    import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.load_library()
+    P = W.c2_problem(seed=0, device="cuda", m=args.m, n=args.n, rank=args.rank)
+    mode = sketch_mode_of(L, args.sketch)
+    plan = L.lsrn_plan(P.A, L.default_options(seed=1234, sketch_mode=mode))
+    lib = L.load_library()
+    s = math.ceil(2.0 * args.n)
+
+    def one():
+        L.lsrn_sketch(plan)
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        one()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = L.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gemm_ms = []
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        one()
+        # the library accumulates its GEMM events into the plan until lsrn_precond reads them;
+        # lsrn_plan_get_sketch does not, so time the GEMM through a precond-free probe below
+    ev1.record()
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1)
+    launches = L.kernel_launches() - launches0
+    clk = clocks.stop()
+    # one more sketch + precond to read the GEMM kernel time from lsrn_info
+    L.lsrn_sketch(plan)
+    L.lsrn_precond(plan)
+    _, info = L.lsrn_solve_lsqr(plan, P.b, allow=(L.LSRN_OK, L.LSRN_ERR_NOT_CONVERGED))
+    plan.close()
+    t_gemm = info["t_sketch_gemm_ms"] if mode in (L.LSRN_SKETCH_TC_SLICED, L.LSRN_SKETCH_BF16) \
+        else info["t_sketch_ms"]
+    peaks = _measured_peaks()
+    bf16 = peaks.get("bf16_tflops_burst", peaks.get("bf16_tflops", 1902.3))
+    flops = 2.0 * s * args.m * args.n
+    ach = flops / (t_gemm * 1e-3) / 1e12
+    work_mult = 15 if mode == L.LSRN_SKETCH_TC_SLICED else 1
+    line = {
+        "metric": f"sketch A~ = G A per second (dense {args.m}x{args.n}, s = {s}, sketch {args.sketch})",
+        "value": args.steps / (elapsed * 1e-3), "unit": "sketches/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": elapsed / args.steps,
+        "higher_is_better": True,
+        "dtype": {"tc": "bf16 exact digit slices (FP64-accurate)", "bf16": "bf16 operands, f32 accumulate",
+                  "f64": "f64", "auto": "bf16 (auto)"}[args.sketch],
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": f"dense tall {args.m}x{args.n} rank {args.rank}, gamma 2",
+                   "l2": "inputs larger than L2 (A is 16 GB)"},
+        "roofline": {"kernel": {"tc": "sketch_tc_kernel", "bf16": "sketch_bf16_kernel",
+                                "auto": "sketch_bf16_kernel", "f64": "sketch_f64_kernel"}[args.sketch],
+                     "bound": "tensor" if mode != L.LSRN_SKETCH_F64 else "alu",
+                     "ms": t_gemm, "achieved": ach, "unit": "TFLOP/s",
+                     "peak": bf16 if mode != L.LSRN_SKETCH_F64 else L.probe_fp64_fma(),
+                     "peak_source": "bf16_tflops (burst) of measured (MEASURED_PEAKS.json)"
+                     if mode != L.LSRN_SKETCH_F64 else "FP64 FMA rate probed in this run",
+                     "work": f"2*s*m*n = {flops:.3e} flop", "mma_work_multiple": work_mult},
+        "sketch_ms_total": info["t_sketch_ms"], "gpu_launches": int(launches), "clocks": clk,
+    }
+    line["roofline"]["frac"] = ach / line["roofline"]["peak"]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_dense(args):
     import torch
     import paper_1109_5981_gb300 as L
@@ -573,8 +652,7 @@ def run_dense(args):
     # x* = V Sigma^-1 U^T b from the generator's planted factors
     xstar = P.apply_V(P.apply_Ut(b_full) / P.sigma)
     opts = L.default_options(seed=1234 + (0 if sharded else rank),
-                             sketch_mode=L.LSRN_SKETCH_TC_SLICED if args.sketch == "tc"
-                             else L.LSRN_SKETCH_F64,
+                             sketch_mode=sketch_mode_of(L, args.sketch),
                              iter_mode={"f32": L.LSRN_ITER_F32, "x2": L.LSRN_ITER_F32X2}.get(
                                  args.iter, L.LSRN_ITER_F64))
     solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
@@ -741,6 +819,8 @@ def main():
         return run_serving(args)
     if args.workload == "c1":
         return run_small(args)
+    if args.workload == "sketch":
+        return run_sketch(args)
     return run_dense(args)
 
 

@@ -89,8 +89,19 @@ typedef enum {
 
 typedef enum {
   LSRN_SKETCH_F64 = 0,          /* FP64 FMA arithmetic */
-  LSRN_SKETCH_TC_SLICED = 1     /* tensor cores on exact bf16 slices of G and A,
+  LSRN_SKETCH_TC_SLICED = 1,    /* tensor cores on exact bf16 slices of G and A,
                                    FP64-accurate (dense A only) */
+  LSRN_SKETCH_BF16 = 2,         /* tensor cores on G and A rounded once to bf16, FP32
+                                   accumulation per 2048 rows, FP64 beyond (dense A only): a
+                                   subspace embedding with ~2^-8 relative error, enough for a
+                                   preconditioner of a well-conditioned full-rank A; the
+                                   iterations still use the FP64 A */
+  LSRN_SKETCH_AUTO = 3          /* dense A: BF16 first; the exact sliced sketch instead as
+                                   soon as the BF16 noise floor eta = 2^-8 ||A~||_F / sqrt(n')
+                                   exceeds sigma_min(A~) / 16 (seen on the QR's diagonal or
+                                   in the final spectrum: rank-deficient or ill-conditioned A).
+                                   A kept BF16 preconditioner widens the Chebyshev bounds by
+                                   2 eta / sigma_min.  CSR: the FP64 sketch. */
 } lsrn_sketch_mode;
 
 /* The matrix A (m x n).  For LSRN_CSR, columns within a row need not be
@@ -149,6 +160,8 @@ typedef struct {
   float t_qr_ms;                  /* Householder QR of the sketch inside t_precond_ms */
   int32_t jacobi_sweeps;          /* one-sided Jacobi sweeps of the preconditioner */
   float t_jacobi_ms;              /* the Jacobi sweeps inside t_precond_ms */
+  int32_t sketch_used;            /* lsrn_sketch_mode of the sketch the preconditioner used */
+  int32_t sketch_escalated;       /* 1: LSRN_SKETCH_AUTO replaced the BF16 sketch by the exact one */
 } lsrn_info;
 
 typedef struct lsrn_plan_s* lsrn_plan_t;

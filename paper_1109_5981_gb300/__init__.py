@@ -36,7 +36,7 @@ LSRN_ERR_COMM = -10
 
 LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
-LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED = 0, 1
+LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED, LSRN_SKETCH_BF16, LSRN_SKETCH_AUTO = 0, 1, 2, 3
 LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2 = 0, 1, 2
 LSRN_KNOB_JACOBI_WAIT_NS, LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 0, 1
 
@@ -69,7 +69,8 @@ class lsrn_info(ctypes.Structure):
                 ("t_refine_ms", ctypes.c_float), ("t_sketch_gemm_ms", ctypes.c_float),
                 ("t_pass_ms", ctypes.c_float), ("n_pass", ctypes.c_int32),
                 ("t_qr_ms", ctypes.c_float), ("jacobi_sweeps", ctypes.c_int32),
-                ("t_jacobi_ms", ctypes.c_float)]
+                ("t_jacobi_ms", ctypes.c_float), ("sketch_used", ctypes.c_int32),
+                ("sketch_escalated", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

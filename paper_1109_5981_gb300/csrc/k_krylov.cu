@@ -528,6 +528,9 @@ lsrn_status thm45_bounds(const Plan* p, double* sL, double* sU) {
   if (!(lo > 0.0)) return LSRN_ERR_INVALID_ARG;
   *sU = 1.0 / lo;
   *sL = 1.0 / ((1.0 + a) * std::sqrt(s) + std::sqrt(r));
+  // a BF16 preconditioner: sigma(AN) may leave the bounds by its noise floor
+  *sU *= 1.0 + p->bound_widen;
+  *sL *= 1.0 - p->bound_widen;
   return LSRN_OK;
 }
 

@@ -22,6 +22,8 @@
 // FP32 accumulators in TMEM, 8 x 64 columns).  The planes are stored as
 // pre-swizzled tiles, so each stage is ten contiguous bulk copies
 // (cp.async.bulk with mbarrier transaction counts).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -69,6 +71,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
   for (long long it = 0; it < kSpinLimit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(err, 1);
+  return false;
+}
+
+// Wait bounded by elapsed time on the global timer (ns); on timeout record the
+// failure and return false.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, int* err,
+                                             uint64_t limit_ns) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 63) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > limit_ns) break;
+    }
+  }
   atomicExch(err, 1);
   return false;
 }
@@ -461,6 +481,267 @@ __global__ void zero_kernel(double* __restrict__ C, int64_t S, int64_t Q, int64_
   if (idx < S * Q) C[(idx / Q) * ldc + idx % Q] = 0.0;
 }
 
+
+// ---- single-pass BF16 sketch (sketch mode LSRN_SKETCH_BF16) -------------------
+// C = Gamma^T X with both operands rounded to bf16 once (Gamma's 2^-12 grid
+// value, and X / 2^e_j with a per-column exponent so any FP64 range fits) and
+// FP32 accumulation on the tensor cores: a subspace embedding with relative
+// error ~2^-8, for well-conditioned full-rank problems (see the AUTO mode).
+// Tile 128 sketch rows x 256 columns of X; one CTA per tile and K split.
+// Warp 0 streams K-tiles (16 KB of Gamma, 32 KB of X, pre-swizzled) into a
+// four-stage ring with bulk copies; warp 1 issues the MMAs (M=128, N=256,
+// K=16) into one of two TMEM accumulators (256 columns each), switching every
+// 2048 rows; warps 2-9 drain a finished accumulator into FP32 registers while
+// the MMAs fill the other, so FP32 rounding grows with 2048 rather than with
+// the whole K range.  Each CTA writes its FP64 partial tile; a fixed-order
+// reduction adds the K splits.
+constexpr int BF_M = 128, BF_N = 256, BF_KT = 64, BF_STAGES = 4, BF_CHUNK_KT = 32;
+constexpr int BF_A_BYTES = BF_M * BF_KT * 2;             // 16 KB
+constexpr int BF_B_BYTES = BF_N * BF_KT * 2;             // 32 KB
+constexpr int BF_STAGE_BYTES = BF_A_BYTES + BF_B_BYTES;  // 48 KB
+constexpr int BF_THREADS = 320;
+constexpr int BF_SMEM = BF_STAGES * BF_STAGE_BYTES + 1024 + 256;
+constexpr uint64_t kBfWaitNs = 200000000ull;   // 0.2 s per wait
+__device__ __forceinline__ bool bf_wait(uint64_t* bar, uint32_t parity, int* err) {
+  return mbar_wait_ns(bar, parity, err, kBfWaitNs);
+}
+
+__global__ void __launch_bounds__(BF_THREADS, 1) sketch_bf16_kernel(
+    const uint16_t* __restrict__ Gt, const uint16_t* __restrict__ Xt, int64_t Lp, int64_t nkt,
+    int64_t kt_per_split, const int* __restrict__ ecol, int64_t S, int64_t Q,
+    double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + BF_STAGES * BF_STAGE_BYTES);
+  uint64_t* full = bars;                       // [BF_STAGES]
+  uint64_t* empty = bars + BF_STAGES;          // [BF_STAGES]
+  uint64_t* tfull = bars + 2 * BF_STAGES;      // [2] accumulator b holds a finished chunk
+  uint64_t* tempty = tfull + 2;                // [2] accumulator b drained (8 warp arrivals)
+  uint64_t* mdone = tempty + 2;                // all MMAs of this CTA complete
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* s_issued = (volatile int*)(tmem_slot + 2);
+  volatile int* s_consumed = (volatile int*)(tmem_slot + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * BF_M;
+  const int64_t j0 = (int64_t)blockIdx.y * BF_N;
+  const int64_t kb = (int64_t)blockIdx.z * kt_per_split;
+  const int64_t ke = min(nkt, kb + kt_per_split);
+  const int nk = (int)max((int64_t)0, ke - kb);
+  const int nchunks = (nk + BF_CHUNK_KT - 1) / BF_CHUNK_KT;
+  const int64_t nkt_row = Lp / BF_KT;          // K-tiles per tile row of a plane
+
+  if (tid == 0) {
+    for (int q = 0; q < BF_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(&tfull[0], 1);
+    mbar_init(&tfull[1], 1);
+    mbar_init(&tempty[0], 8);
+    mbar_init(&tempty[1], 8);
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    *s_issued = 0;
+    *s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int k = 0; k < nk && !*abort_flag; ++k) {
+        const int st = k % BF_STAGES, n = k / BF_STAGES;
+        if (n >= 1 && !bf_wait(&empty[st], (uint32_t)((n - 1) & 1), err)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         smem_addr(&full[st])),
+                     "r"(BF_STAGE_BYTES)
+                     : "memory");
+        const uint32_t sa = smem_addr(smem + st * BF_STAGE_BYTES);
+        const int64_t kt = kb + k;
+        bulk_g2s(sa, Gt + tiled_off(i0, kt * BF_KT, BF_M, nkt_row), BF_A_BYTES, &full[st]);
+        bulk_g2s(sa + BF_A_BYTES, Xt + tiled_off(j0, kt * BF_KT, BF_N, nkt_row), BF_B_BYTES,
+                 &full[st]);
+        *s_issued = k + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc(BF_M, BF_N);
+      for (int k = 0; k < nk && !*abort_flag; ++k) {
+        const int c = k / BF_CHUNK_KT, b = c & 1;
+        const bool first = (k % BF_CHUNK_KT) == 0;
+        if (first && c >= 2 && !bf_wait(&tempty[b], (uint32_t)(((c >> 1) - 1) & 1), err)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int st = k % BF_STAGES;
+        if (!bf_wait(&full[st], (uint32_t)((k / BF_STAGES) & 1), err)) {
+          *abort_flag = 1;
+          break;
+        }
+        *s_consumed = k + 1;
+        tc_fence_after();
+        const uint64_t da = smem_desc(smem_addr(smem + st * BF_STAGE_BYTES));
+        const uint64_t db = da + (BF_A_BYTES >> 4);
+#pragma unroll
+        for (int ks = 0; ks < BF_KT / 16; ++ks)
+          mma_bf16(tmem + (uint32_t)(b * BF_N), da + 2 * ks, db + 2 * ks, idesc,
+                   (first && ks == 0) ? 0u : 1u);
+        mma_commit(&empty[st]);
+        if ((k % BF_CHUNK_KT) == BF_CHUNK_KT - 1 || k == nk - 1) mma_commit(&tfull[b]);
+      }
+      // every MMA issued above completes before the CTA frees TMEM or exits
+      mma_commit(mdone);
+      bf_wait(mdone, 0u, err);
+    }
+    __syncwarp();
+  } else {
+    // warps 2..9: TMEM lane quadrant warp % 4, columns [128 h, 128 h + 128), h = (warp - 2) / 4
+    const int quad = warp & 3, h = (warp - 2) >> 2;
+    float acc[128];
+#pragma unroll
+    for (int t = 0; t < 128; ++t) acc[t] = 0.0f;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      bool ok = true;
+      if (lane == 0) ok = bf_wait(&tfull[b], (uint32_t)((c >> 1) & 1), err);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || *abort_flag) {
+        if (lane == 0) *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BF_N + h * 128);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float v[32];
+        tmem_ld32(base + (uint32_t)(g * 32), v);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) acc[g * 32 + t] += v[t];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty[b])) : "memory");
+    }
+    const int64_t i = i0 + quad * 32 + lane;
+    if (i < S && !*abort_flag) {
+      double* out = part + (int64_t)blockIdx.z * S * Q + i * Q;
+#pragma unroll
+      for (int t = 0; t < 128; ++t) {
+        const int64_t j = j0 + h * 128 + t;
+        if (j < Q) out[j] = ldexp((double)acc[t], col_exponent(ecol, j));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort_flag) {
+    atomicExch(err, 1);
+    // copies issued but never consumed must land before the CTA's memory is released
+    for (int k = *s_consumed; k < *s_issued; ++k)
+      bf_wait(&full[k % BF_STAGES], (uint32_t)((k / BF_STAGES) & 1), err);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// bf16 tiles of X rows [l0, l1) scaled by 2^-e_j: D[tiled_off(j, l - l0, 256, Lp / 64)]
+__global__ void __launch_bounds__(256) x_bf16_kernel(const double* __restrict__ X, int64_t l0,
+                                                     int64_t l1, int64_t Q, int64_t ldx,
+                                                     const int* __restrict__ ecol, int64_t Qp,
+                                                     int64_t Lp, uint16_t* __restrict__ D) {
+  __shared__ unsigned short tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t jb = (int64_t)blockIdx.x * 32, lb = (int64_t)blockIdx.y * 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t l = l0 + lb + r, j = jb + tx;
+    unsigned short v = 0;
+    if (l < l1 && j < Q) {
+      const __nv_bfloat16 bv = __double2bfloat16(ldexp(X[l * ldx + j], -col_exponent(ecol, j)));
+      v = *reinterpret_cast<const unsigned short*>(&bv);
+    }
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = jb + r, l = lb + tx;
+    if (j < Qp && l < Lp) D[tiled_off(j, l, BF_N, Lp / BF_KT)] = tile[tx][r];
+  }
+}
+
+// bf16 tiles of Gamma rows [l0, l1): G[tiled_off(i, l - l0, 128, Lp / 64)] = bf16(Gamma[l, i])
+__global__ void __launch_bounds__(256) gamma_bf16_kernel(uint64_t seed, uint32_t tag, int64_t l0,
+                                                         int64_t l1, int64_t S, int64_t Sp, int64_t Lp,
+                                                         uint16_t* __restrict__ G, int64_t lbase) {
+  __shared__ unsigned short tg[32][129];
+  const int64_t ib = (int64_t)blockIdx.x * 128, lb = (int64_t)blockIdx.y * 32;
+  for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+    const int r = q >> 5, g4 = q & 31;
+    const int64_t l = l0 + lb + r;
+    const int64_t i = ib + 4 * g4;
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l < l1 && i < S) z = normal4(seed, tag, (uint64_t)(lbase + l), (uint64_t)(i >> 2));
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float g = (l < l1 && i + k < S) ? quantize_g(zz[k]) : 0.0f;
+      const __nv_bfloat16 bv = __float2bfloat16_rn(g);
+      tg[r][4 * g4 + k] = *reinterpret_cast<const unsigned short*>(&bv);
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 128 * 32; q += 256) {
+    const int ii = q >> 5, r = q & 31;
+    const int64_t i = ib + ii, l = lb + r;
+    if (i < Sp && l < Lp) G[tiled_off(i, l, BF_M, Lp / BF_KT)] = tg[r][ii];
+  }
+}
+
+// C[i, j] += scale * sum_z part[z][i, j], z in order
+__global__ void bf16_reduce_kernel(const double* __restrict__ part, int nz, int64_t S, int64_t Q,
+                                   double scale, double* __restrict__ C, int64_t ldc) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * Q) return;
+  double acc = 0.0;
+  for (int z = 0; z < nz; ++z) acc += part[(int64_t)z * S * Q + idx];
+  C[(idx / Q) * ldc + idx % Q] += scale * acc;
+}
+
+// K split of the BF16 sketch: the smallest split whose CTA count fills whole
+// waves of one CTA per SM to >= 95%, else the best of at most 64.
+int bf16_ksplit(int64_t tiles, int64_t nkt) {
+  const int64_t sms = num_sms();
+  int best = 1;
+  double best_eff = 0.0;
+  for (int z = 1; z <= 64 && z <= std::max<int64_t>(1, nkt / 8); ++z) {
+    const int64_t ctas = tiles * z;
+    const int64_t waves = (ctas + sms - 1) / sms;
+    const double eff = (double)ctas / (double)(waves * sms);
+    if (eff >= 0.95) return z;
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = z;
+    }
+  }
+  return best;
+}
 }  // namespace
 
 // Scratch bytes for a given segment length (rows of X per segment).
@@ -526,6 +807,85 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
       cudaEventRecord(e1, st);
       gemm_events->emplace_back(e0, e1);
     }
+  }
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+
+// ---- BF16 sketch launcher -----------------------------------------------------
+static int64_t bf16_dims_Sp(int64_t S) { return (S + BF_M - 1) / BF_M * BF_M; }
+static int64_t bf16_dims_Qp(int64_t Q) { return (Q + BF_N - 1) / BF_N * BF_N; }
+// K splits of a segment of nkt K-tiles: bf16_ksplit, with the FP64 partial
+// tiles (one S x Q copy per split) held to 1 GiB.
+static int bf16_split_for(int64_t S, int64_t Q, int64_t nkt) {
+  const int64_t tiles = (bf16_dims_Sp(S) / BF_M) * (bf16_dims_Qp(Q) / BF_N);
+  const int64_t cap = std::max<int64_t>(1, ((int64_t)1 << 30) / std::max<int64_t>(1, S * Q * 8));
+  return (int)std::min<int64_t>(bf16_ksplit(tiles, nkt), cap);
+}
+
+size_t sketch_bf16_scratch_bytes(int64_t Ls, int64_t Q, int64_t S) {
+  const int64_t Lp = (Ls + BF_KT - 1) / BF_KT * BF_KT;
+  return (size_t)(bf16_dims_Sp(S) + bf16_dims_Qp(Q)) * Lp * 2 + (size_t)Q * sizeof(int) + 256 +
+         (size_t)bf16_split_for(S, Q, Lp / BF_KT) * S * Q * sizeof(double);
+}
+
+int64_t sketch_bf16_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_bytes) {
+  const size_t fixed = ((size_t)1 << 30) + (size_t)Q * 4 + 256;
+  const int64_t per_row = (bf16_dims_Sp(S) + bf16_dims_Qp(Q)) * 2;
+  const size_t room = budget_bytes > fixed ? budget_bytes - fixed : (size_t)per_row * BF_KT;
+  int64_t rows = (int64_t)(room / (size_t)per_row);
+  rows = std::max<int64_t>(BF_KT, rows / BF_KT * BF_KT);
+  const int64_t Lr = (L + BF_KT - 1) / BF_KT * BF_KT;
+  return std::min(rows, Lr);
+}
+
+lsrn_status launch_sketch_bf16(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
+                               int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
+                               void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
+                               cudaStream_t st,
+                               std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events,
+                               int64_t lbase) {
+  const int64_t Sp = bf16_dims_Sp(S), Qp = bf16_dims_Qp(Q);
+  const int64_t Lp = (seg_rows + BF_KT - 1) / BF_KT * BF_KT;
+  if (scratch_bytes < sketch_bf16_scratch_bytes(seg_rows, Q, S)) return LSRN_ERR_INVALID_ARG;
+  LSRN_CUDA_TRY(cudaFuncSetAttribute(sketch_bf16_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, BF_SMEM));
+  uint16_t* Gt = (uint16_t*)scratch;
+  uint16_t* Xt = Gt + Sp * Lp;
+  int* ecol = (int*)(Xt + Qp * Lp);
+  double* part = (double*)(((uintptr_t)(ecol + Q) + 255) & ~(uintptr_t)255);
+  const int64_t tot = S * Q;
+  launch(zero_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, C, S, Q, ldc);
+  const int64_t tiles = (Sp / BF_M) * (Qp / BF_N);
+  for (int64_t l0 = 0; l0 < L; l0 += seg_rows) {
+    const int64_t l1 = std::min(L, l0 + seg_rows);
+    const int64_t nkt = (l1 - l0 + BF_KT - 1) / BF_KT;
+    const int64_t rpb = 1024;
+    launch(colexp_init_kernel, dim3((unsigned)((Q + 255) / 256)), dim3(256), 0, st, ecol, Q);
+    launch(colexp_kernel, dim3((unsigned)((Q + 127) / 128), (unsigned)((l1 - l0 + rpb - 1) / rpb)),
+           dim3(128), 0, st, X, l0, l1, Q, ldx, rpb, ecol);
+    launch(x_bf16_kernel, dim3((unsigned)(Qp / 32), (unsigned)(Lp / 32)), dim3(256), 0, st, X, l0, l1,
+           Q, ldx, (const int*)ecol, Qp, Lp, Xt);
+    launch(gamma_bf16_kernel, dim3((unsigned)(Sp / 128), (unsigned)(Lp / 32)), dim3(256), 0, st,
+           seed, tag, l0, l1, S, Sp, Lp, Gt, lbase);
+    const int z = bf16_split_for(S, Q, nkt);
+    const int64_t per = (nkt + z - 1) / z;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (gemm_events) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, st);
+    }
+    launch(sketch_bf16_kernel, dim3((unsigned)(Sp / BF_M), (unsigned)(Qp / BF_N), (unsigned)z),
+           dim3(BF_THREADS), (size_t)BF_SMEM, st, (const uint16_t*)Gt, (const uint16_t*)Xt, Lp, nkt,
+           per, (const int*)ecol, S, Q, part, err);
+    if (gemm_events) {
+      cudaEventRecord(e1, st);
+      gemm_events->emplace_back(e0, e1);
+    }
+    launch(bf16_reduce_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st,
+           (const double*)part, z, S, Q, xscale, C, ldc);
   }
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;

@@ -760,12 +760,52 @@ __global__ void form_n_kernel(const double* __restrict__ W, int64_t Q, const int
   N[i * r + k] = v;
 }
 
+// out[0] = sum of squares of v[0:n] (one CTA, fixed order per thread then tree)
+__global__ void __launch_bounds__(1024) sumsq_one_kernel(const double* __restrict__ v, int64_t n,
+                                                         double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 1024) acc = fma(v[i], v[i], acc);
+  acc = group_sum<32>(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 32; ++w) t += sh[w];
+    out[0] = t;
+  }
+}
+
+// out[0] = min_i |R[i, i]| over the diagonal of the QR-factored sketch (row-major, ld Q)
+__global__ void __launch_bounds__(1024) min_abs_diag_kernel(const double* __restrict__ X, int64_t Q,
+                                                            double* __restrict__ out) {
+  __shared__ double sh[32];
+  double mn = INFINITY;
+  for (int64_t i = threadIdx.x; i < Q; i += 1024) mn = fmin(mn, fabs(X[i * Q + i]));
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = INFINITY;
+    for (int w = 0; w < 32; ++w) t = fmin(t, sh[w]);
+    out[0] = t;
+  }
+}
+
 }  // namespace
 
-lsrn_status run_precond(Plan* p) {
+lsrn_status run_precond(Plan* p, bool bf16_check) {
   cudaStream_t st = p->stream;
   const int64_t S = p->s, Q = p->q;
   double* X = p->Xs;
+  if (bf16_check) {
+    // noise floor of a BF16 sketch: 2^-8 of the root-mean-square singular value
+    double f2 = 0.0;
+    launch(sumsq_one_kernel, 1, 1024, 0, st, (const double*)X, S * Q, p->tmpq);
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&f2, p->tmpq, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+    p->bf16_noise = 0x1p-8 * std::sqrt(f2 / (double)std::max<int64_t>(Q, 1));
+  }
   // 1. Householder QR.  Up to kQrBlockedMin columns one column at a time (three
   // launches per column, the trailing update spread over the whole GPU); beyond
   // that in panels of kQrNb columns, where the O(S q^2) trailing work runs as a
@@ -816,6 +856,14 @@ lsrn_status run_precond(Plan* p) {
     cudaFreeAsync(qws, st);
   }
   cudaEventRecord(p->ev[8], st);
+  if (bf16_check && p->opt.sketch_mode == LSRN_SKETCH_AUTO) {
+    // sigma_min(R) <= min |R_ii|: below the floor already, the Jacobi is skipped
+    double dmin = 0.0;
+    launch(min_abs_diag_kernel, 1, 1024, 0, st, (const double*)X, Q, p->tmpq);
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&dmin, p->tmpq, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(dmin >= 16.0 * p->bf16_noise)) return kPrecondEscalate;
+  }
   // 2. One-sided Jacobi on the rows of R.
   const int64_t QQ = Q * Q;
   launch(extract_r_kernel, (unsigned)((QQ + 255) / 256), 256, 0, st, X, Q, p->Wj);

@@ -180,8 +180,7 @@ static lsrn_status validate_options(const lsrn_options& o) {
   if (!(o.lambda >= 0.0) || !std::isfinite(o.lambda)) return LSRN_ERR_INVALID_ARG;
   if (o.refine_max < 0 || o.refine_max > 16) return LSRN_ERR_INVALID_ARG;
   if (!(o.refine_tol > 0.0) || !(o.refine_tol < 1.0)) return LSRN_ERR_INVALID_ARG;
-  if (o.sketch_mode != LSRN_SKETCH_F64 && o.sketch_mode != LSRN_SKETCH_TC_SLICED)
-    return LSRN_ERR_INVALID_ARG;
+  if (o.sketch_mode < LSRN_SKETCH_F64 || o.sketch_mode > LSRN_SKETCH_AUTO) return LSRN_ERR_INVALID_ARG;
   if (o.iter_mode != LSRN_ITER_F64 && o.iter_mode != LSRN_ITER_F32 &&
       o.iter_mode != LSRN_ITER_F32X2)
     return LSRN_ERR_INVALID_ARG;
@@ -454,30 +453,38 @@ lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* op
   return plan_create(A_local, opt, stream, &sh, out);
 }
 
-lsrn_status lsrn_sketch(lsrn_plan_t p) {
-  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
-  cudaSetDevice(p->device);
-  cudaEventRecord(p->ev[0], p->stream);
+// The sketch Xs with the given arithmetic (dense: F64, TC_SLICED or BF16; CSR
+// always FP64), plus the ridge rows and, for a shard, the sum over shards.
+static lsrn_status sketch_with(Plan* p, int mode) {
   const uint32_t tag = 0;
   if (p->csr) {
+    mode = LSRN_SKETCH_F64;
     LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, p->xscale, p->s,
                                p->opt.seed, tag, p->Xs, p->q, p->stream, p->shard.lbase));
-  } else if (p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED) {
-    int64_t seg = sketch_tc_plan_segment_rows(p->xrows, p->q, p->s);
+  } else if (mode == LSRN_SKETCH_TC_SLICED || mode == LSRN_SKETCH_BF16) {
+    const bool bf = mode == LSRN_SKETCH_BF16;
+    int64_t seg = bf ? sketch_bf16_segment_rows(p->xrows, p->q, p->s, kTcScratchBudget)
+                     : sketch_tc_plan_segment_rows(p->xrows, p->q, p->s);
     if (const char* env = getenv("LSRN_TC_SEGMENT_ROWS")) {   // testing: force small segments
       const long long v = atoll(env);
       if (v >= 64) seg = std::min<int64_t>(seg, (int64_t)(v / 64 * 64));
     }
-    const size_t scratch = sketch_tc_scratch_bytes(seg, p->q, p->s);
+    const size_t scratch = bf ? sketch_bf16_scratch_bytes(seg, p->q, p->s)
+                              : sketch_tc_scratch_bytes(seg, p->q, p->s);
     void* buf = nullptr;
     LSRN_CUDA_TRY(lsrn_malloc_async(&buf, scratch, p->stream));
     LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), p->stream));
-    lsrn_status st = launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
-                                      tag, p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR,
-                                      p->stream, &p->gemm_events, p->shard.lbase);
+    lsrn_status st =
+        bf ? launch_sketch_bf16(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed, tag,
+                                p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR, p->stream,
+                                &p->gemm_events, p->shard.lbase)
+           : launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed, tag,
+                              p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR, p->stream,
+                              &p->gemm_events, p->shard.lbase);
     cudaFreeAsync(buf, p->stream);
     LSRN_TRY(st);
   } else {
+    mode = LSRN_SKETCH_F64;
     const size_t scratch = sketch_f64_scratch_bytes(p->xrows, p->q, p->s);
     double* buf = nullptr;
     if (scratch) LSRN_CUDA_TRY(lsrn_malloc_async((void**)&buf, scratch, p->stream));
@@ -492,6 +499,33 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
                                      p->extra_coef,
                                      p->stream));
   LSRN_TRY(shard_sum(p, p->Xs, p->s * p->q));   // A~ = sum over shards of G_p A_p
+  p->sketch_used = mode;
+  return LSRN_OK;
+}
+
+// A tensor-core sketch's bounded waits: LSRN_ERR_TIMEOUT if one gave up.
+static lsrn_status check_tc_error(Plan* p) {
+  if (p->sketch_used != LSRN_SKETCH_TC_SLICED && p->sketch_used != LSRN_SKETCH_BF16) return LSRN_OK;
+  int tcerr = 0;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(&tcerr, p->iscal + IC_TCERR, sizeof(int), cudaMemcpyDeviceToHost,
+                                p->stream));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return tcerr ? LSRN_ERR_TIMEOUT : LSRN_OK;
+}
+
+lsrn_status lsrn_sketch(lsrn_plan_t p) {
+  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
+  cudaSetDevice(p->device);
+  cudaEventRecord(p->ev[0], p->stream);
+  const int mode = p->opt.sketch_mode == LSRN_SKETCH_AUTO ? LSRN_SKETCH_BF16 : p->opt.sketch_mode;
+  for (auto& pr : p->gemm_events) {   // GEMM times of an earlier sketch of this plan
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  p->gemm_events.clear();
+  p->sketch_escalated = false;
+  p->bound_widen = 0.0;
+  LSRN_TRY(sketch_with(p, mode));
   cudaEventRecord(p->ev[1], p->stream);
   p->state = 1;   // a new sketch invalidates an earlier preconditioner
   return LSRN_OK;
@@ -501,16 +535,33 @@ lsrn_status lsrn_precond(lsrn_plan_t p, int64_t* rank_out) {
   if (p == nullptr) return LSRN_ERR_INVALID_ARG;
   if (p->state < 1) return LSRN_ERR_STATE;
   cudaSetDevice(p->device);
-  if (!p->csr && p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED) {
-    int tcerr = 0;
-    LSRN_CUDA_TRY(cudaMemcpyAsync(&tcerr, p->iscal + IC_TCERR, sizeof(int), cudaMemcpyDeviceToHost,
-                                  p->stream));
-    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    if (tcerr) return LSRN_ERR_TIMEOUT;
+  {
+    const lsrn_status st = check_tc_error(p);
+    if (st != LSRN_OK) {
+      p->state = 0;
+      return st;
+    }
   }
   cudaEventRecord(p->ev[2], p->stream);
   {
-    const lsrn_status st = run_precond(p);
+    const bool auto_bf16 = p->opt.sketch_mode == LSRN_SKETCH_AUTO && p->sketch_used == LSRN_SKETCH_BF16;
+    const bool measure = auto_bf16 || p->sketch_used == LSRN_SKETCH_BF16;
+    lsrn_status st = run_precond(p, measure);
+    double eta = 1.0;   // BF16 noise floor relative to sigma_min
+    if (st == LSRN_OK && measure)
+      eta = (p->rank == p->q && p->sigma_min > 0.0) ? p->bf16_noise / p->sigma_min : 1.0;
+    if (auto_bf16 && (st == kPrecondEscalate || (st == LSRN_OK && !(eta <= 1.0 / 16.0)))) {
+      // the BF16 embedding cannot resolve this spectrum: the exact sketch instead
+      st = sketch_with(p, LSRN_SKETCH_TC_SLICED);
+      if (st == LSRN_OK) st = check_tc_error(p);
+      if (st == LSRN_OK) st = run_precond(p, false);
+      p->sketch_escalated = true;
+      p->bound_widen = 0.0;
+    } else if (st == kPrecondEscalate) {
+      st = LSRN_ERR_CUDA;   // cannot happen: only AUTO asks for the early check to return
+    } else if (st == LSRN_OK && measure) {
+      p->bound_widen = std::min(2.0 * eta, 0.9);
+    }
     if (st != LSRN_OK) {
       p->state = 0;   // the QR has overwritten the sketch: a retry must sketch again
       return st;
@@ -562,6 +613,8 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   inf.t_qr_ms = p->t_qr_ms;
   inf.jacobi_sweeps = p->sweeps;
   inf.t_jacobi_ms = p->t_jacobi_ms;
+  inf.sketch_used = p->sketch_used;
+  inf.sketch_escalated = p->sketch_escalated ? 1 : 0;
   inf.t_sketch_gemm_ms = p->t_sketch_gemm_ms;
   lsrn_status result = LSRN_OK;
   const bool xdev = is_device_pointer(x);

@@ -170,6 +170,10 @@ struct Plan {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;   // fused passes of the main sweep
   bool time_passes = false;
   float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0, t_qr_ms = 0, t_jacobi_ms = 0;
+  int sketch_used = LSRN_SKETCH_F64;   // sketch arithmetic that produced Xs
+  bool sketch_escalated = false;       // AUTO replaced the BF16 sketch by the exact one
+  double bf16_noise = 0.0;             // 2^-8 ||A~||_F / sqrt(q) of a BF16 sketch
+  double bound_widen = 0.0;            // relative widening of the Theorem 4.5 bounds
   bool sharded = false;             // a shard of a row-partitioned matrix (lsrn_plan_sharded)
   Shard shard;
 };
@@ -214,6 +218,16 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
                              cudaStream_t st,
                              std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events,
                              int64_t lbase = 0);
+// Single-pass BF16 sketch (operands rounded to bf16 once, FP32 accumulation in
+// TMEM per 2048 rows, FP64 across chunks and K splits); same contract.
+size_t sketch_bf16_scratch_bytes(int64_t Ls, int64_t Q, int64_t S);
+int64_t sketch_bf16_segment_rows(int64_t L, int64_t Q, int64_t S, size_t budget_bytes);
+lsrn_status launch_sketch_bf16(const double* X, int64_t L, int64_t Q, int64_t ldx, double xscale,
+                               int64_t S, uint64_t seed, uint32_t tag, double* C, int64_t ldc,
+                               void* scratch, size_t scratch_bytes, int64_t seg_rows, int* err,
+                               cudaStream_t st,
+                               std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events,
+                               int64_t lbase = 0);
 // C[i, j] = scale_c * C[i, j] + coef * Gamma[lrow0 + j, i], i < S, j < Q
 lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st);
@@ -229,8 +243,12 @@ lsrn_status launch_sketch_csr(const int64_t* colptr, const int32_t* rowidx, cons
 lsrn_status thm45_bounds(const Plan* p, double* sL, double* sU);
 bool is_device_pointer(const void* ptr);
 
-// SVD / preconditioner: Xs (S x Q) -> N (Q x r), NT, sig; returns rank
-lsrn_status run_precond(Plan* p);
+// SVD / preconditioner: Xs (S x Q) -> N (Q x r), NT, sig; returns rank.
+// With bf16_check the sketch's noise floor p->bf16_noise is measured first, and
+// the call returns kPrecondEscalate right after the QR when the smallest
+// |R_ii| (an upper bound on sigma_min) is below 16 times it.
+constexpr lsrn_status kPrecondEscalate = (lsrn_status)100;   // internal, never returned by the ABI
+lsrn_status run_precond(Plan* p, bool bf16_check = false);
 // Server-owned plans launch the Jacobi rounds directly (see Plan::graph_sweeps).
 void plan_disable_sweep_graphs(lsrn_plan_t p);
 

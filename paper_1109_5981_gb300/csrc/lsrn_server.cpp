@@ -58,8 +58,12 @@ size_t estimate_bytes(const lsrn_matrix& A, const lsrn_options& o) {
   size_t work = 8 * ((size_t)s * q + 3 * (size_t)q * q + 6 * (size_t)(rows + extra) + 16 * (size_t)q);
   if (o.iter_mode == LSRN_ITER_F32 && A.format != LSRN_CSR) work += (size_t)m * n * 4;
   if (o.iter_mode == LSRN_ITER_F32X2 && A.format != LSRN_CSR) work += (size_t)m * n * 12;   // 3 planes
-  if (o.sketch_mode == LSRN_SKETCH_TC_SLICED && A.format != LSRN_CSR)   // the plan's exact sizing
+  if ((o.sketch_mode == LSRN_SKETCH_TC_SLICED || o.sketch_mode == LSRN_SKETCH_AUTO) &&
+      A.format != LSRN_CSR)   // the plan's exact sizing
     work += lsrn::sketch_tc_scratch_bytes(lsrn::sketch_tc_plan_segment_rows(rows, q, s - 1), q, s - 1);
+  if ((o.sketch_mode == LSRN_SKETCH_BF16 || o.sketch_mode == LSRN_SKETCH_AUTO) && A.format != LSRN_CSR)
+    work += lsrn::sketch_bf16_scratch_bytes(
+        lsrn::sketch_bf16_segment_rows(rows, q, s - 1, lsrn::kTcScratchBudget), q, s - 1);
   return a_bytes + work + ((size_t)64 << 20);
 }
 
