@@ -68,7 +68,10 @@ def parse(argv=None):
     ap.add_argument("--parallel", default="shard", choices=["shard", "replica"],
                     help="N > 1: shard = one problem split by rows over the ranks (section 4.4, "
                          "strong scaling); replica = an independent problem per rank (weak)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "serving", "c1", "sketch"],
+    ap.add_argument("--single-limit", type=int, default=512,
+                    help="batch workload: problems solved one at a time for the comparison lines")
+    ap.add_argument("--workload", default="dense",
+                    choices=["dense", "serving", "c1", "sketch", "batch"],
                     help="dense: the 1e6 x 2000 solve; serving: a Poisson stream of mixed-size "
                          "requests through lsrn_submit/lsrn_poll; c1: latency of the 2000 x 100 "
                          "rank-80 FP64 solve")
@@ -614,6 +617,92 @@ def run_sketch(args):
     return 0
 
 
+def run_batch(args):
+    """Many independent uneven problems: the batched configuration.  m
+    log-uniform in [5e3, 2e5], n log-uniform in [32, 512], 70% tall / 30% fat
+    (stored n x m), rank 0.8-1.0 min(m, n), condition 1e2-1e6, noise 1e-4.
+    Mixed precision, batched: one lsrn_solve_batch call (exact tensor-core
+    sketch, FP32 passes for tall problems with FP64 refinement, all small
+    preconditioners in one launch).  Compared with the FP64-plain solves (FP64
+    sketch and passes) and the same mixed solves, one problem at a time."""
+    import torch
+    import paper_1109_5981_gb300 as L
+    import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.load_library()
+    rng = np.random.Generator(np.random.PCG64(12))
+    count = args.requests
+    probs, xstars = [], []
+    for P, tall in W.serving_mix(count, seed=1000, device="cuda"):
+        if tall:
+            A, b = P.A, P.b
+            xstars.append(P.apply_V(P.apply_Ut(b.cpu().numpy()) / P.sigma))
+        else:
+            A = P.A.T.contiguous()
+            bn = rng.standard_normal(A.shape[0])
+            b = torch.from_numpy(bn).cuda()
+            xstars.append(P.apply_U(P.apply_Vt(bn) / P.sigma))
+        probs.append((A, b))
+    elems = sum(int(A.shape[0]) * int(A.shape[1]) for A, _ in probs)
+    mixed = L.default_options(seed=99, sketch_mode=L.LSRN_SKETCH_TC_SLICED, iter_mode=L.LSRN_ITER_F32)
+    plain = L.default_options(seed=99, sketch_mode=L.LSRN_SKETCH_F64, iter_mode=L.LSRN_ITER_F64)
+    solver = args.solver
+
+    def errors(xs):
+        return np.array([rel_error(x.cpu().numpy(), xs_) for x, xs_ in zip(xs, xstars)])
+
+    # warm-up on a few problems
+    L.lsrn_solve_batch(probs[:8], mixed, solver)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = L.kernel_launches()
+    t0 = time.perf_counter()
+    xs, infos, stats = L.lsrn_solve_batch(probs, mixed, solver)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    launches = L.kernel_launches() - launches0
+    clk = clocks.stop()
+    err_b = errors(xs)
+    ok_b = int(np.sum((np.array(stats) == L.LSRN_OK) & (err_b <= 1e-10)))
+    k1 = min(args.single_limit, count)
+
+    def one_at_a_time(opt):
+        out, t = [], time.perf_counter()
+        for A, b in probs[:k1]:
+            x, _ = L.solve(A, b, solver=solver, allow=(L.LSRN_OK, L.LSRN_ERR_NOT_CONVERGED),
+                           **{f: getattr(opt, f) for f, _ in L.lsrn_options._fields_})
+            out.append(x)
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t
+    xs1, t_mixed1 = one_at_a_time(mixed)
+    e1 = errors(xs1)[:k1]
+    xs64, t_plain = one_at_a_time(plain)
+    e64 = np.array([rel_error(x.cpu().numpy(), xs_) for x, xs_ in zip(xs64, xstars[:k1])])
+    ok64 = int(np.sum(e64 <= 1e-10))
+    line = {
+        "metric": "LS solves/s at <=1e-10 rel err: mixed batched vs FP64 plain (batched uneven mix)",
+        "value": ok_b / t_batch, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+        "problems": count, "solved_within_1e-10": ok_b, "batch_s": t_batch,
+        "elements_of_A": elems, "gb_of_A_fp64": elems * 8 / 1e9,
+        "rel_err": {"max": float(err_b.max()), "median": float(np.median(err_b))},
+        "fp64_plain_one_at_a_time": {"value": ok64 / t_plain, "problems": k1, "seconds": t_plain,
+                                     "within_1e-10": ok64, "max_rel_err": float(e64.max())},
+        "mixed_one_at_a_time": {"value": int(np.sum(e1 <= 1e-10)) / t_mixed1, "problems": k1,
+                                "seconds": t_mixed1},
+        "batched_over_fp64_plain": (ok_b / t_batch) / max(ok64 / t_plain, 1e-30),
+        "batched_precond_ms": float(np.median([i["t_precond_ms"] for i in infos])),
+        "dtype": "mixed: bf16 exact-slice sketch, f32 passes (tall) with f64 refinement, f64 SVD",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": f"{count} problems: m log-uniform [5e3, 2e5], n log-uniform [32, 512], "
+                               "70% tall / 30% fat, rank 0.8-1.0 min(m, n), cond 1e2-1e6, noise 1e-4",
+                   "solver": solver, "threads": 8},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_dense(args):
     import torch
     import paper_1109_5981_gb300 as L
@@ -821,6 +910,8 @@ def main():
         return run_small(args)
     if args.workload == "sketch":
         return run_sketch(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_dense(args)
 
 

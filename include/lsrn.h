@@ -104,6 +104,17 @@ typedef enum {
                                    2 eta / sigma_min.  CSR: the FP64 sketch. */
 } lsrn_sketch_mode;
 
+typedef enum {
+  LSRN_PRECOND_SVD = 0,         /* N = V~ Sigma~^-1 from the SVD of A~ (Algorithm 1/2 steps 4-5) */
+  LSRN_PRECOND_QR = 1           /* lambda > 0 only: N = R^-1 from the QR of A~.  The augmented
+                                   matrix has full rank, so A R^-1 = (A V~ Sigma~^-1) U_R^T has
+                                   the same singular values as A N (Lemma 4.3 unchanged), the
+                                   same Theorem 4.5 bounds and CS step count, and LSQR's
+                                   iterates up to the orthogonal change of variable U_R; the
+                                   one-sided Jacobi sweeps are not needed.  lsrn_plan_get_precond
+                                   then reports |R_ii| (descending) in place of sigma~. */
+} lsrn_precond_mode;
+
 /* The matrix A (m x n).  For LSRN_CSR, columns within a row need not be
  * sorted but must be in [0, n) and row_ptr must be non-decreasing with
  * row_ptr[0] = 0 and row_ptr[m] = nnz. */
@@ -135,6 +146,8 @@ typedef struct {
                           refinement steps, stopping once a step changes x by <= 1e-12;
                           correction passes switch from FP32 to FP64 as soon as a step
                           shrinks the change by less than 20x */
+  int32_t precond_mode;  /* lsrn_precond_mode (default LSRN_PRECOND_SVD); LSRN_PRECOND_QR
+                            needs lambda > 0 (INVALID_ARG otherwise) */
 } lsrn_options;
 
 typedef struct {
@@ -212,6 +225,16 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
  * Asynchronous on the plan's stream. */
 lsrn_status lsrn_sketch(lsrn_plan_t p);
 
+/* Sketch reuse across lambda (section 5): a plan created with lambda > 0 keeps
+ * the unaugmented part of its sketch (G_1 A for m >= n, A G_1 for m < n), and
+ * this call rebuilds A~ for a new lambda > 0 without touching A:
+ * A~ = G_1 A + lambda G_2 (m >= n, B = [A; lambda I]) or A G_1 / lambda + G_2
+ * (m < n, B = [A / lambda, I_m]).  The preconditioner is then recomputed by the
+ * next lsrn_precond / lsrn_solve_*.  INVALID_ARG if the plan was created with
+ * lambda = 0 or lambda is not finite and positive.  Before the first sketch it
+ * only records lambda.  Asynchronous. */
+lsrn_status lsrn_plan_set_lambda(lsrn_plan_t p, double lambda);
+
 /* Algorithm 1 steps 4-5 / Algorithm 2 steps 4-5: SVD of A~ on the device
  * (Householder QR, then one-sided Jacobi), numerical rank r, and N = V~
  * Sigma~^-1 (n x r) or M = U~ Sigma~^-1 (m x r).  Requires lsrn_sketch first
@@ -239,6 +262,56 @@ lsrn_status lsrn_solve_lsqr(lsrn_plan_t p, const double* b, double* x, lsrn_info
  * (the bounds did not hold); x then holds the last iterate.  INVALID_ARG if
  * (1 - alpha) sqrt(s) <= sqrt(r) (no valid upper bound). */
 lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* info);
+
+/* ---- choice of the oversampling factor gamma (section 4.3's cost model) ----
+ * The paper's operation count of a solve, split into the parts that depend on
+ * s = ceil(gamma q) (q = min(m, n)): the sketch (s m randn + 2 s m n) and the QR
+ * of the s x q sketch (2 s q^2) grow linearly in s, the SVD of the q x q
+ * triangle does not depend on s, and the iteration count falls with s --
+ * Theorem 4.6's bound (log eps - log 2) / log sqrt(r/s) for LSQR, Algorithm 3's
+ * K + 1 with Theorem 4.5's bounds (alpha = 1/sqrt(s)) for CS.  With per-unit
+ * costs measured on this GPU (e.g. from lsrn_info of an earlier solve), the
+ * predicted time T(gamma) = (c_sketch + c_qr) s + c_svd + c_iter N(gamma) is
+ * minimised over gamma on a grid of step 0.01.  Host arithmetic only. */
+typedef struct {
+  int64_t m, n;               /* problem size */
+  int64_t rank;               /* expected numerical rank r (<= 0: min(m, n)) */
+  double tol;                 /* epsilon of the iteration (<= 0: 1e-14) */
+  int32_t solver;             /* 0 LSQR, 1 CS */
+  double c_sketch;            /* ms per unit of s in the sketch */
+  double c_qr;                /* ms per unit of s in the QR of the sketch */
+  double c_svd;               /* ms of the SVD of the q x q triangle */
+  double c_iter;              /* ms per iteration */
+  double gamma_min, gamma_max;  /* search range (<= 0: 1.05 and 8) */
+} lsrn_gamma_model;
+
+/* Writes the gamma of least predicted time to *gamma and that time (ms) to
+ * *predicted_ms (either may be NULL).  INVALID_ARG for a NULL model, sizes < 1,
+ * negative costs or an empty range; UNSUPPORTED if no gamma in the range admits
+ * the solver (CS needs (1 - 1/sqrt(s)) sqrt(s) > sqrt(r)). */
+lsrn_status lsrn_choose_gamma(const lsrn_gamma_model* model, double* gamma, double* predicted_ms);
+
+/* ---- batched solve: many independent problems, phase by phase ----
+ * Solves count independent problems (A[k], b[k]) -> x[k] with the same options
+ * and solver (0 = LSQR, 1 = CS), each exactly as lsrn_plan + lsrn_solve_* would
+ * (Algorithm 1 or 2 per problem, by its own shape), but phase by phase over the
+ * whole batch:
+ *   - plans and sketches are issued for all problems from `threads` host threads
+ *     (0: 8), each problem on its own stream, so the sketches overlap on the GPU;
+ *   - the preconditioners of all problems whose short side is at most 512 and
+ *     whose sketch is F64 or TC_SLICED run in ONE persistent launch, one CTA per
+ *     problem (Householder QR, one-sided Jacobi, rank, N), largest first; other
+ *     problems take the per-problem path;
+ *   - the iterations run per problem from the host threads, overlapping.
+ * A, b, x: arrays of count descriptors / pointers (host or device data, as for
+ * lsrn_plan and lsrn_solve_*).  info, status: optional arrays of count entries
+ * receiving each problem's info and status.  Returns LSRN_OK if every problem
+ * succeeded, else the first failing status (the others are still solved).
+ * INVALID_ARG: count < 0, NULL arrays with count > 0, bad threads or solver.
+ * Synchronises. */
+lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* const* b,
+                             double* const* x, const lsrn_options* opt, int32_t solver,
+                             int32_t threads, lsrn_info* info, int32_t* status);
 
 /* ---- row-sharded solve (section 4.4: A partitioned by rows over processes) ----
  * One plan per shard (a GPU, a process or a host thread), each holding a block

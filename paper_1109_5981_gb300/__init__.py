@@ -39,6 +39,7 @@ LSRN_F64, LSRN_F32 = 0, 1
 LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED, LSRN_SKETCH_BF16, LSRN_SKETCH_AUTO = 0, 1, 2, 3
 LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2 = 0, 1, 2
 LSRN_KNOB_JACOBI_WAIT_NS, LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 0, 1
+LSRN_PRECOND_SVD, LSRN_PRECOND_QR = 0, 1
 
 
 class lsrn_matrix(ctypes.Structure):
@@ -53,7 +54,8 @@ class lsrn_options(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("cs_alpha", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("sketch_mode", ctypes.c_int32), ("iter_mode", ctypes.c_int32)]
+                ("sketch_mode", ctypes.c_int32), ("iter_mode", ctypes.c_int32),
+                ("precond_mode", ctypes.c_int32)]
 
 
 class lsrn_info(ctypes.Structure):
@@ -86,6 +88,14 @@ class lsrn_shard(ctypes.Structure):
                 ("allgather", lsrn_allgather_fn), ("ctx", ctypes.c_void_p)]
 
 
+class lsrn_gamma_model(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("rank", ctypes.c_int64),
+                ("tol", ctypes.c_double), ("solver", ctypes.c_int32),
+                ("c_sketch", ctypes.c_double), ("c_qr", ctypes.c_double),
+                ("c_svd", ctypes.c_double), ("c_iter", ctypes.c_double),
+                ("gamma_min", ctypes.c_double), ("gamma_max", ctypes.c_double)]
+
+
 class LsrnError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -109,6 +119,12 @@ _SIGS = {
     "lsrn_plan_sharded": ([ctypes.POINTER(lsrn_matrix), ctypes.POINTER(lsrn_options),
                            ctypes.POINTER(lsrn_shard), ctypes.c_void_p,
                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "lsrn_solve_batch": ([ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.POINTER(lsrn_options), ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "lsrn_plan_set_lambda": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    "lsrn_choose_gamma": ([ctypes.POINTER(lsrn_gamma_model), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lsrn_sketch": ([ctypes.c_void_p], ctypes.c_int),
     "lsrn_precond": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "lsrn_solve_lsqr": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -374,6 +390,66 @@ def lsrn_plan_sharded(A_local, opt: Optional[lsrn_options], rank: int, world: in
     _check(lib.lsrn_plan_sharded(ctypes.byref(mat), ctypes.byref(o), ctypes.byref(sh),
                                  ctypes.c_void_p(stream), ctypes.byref(h)), "lsrn_plan_sharded")
     return Plan(h.value, tuple(keep), mat.m, mat.n)
+
+
+def lsrn_solve_batch(problems, opt: Optional[lsrn_options] = None, solver: str = "lsqr",
+                     threads: int = 0, xs=None):
+    """lsrn_solve_batch(): problems is a list of (A, b) with A a dense array or a
+    csr tuple (m, n, row_ptr, col_idx, values).  Returns (xs, infos, statuses)."""
+    lib = load_library()
+    n = len(problems)
+    mats = (lsrn_matrix * max(n, 1))()
+    keep = []
+    if xs is None:
+        xs = []
+        for A, b in problems:
+            cols = A[1] if isinstance(A, tuple) else A.shape[1]
+            xs.append(np.empty(cols) if isinstance(b, np.ndarray) else b.new_empty(cols))
+    for k, (A, b) in enumerate(problems):
+        mats[k] = csr_matrix(*A) if isinstance(A, tuple) else dense_matrix(A, "row")
+        keep.append(A)
+    bptr = (ctypes.c_void_p * max(n, 1))(*[_ptr(b) for _, b in problems])
+    xptr = (ctypes.c_void_p * max(n, 1))(*[_ptr(x) for x in xs])
+    infos = (lsrn_info * max(n, 1))()
+    stat = (ctypes.c_int32 * max(n, 1))()
+    o = opt if opt is not None else default_options()
+    code = {"lsqr": 0, "cs": 1}[solver]
+    st = lib.lsrn_solve_batch(n, ctypes.byref(mats), ctypes.byref(bptr), ctypes.byref(xptr),
+                              ctypes.byref(o), code, threads, ctypes.byref(infos),
+                              ctypes.byref(stat))
+    out_info = []
+    for k in range(n):
+        d = infos[k].as_dict()
+        d["status"] = int(stat[k])
+        out_info.append(d)
+    _check(st, "lsrn_solve_batch", (LSRN_OK, LSRN_ERR_NOT_CONVERGED, LSRN_ERR_DIVERGED))
+    return xs, out_info, [int(stat[k]) for k in range(n)]
+
+
+def lsrn_choose_gamma(m: int, n: int, rank: int = 0, tol: float = 1e-14, solver: str = "lsqr",
+                      c_sketch: float = 0.0, c_qr: float = 0.0, c_svd: float = 0.0,
+                      c_iter: float = 0.0, gamma_min: float = 0.0, gamma_max: float = 0.0):
+    """Returns (gamma, predicted ms) minimising the section 4.3 cost model."""
+    md = lsrn_gamma_model(m=m, n=n, rank=rank, tol=tol, solver={"lsqr": 0, "cs": 1}[solver],
+                          c_sketch=c_sketch, c_qr=c_qr, c_svd=c_svd, c_iter=c_iter,
+                          gamma_min=gamma_min, gamma_max=gamma_max)
+    g, t = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().lsrn_choose_gamma(ctypes.byref(md), ctypes.byref(g), ctypes.byref(t)),
+           "lsrn_choose_gamma")
+    return g.value, t.value
+
+
+def gamma_costs_from_info(info: dict) -> dict:
+    """Per-unit costs of the gamma model from an earlier solve's lsrn_info."""
+    s = max(1, info["s"])
+    its = max(1, info["iterations"] + info["refine_iterations"])
+    return {"c_sketch": info["t_sketch_ms"] / s, "c_qr": info["t_qr_ms"] / s,
+            "c_svd": max(0.0, info["t_precond_ms"] - info["t_qr_ms"]),
+            "c_iter": (info["t_iter_ms"] + info["t_refine_ms"]) / its}
+
+
+def lsrn_plan_set_lambda(plan: Plan, lam: float) -> None:
+    _check(load_library().lsrn_plan_set_lambda(plan.handle, float(lam)), "lsrn_plan_set_lambda")
 
 
 def lsrn_sketch(plan: Plan) -> None:

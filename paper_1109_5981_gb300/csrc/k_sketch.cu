@@ -138,6 +138,24 @@ __global__ void sketch_add_gamma_kernel(double* __restrict__ C, int64_t ldc, int
   }
 }
 
+// C[i, j] = scale * base[i, j] + coef * Gamma[lrow0 + j, i]   (the sketch of a ridge
+// problem from its unaugmented part: G_1 A + lambda G_2, or A G_1 / lambda + G_2)
+__global__ void ridge_combine_kernel(const double* __restrict__ base, double* __restrict__ C,
+                                     int64_t ldc, int64_t S, int64_t Q, double scale,
+                                     uint64_t seed, uint32_t tag, int64_t lrow0, double coef) {
+  const int64_t ng = (S + 3) / 4;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ng * Q) return;
+  const int64_t j = idx / ng, g = idx % ng;
+  const float4 z = normal4(seed, tag, (uint64_t)(lrow0 + j), (uint64_t)g);
+  const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t i = 4 * g + k;
+    if (i < S) C[i * ldc + j] = fma(coef, (double)quantize_g(zz[k]), scale * base[i * ldc + j]);
+  }
+}
+
 __global__ void gamma_block_kernel(uint64_t seed, uint32_t tag, int64_t i0, int64_t j0, int64_t rows,
                                    int64_t cols, double* __restrict__ g, float* __restrict__ z) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,6 +265,17 @@ lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q
   if (tot == 0) return LSRN_OK;
   launch(sketch_add_gamma_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, C, ldc, S, Q, seed, tag,
                                                                           lrow0, coef);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
+lsrn_status launch_ridge_combine(const double* base, double* C, int64_t ldc, int64_t S, int64_t Q,
+                                 double scale, uint64_t seed, uint32_t tag, int64_t lrow0,
+                                 double coef, cudaStream_t st) {
+  const int64_t tot = ((S + 3) / 4) * Q;
+  if (tot == 0) return LSRN_OK;
+  launch(ridge_combine_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, base, C, ldc, S, Q, scale,
+         seed, tag, lrow0, coef);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }

@@ -14,6 +14,7 @@
 //    N = V~ Sigma~^-1 = W_r Sigma_r^-2 (Q x r), also stored transposed.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "lsrn_device.cuh"
 #include "lsrn_internal.h"
@@ -863,6 +864,28 @@ lsrn_status run_precond(Plan* p, bool bf16_check) {
     LSRN_CUDA_TRY(cudaMemcpyAsync(&dmin, p->tmpq, sizeof(double), cudaMemcpyDeviceToHost, st));
     LSRN_CUDA_TRY(cudaStreamSynchronize(st));
     if (!(dmin >= 16.0 * p->bf16_noise)) return kPrecondEscalate;
+  }
+  if (p->opt.precond_mode == LSRN_PRECOND_QR && p->ridge) {
+    // full rank by construction: N = R^-1, no Jacobi sweeps (k_trinv.cu)
+    double* T = nullptr;
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&T, (size_t)64 * Q * sizeof(double), st));
+    const lsrn_status ts = launch_trinv(X, Q, p->Nm, p->NT, T, p->tmpq, st);
+    cudaFreeAsync(T, st);
+    LSRN_TRY(ts);
+    cudaEventRecord(p->ev[9], st);
+    std::vector<double> d((size_t)Q);
+    LSRN_CUDA_TRY(cudaMemcpyAsync(d.data(), p->tmpq, (size_t)Q * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+    std::sort(d.begin(), d.end(), [](double a, double b) { return a > b; });
+    LSRN_CUDA_TRY(cudaMemcpyAsync(p->sig, d.data(), (size_t)Q * sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+    p->rank = Q;
+    p->sigma_max = d.front();
+    p->sigma_min = d.back();
+    p->sweeps = 0;
+    return LSRN_OK;
   }
   // 2. One-sided Jacobi on the rows of R.
   const int64_t QQ = Q * Q;

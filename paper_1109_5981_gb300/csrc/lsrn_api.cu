@@ -1,10 +1,12 @@
 // C ABI of the LSRN library: plan management and the solve entry points.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "lsrn_device.cuh"
@@ -159,6 +161,7 @@ static void release(Plan* p) {
   if (p->stream) {
     for (void* ptr : p->owned) cudaFreeAsync(ptr, p->stream);
     if (p->coefs) cudaFreeAsync(p->coefs, p->stream);
+    if (p->sk_base) cudaFreeAsync(p->sk_base, p->stream);
     if (p->shard.send) cudaFreeAsync(p->shard.send, p->stream);
     if (p->shard.recv) cudaFreeAsync(p->shard.recv, p->stream);
     cudaStreamSynchronize(p->stream);
@@ -184,6 +187,9 @@ static lsrn_status validate_options(const lsrn_options& o) {
   if (o.iter_mode != LSRN_ITER_F64 && o.iter_mode != LSRN_ITER_F32 &&
       o.iter_mode != LSRN_ITER_F32X2)
     return LSRN_ERR_INVALID_ARG;
+  if (o.precond_mode != LSRN_PRECOND_SVD && o.precond_mode != LSRN_PRECOND_QR)
+    return LSRN_ERR_INVALID_ARG;
+  if (o.precond_mode == LSRN_PRECOND_QR && !(o.lambda > 0.0)) return LSRN_ERR_INVALID_ARG;
   return LSRN_OK;
 }
 
@@ -453,13 +459,25 @@ lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* op
   return plan_create(A_local, opt, stream, &sh, out);
 }
 
+// Ridge sketch from the kept unaugmented part: tall, B = [A; lambda I] and
+// A~ = G_1 A + lambda G_2; fat, B = [A / lambda, I_m] and A~ = A G_1 / lambda +
+// G_2 (section 5), G_2 being G's rows that meet the appended block.
+static lsrn_status ridge_sketch(Plan* p) {
+  const int64_t lrow0 = p->shard.long_total > 0 ? p->shard.long_total : p->xrows;
+  return launch_ridge_combine(p->sk_base, p->Xs, p->q, p->s, p->q, p->xscale, p->opt.seed, 0u,
+                              lrow0, p->extra_coef, p->stream);
+}
+
 // The sketch Xs with the given arithmetic (dense: F64, TC_SLICED or BF16; CSR
 // always FP64), plus the ridge rows and, for a shard, the sum over shards.
 static lsrn_status sketch_with(Plan* p, int mode) {
   const uint32_t tag = 0;
+  // A ridge plan sketches X unscaled and keeps that part (sk_base), so that a
+  // new lambda only recombines it with the rows of G that meet lambda I / I_m.
+  const double xs_sk = p->ridge ? 1.0 : p->xscale;
   if (p->csr) {
     mode = LSRN_SKETCH_F64;
-    LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, p->xscale, p->s,
+    LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, xs_sk, p->s,
                                p->opt.seed, tag, p->Xs, p->q, p->stream, p->shard.lbase));
   } else if (mode == LSRN_SKETCH_TC_SLICED || mode == LSRN_SKETCH_BF16) {
     const bool bf = mode == LSRN_SKETCH_BF16;
@@ -475,10 +493,10 @@ static lsrn_status sketch_with(Plan* p, int mode) {
     LSRN_CUDA_TRY(lsrn_malloc_async(&buf, scratch, p->stream));
     LSRN_CUDA_TRY(cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), p->stream));
     lsrn_status st =
-        bf ? launch_sketch_bf16(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed, tag,
+        bf ? launch_sketch_bf16(p->X, p->xrows, p->q, p->ldx, xs_sk, p->s, p->opt.seed, tag,
                                 p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR, p->stream,
                                 &p->gemm_events, p->shard.lbase)
-           : launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed, tag,
+           : launch_sketch_tc(p->X, p->xrows, p->q, p->ldx, xs_sk, p->s, p->opt.seed, tag,
                               p->Xs, p->q, buf, scratch, seg, p->iscal + IC_TCERR, p->stream,
                               &p->gemm_events, p->shard.lbase);
     cudaFreeAsync(buf, p->stream);
@@ -488,18 +506,21 @@ static lsrn_status sketch_with(Plan* p, int mode) {
     const size_t scratch = sketch_f64_scratch_bytes(p->xrows, p->q, p->s);
     double* buf = nullptr;
     if (scratch) LSRN_CUDA_TRY(lsrn_malloc_async((void**)&buf, scratch, p->stream));
-    lsrn_status st = launch_sketch_f64(p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed,
+    lsrn_status st = launch_sketch_f64(p->X, p->xrows, p->q, p->ldx, xs_sk, p->s, p->opt.seed,
                                        tag, p->Xs, p->q, buf, scratch, p->stream, p->shard.lbase);
     if (buf) cudaFreeAsync(buf, p->stream);
     LSRN_TRY(st);
   }
-  if (p->ridge && p->extra_rows > 0)   // the rows lambda I (or I_m) follow the last row of X
-    LSRN_TRY(launch_sketch_add_gamma(p->Xs, p->q, p->s, p->q, p->opt.seed, tag,
-                                     p->shard.long_total > 0 ? p->shard.long_total : p->xrows,
-                                     p->extra_coef,
-                                     p->stream));
   LSRN_TRY(shard_sum(p, p->Xs, p->s * p->q));   // A~ = sum over shards of G_p A_p
   p->sketch_used = mode;
+  if (p->ridge) {
+    if (p->sk_base == nullptr)
+      LSRN_CUDA_TRY(lsrn_malloc_async((void**)&p->sk_base, (size_t)p->s * p->q * sizeof(double),
+                                      p->stream));
+    LSRN_CUDA_TRY(cudaMemcpyAsync(p->sk_base, p->Xs, (size_t)p->s * p->q * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, p->stream));
+    LSRN_TRY(ridge_sketch(p));
+  }
   return LSRN_OK;
 }
 
@@ -528,6 +549,26 @@ lsrn_status lsrn_sketch(lsrn_plan_t p) {
   LSRN_TRY(sketch_with(p, mode));
   cudaEventRecord(p->ev[1], p->stream);
   p->state = 1;   // a new sketch invalidates an earlier preconditioner
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_plan_set_lambda(lsrn_plan_t p, double lambda) {
+  if (p == nullptr || !(lambda > 0.0) || !std::isfinite(lambda)) return LSRN_ERR_INVALID_ARG;
+  if (!p->ridge) return LSRN_ERR_INVALID_ARG;
+  cudaSetDevice(p->device);
+  p->lam = lambda;
+  p->opt.lambda = lambda;
+  p->extra_coef = p->tall ? lambda : 1.0;
+  p->xscale = p->tall ? 1.0 : 1.0 / lambda;
+  if (p->sk_base == nullptr) {   // not sketched yet: the next sketch uses the new lambda
+    p->state = 0;
+    return LSRN_OK;
+  }
+  cudaEventRecord(p->ev[0], p->stream);
+  LSRN_TRY(ridge_sketch(p));
+  cudaEventRecord(p->ev[1], p->stream);
+  p->bound_widen = 0.0;
+  p->state = 1;   // the preconditioner must be recomputed
   return LSRN_OK;
 }
 
@@ -686,6 +727,205 @@ lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* 
     if (thm45_bounds(p, &sL, &sU) != LSRN_OK) return LSRN_ERR_INVALID_ARG;
   }
   return solve_common(p, b, x, info, true);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Run body(i) for i in [0, n) on `threads` host threads, each bound to `dev`.
+template <class F>
+void parallel_for(int n, int threads, int dev, F body) {
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) body(i);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+lsrn_status lsrn_choose_gamma(const lsrn_gamma_model* md, double* gamma, double* predicted_ms) {
+  if (md == nullptr || md->m < 1 || md->n < 1) return LSRN_ERR_INVALID_ARG;
+  if (!(md->c_sketch >= 0.0) || !(md->c_qr >= 0.0) || !(md->c_svd >= 0.0) || !(md->c_iter >= 0.0))
+    return LSRN_ERR_INVALID_ARG;
+  const double q = (double)std::min(md->m, md->n);
+  const double r = md->rank > 0 ? (double)std::min<int64_t>(md->rank, std::min(md->m, md->n)) : q;
+  const double eps = md->tol > 0.0 ? md->tol : 1e-14;
+  const double g0 = md->gamma_min > 0.0 ? md->gamma_min : 1.05;
+  const double g1 = md->gamma_max > 0.0 ? md->gamma_max : 8.0;
+  if (!(g1 >= g0) || !(g0 > 1.0)) return LSRN_ERR_INVALID_ARG;
+  double best_t = INFINITY, best_g = 0.0;
+  const int steps = (int)std::floor((g1 - g0) / 0.01 + 1e-9);
+  for (int k = 0; k <= steps; ++k) {
+    const double g = g0 + 0.01 * k;
+    const double s = std::ceil(g * q);
+    if (!(s > r) || !(s > q)) continue;
+    double iters;
+    if (md->solver == 1) {
+      const double a = 1.0 / std::sqrt(s);
+      const double lo = (1.0 - a) * std::sqrt(s) - std::sqrt(r);
+      if (!(lo > 0.0)) continue;
+      const double sU = 1.0 / lo, sL = 1.0 / ((1.0 + a) * std::sqrt(s) + std::sqrt(r));
+      const double rho = (sU - sL) / (sU + sL);
+      iters = std::ceil((std::log(eps) - std::log(2.0)) / std::log(rho)) + 1.0;
+    } else {
+      iters = std::ceil((std::log(eps) - std::log(2.0)) / std::log(std::sqrt(r / s)));
+    }
+    const double t = (md->c_sketch + md->c_qr) * s + md->c_svd + md->c_iter * iters;
+    if (t < best_t) {
+      best_t = t;
+      best_g = g;
+    }
+  }
+  if (!(best_g > 0.0)) return LSRN_ERR_UNSUPPORTED;
+  if (gamma) *gamma = best_g;
+  if (predicted_ms) *predicted_ms = best_t;
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* const* b,
+                             double* const* x, const lsrn_options* opt, int32_t solver,
+                             int32_t threads, lsrn_info* info, int32_t* status) {
+  if (count < 0 || threads < 0 || (solver != 0 && solver != 1)) return LSRN_ERR_INVALID_ARG;
+  if (count == 0) return LSRN_OK;
+  if (A == nullptr || b == nullptr || x == nullptr) return LSRN_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return LSRN_ERR_CUDA;
+  }
+  const int nth = std::max(1, std::min<int>(threads > 0 ? threads : 8, count));
+  std::vector<lsrn_plan_t> plans((size_t)count, nullptr);
+  std::vector<lsrn_status> st((size_t)count, LSRN_OK);
+  // 1. plans and sketches, each problem on its own stream
+  parallel_for(count, nth, dev, [&](int i) {
+    st[i] = lsrn_plan(&A[i], opt, nullptr, &plans[i]);
+    if (st[i] == LSRN_OK) st[i] = lsrn_sketch(plans[i]);
+  });
+  // 2. preconditioners: one launch for the small dense-sketch problems, largest first
+  std::vector<int> batched, single;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] != LSRN_OK) continue;
+    Plan* p = plans[i];
+    const bool ok_mode = p->sketch_used == LSRN_SKETCH_F64 || p->sketch_used == LSRN_SKETCH_TC_SLICED;
+    const bool ok_mode2 = p->opt.sketch_mode != LSRN_SKETCH_AUTO &&
+                          p->opt.sketch_mode != LSRN_SKETCH_BF16 &&
+                          p->opt.precond_mode == LSRN_PRECOND_SVD;
+    if (ok_mode && ok_mode2 && batch_precond_applies(p->q)) batched.push_back(i);
+    else single.push_back(i);
+  }
+  std::sort(batched.begin(), batched.end(),
+            [&](int a, int c) { return plans[a]->q > plans[c]->q; });
+  if (!batched.empty()) {
+    const int nb = (int)batched.size();
+    cudaStream_t bs = nullptr;
+    lsrn_status bst = LSRN_OK;
+    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) bst = LSRN_ERR_CUDA;
+    std::vector<BatchPrecond> hp((size_t)nb);
+    BatchPrecond* dp = nullptr;
+    int* dout_i = nullptr;
+    double* dout_d = nullptr;
+    int* dnext = nullptr;
+    if (bst == LSRN_OK) {
+      // every sketch must be complete (and its bounded waits clean) first
+      for (int i : batched) {
+        Plan* p = plans[i];
+        if (cudaStreamSynchronize(p->stream) != cudaSuccess) st[i] = LSRN_ERR_CUDA;
+        else if (check_tc_error(p) != LSRN_OK) st[i] = LSRN_ERR_TIMEOUT;
+      }
+      if (lsrn_malloc_async((void**)&dp, sizeof(BatchPrecond) * nb, bs) != cudaSuccess ||
+          lsrn_malloc_async((void**)&dout_i, sizeof(int) * 2 * nb, bs) != cudaSuccess ||
+          lsrn_malloc_async((void**)&dout_d, sizeof(double) * 2 * nb, bs) != cudaSuccess ||
+          lsrn_malloc_async((void**)&dnext, sizeof(int), bs) != cudaSuccess) {
+        cudaGetLastError();
+        bst = LSRN_ERR_OOM;
+      }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float batch_ms = 0.f;
+    if (bst == LSRN_OK) {
+      for (int k = 0; k < nb; ++k) {
+        Plan* p = plans[batched[k]];
+        const double rcond = p->opt.rcond >= 0.0 ? p->opt.rcond : (double)std::max(p->s, p->q) * 0x1p-53;
+        hp[k] = BatchPrecond{p->Xs, p->Wj, p->sig, p->perm, p->Nm, p->NT, p->s, p->q, rcond,
+                             dout_i + 2 * k, dout_d + 2 * k};
+      }
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      if (cudaMemcpyAsync(dp, hp.data(), sizeof(BatchPrecond) * nb, cudaMemcpyHostToDevice, bs) !=
+          cudaSuccess)
+        bst = LSRN_ERR_CUDA;
+      cudaEventRecord(e0, bs);
+      if (bst == LSRN_OK) bst = launch_batched_precond(dp, nb, dnext, bs);
+      cudaEventRecord(e1, bs);
+    }
+    std::vector<int> oi((size_t)2 * nb);
+    std::vector<double> od((size_t)2 * nb);
+    if (bst == LSRN_OK &&
+        (cudaMemcpyAsync(oi.data(), dout_i, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, bs) != cudaSuccess ||
+         cudaMemcpyAsync(od.data(), dout_d, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, bs) != cudaSuccess ||
+         cudaStreamSynchronize(bs) != cudaSuccess))
+      bst = LSRN_ERR_CUDA;
+    if (e0 && e1 && bst == LSRN_OK) cudaEventElapsedTime(&batch_ms, e0, e1);
+    for (int k = 0; k < nb; ++k) {
+      const int i = batched[k];
+      if (st[i] != LSRN_OK) continue;
+      if (bst != LSRN_OK) {
+        st[i] = bst;
+        continue;
+      }
+      Plan* p = plans[i];
+      p->rank = oi[2 * k];
+      p->sweeps = oi[2 * k + 1];
+      p->sigma_max = od[2 * k];
+      p->sigma_min = od[2 * k + 1];
+      if (p->sweeps > 40) {
+        st[i] = LSRN_ERR_NOT_CONVERGED;
+        continue;
+      }
+      cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
+      p->t_precond_ms = batch_ms;   // the whole batch's launch
+      p->t_qr_ms = 0.f;
+      p->t_jacobi_ms = 0.f;
+      p->state = 2;
+    }
+    if (dp) cudaFreeAsync(dp, bs);
+    if (dout_i) cudaFreeAsync(dout_i, bs);
+    if (dout_d) cudaFreeAsync(dout_d, bs);
+    if (dnext) cudaFreeAsync(dnext, bs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (bs) {
+      cudaStreamSynchronize(bs);
+      cudaStreamDestroy(bs);
+    }
+  }
+  // 3. the other preconditioners and all iterations, overlapping across problems
+  parallel_for(count, nth, dev, [&](int i) {
+    if (st[i] == LSRN_OK) {
+      lsrn_info inf;
+      st[i] = solver == 1 ? lsrn_solve_cs(plans[i], b[i], x[i], &inf)
+                          : lsrn_solve_lsqr(plans[i], b[i], x[i], &inf);
+      if (info) info[i] = inf;
+    } else if (info) {
+      memset(&info[i], 0, sizeof(lsrn_info));
+      info[i].status = st[i];
+    }
+    if (plans[i]) lsrn_plan_destroy(plans[i]);
+  });
+  lsrn_status first = LSRN_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = st[i];
+    if (first == LSRN_OK && st[i] != LSRN_OK) first = st[i];
+  }
+  return first;
 }
 
 lsrn_status lsrn_plan_destroy(lsrn_plan_t p) {

@@ -170,6 +170,7 @@ struct Plan {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;   // fused passes of the main sweep
   bool time_passes = false;
   float t_sketch_ms = 0, t_precond_ms = 0, t_sketch_gemm_ms = 0, t_qr_ms = 0, t_jacobi_ms = 0;
+  double* sk_base = nullptr;           // ridge: the unaugmented sketch G_1 A / A G_1 (s x q)
   int sketch_used = LSRN_SKETCH_F64;   // sketch arithmetic that produced Xs
   bool sketch_escalated = false;       // AUTO replaced the BF16 sketch by the exact one
   double bf16_noise = 0.0;             // 2^-8 ||A~||_F / sqrt(q) of a BF16 sketch
@@ -184,6 +185,26 @@ struct Plan {
 lsrn_status shard_sum(Plan* p, double* buf, int64_t count);
 // The same for a double-double vector (hi, lo), summed in double-double.
 lsrn_status shard_sum_dd(Plan* p, double* hi, double* lo, int64_t count);
+
+// ---- batched preconditioner (one launch for many problems) -----------------
+struct BatchPrecond {
+  double* X;      // S x Q sketch (factored in place)
+  double* W;      // Q x Q Jacobi workspace
+  double* sig;    // Q singular values (descending)
+  int* perm;      // Q
+  double* N;      // Q x r
+  double* NT;     // r x Q
+  int64_t S, Q;
+  double rcond;
+  int* out;       // [rank, sweeps] (sweeps > 40: not converged)
+  double* dout;   // [sigma_1, sigma_r]
+};
+bool batch_precond_applies(int64_t Q);
+// N = R^-1 (q x q) and NT from the upper triangle of the factored sketch Xs; T scratch 64 q doubles
+lsrn_status launch_trinv(const double* Xs, int64_t q, double* N, double* NT, double* T,
+                         double* diag, cudaStream_t st);
+lsrn_status launch_batched_precond(const BatchPrecond* dev_probs, int count, int* dev_next,
+                                   cudaStream_t st);
 
 // ---- kernels (launchers) -------------------------------------------------
 // sketch: C (S x Q, ldc) = xscale * Gamma[lrow0 : lrow0+L]^T X   (X: L x Q row-major)
@@ -231,6 +252,10 @@ lsrn_status launch_sketch_bf16(const double* X, int64_t L, int64_t Q, int64_t ld
 // C[i, j] = scale_c * C[i, j] + coef * Gamma[lrow0 + j, i], i < S, j < Q
 lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q, uint64_t seed,
                                     uint32_t tag, int64_t lrow0, double coef, cudaStream_t st);
+// C = scale * base + coef * Gamma[lrow0 + j, i] (ridge sketch from its unaugmented part)
+lsrn_status launch_ridge_combine(const double* base, double* C, int64_t ldc, int64_t S, int64_t Q,
+                                 double scale, uint64_t seed, uint32_t tag, int64_t lrow0,
+                                 double coef, cudaStream_t st);
 lsrn_status launch_gamma_block(uint64_t seed, uint32_t tag, int64_t i0, int64_t j0, int64_t rows,
                                int64_t cols, double* g, float* z, cudaStream_t st);
 // CSR sketch: C (S x Q) = xscale * Gamma^T X with X given by its columns (CSC of X)

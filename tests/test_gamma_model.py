@@ -1,0 +1,81 @@
+"""Choice of the oversampling factor (lsrn_choose_gamma, section 4.3's cost
+model).  Host arithmetic only, so these run without a GPU.  The model is
+evaluated here independently from the paper's formulas (Theorem 4.6's LSQR
+bound, Algorithm 3's step count with Theorem 4.5's bounds) by brute force over
+the same grid; limiting cases fix the answer at the ends of the range; and
+with the per-unit costs of the dense 10^6 x 2000 benchmark on this GPU the
+optimum falls in the paper's empirical range 1.6 - 2.5 (section 6.2)."""
+import math
+
+import numpy as np
+import pytest
+
+L = pytest.importorskip("paper_1109_5981_gb300")
+
+
+def _iters(solver, s, r, eps):
+    if solver == "cs":
+        a = 1 / math.sqrt(s)
+        lo = (1 - a) * math.sqrt(s) - math.sqrt(r)
+        if lo <= 0:
+            return None
+        sU, sL = 1 / lo, 1 / ((1 + a) * math.sqrt(s) + math.sqrt(r))
+        return math.ceil((math.log(eps) - math.log(2)) / math.log((sU - sL) / (sU + sL))) + 1
+    return math.ceil((math.log(eps) - math.log(2)) / math.log(math.sqrt(r / s)))
+
+
+def _brute(m, n, r, eps, solver, cs, cq, cv, ci, g0=1.05, g1=8.0):
+    q = min(m, n)
+    best = (math.inf, None)
+    for k in range(int(math.floor((g1 - g0) / 0.01 + 1e-9)) + 1):
+        g = g0 + 0.01 * k
+        s = math.ceil(g * q)
+        if s <= r or s <= q:
+            continue
+        it = _iters(solver, s, r, eps)
+        if it is None:
+            continue
+        t = (cs + cq) * s + cv + ci * it
+        if t < best[0]:
+            best = (t, g)
+    return best[1], best[0]
+
+
+@pytest.mark.parametrize("solver", ["lsqr", "cs"])
+@pytest.mark.parametrize("m,n,r,costs", [
+    (1_000_000, 2000, 1800, (0.1, 0.0325, 409.0, 6.3)),
+    (10_000, 1_000_000, 10_000, (0.08, 0.5, 100000.0, 2.0)),
+    (2000, 100, 80, (0.001, 0.002, 8.0, 0.09))])
+def test_matches_the_model_by_brute_force(solver, m, n, r, costs):
+    g, t = L.lsrn_choose_gamma(m, n, r, 1e-14, solver, *costs)
+    gb, tb = _brute(m, n, r, 1e-14, solver, *costs)
+    assert abs(g - gb) < 1e-9 and math.isclose(t, tb, rel_tol=1e-12)
+
+
+def test_limiting_cases():
+    # free iterations: the least oversampling wins; free sketch/QR: the most
+    g, _ = L.lsrn_choose_gamma(10_000, 100, 100, 1e-14, "lsqr", 1.0, 1.0, 5.0, 0.0)
+    assert g == pytest.approx(1.05)
+    g, _ = L.lsrn_choose_gamma(10_000, 100, 100, 1e-14, "lsqr", 0.0, 0.0, 5.0, 1.0,
+                               gamma_max=4.0)
+    assert g > 3.9
+
+
+def test_benchmark_costs_give_the_papers_range():
+    # per-unit costs of the 10^6 x 2000, rank 1800 solve on GB300 (sketch 402 ms and QR 130 ms
+    # at s = 4000, Jacobi 409 ms, ~6.3 ms per iteration)
+    for solver in ("lsqr", "cs"):
+        g, _ = L.lsrn_choose_gamma(1_000_000, 2000, 1800, 1e-14, solver, 0.1005, 0.0325, 409.0, 6.3)
+        assert 1.6 <= g <= 2.5
+
+
+def test_invalid_models():
+    with pytest.raises(L.LsrnError) as e:
+        L.lsrn_choose_gamma(0, 10)
+    assert e.value.status == L.LSRN_ERR_INVALID_ARG
+    with pytest.raises(L.LsrnError) as e:
+        L.lsrn_choose_gamma(100, 10, c_iter=-1.0)
+    assert e.value.status == L.LSRN_ERR_INVALID_ARG
+    with pytest.raises(L.LsrnError) as e:     # CS needs sqrt(s) - 1 > sqrt(r): not for s <= 1060
+        L.lsrn_choose_gamma(1000, 1000, 1000, 1e-14, "cs", 1, 1, 1, 1, gamma_min=1.05, gamma_max=1.06)
+    assert e.value.status == L.LSRN_ERR_UNSUPPORTED

@@ -108,13 +108,15 @@ def test_sparse_fat_ridge_full_size(c3):
 
 def test_sparse_fat_ridge_full_size_f32_values():
     """The same 10^4 x 10^6 shape with FP32 values (the oracle uses the rounded
-    values): LSQR against the ridge closed form."""
+    values), with the QR preconditioner N = R^-1 of the full-rank augmented
+    matrix: LSQR against the ridge closed form."""
     import scipy.sparse as sp
     A, b = W.c3_problem(seed=1, dtype=np.float32)
     lam = 1e-3
     csr = (A.m, A.n, torch.from_numpy(A.row_ptr).to("cuda"), torch.from_numpy(A.col_idx).to("cuda"),
            torch.from_numpy(A.values).to("cuda"))
-    plan = L.lsrn_plan(None, L.default_options(seed=4, lambda_=lam), csr=csr)
+    plan = L.lsrn_plan(None, L.default_options(seed=4, lambda_=lam, precond_mode=L.LSRN_PRECOND_QR),
+                       csr=csr)
     try:
         x, info = L.lsrn_solve_lsqr(plan, torch.from_numpy(b).to("cuda"))
     finally:
