@@ -70,14 +70,18 @@ def parse(argv=None):
                          "strong scaling); replica = an independent problem per rank (weak)")
     ap.add_argument("--single-limit", type=int, default=512,
                     help="batch workload: problems solved one at a time for the comparison lines")
+    ap.add_argument("--precond", default="qr", choices=["qr", "svd"],
+                    help="c3 workload: N = R^-1 (full-rank ridge) or the SVD preconditioner")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "serving", "c1", "sketch", "batch"],
+                    choices=["dense", "serving", "c1", "sketch", "batch", "c3"],
                     help="dense: the 1e6 x 2000 solve; serving: a Poisson stream of mixed-size "
                          "requests through lsrn_submit/lsrn_poll; c1: latency of the 2000 x 100 "
                          "rank-80 FP64 solve")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: all at once)")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--pool", type=int, default=96,
+                    help="serving: distinct problems the request stream cycles through")
     return ap.parse_args(argv)
 
 
@@ -307,8 +311,33 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # our implementation                                                           #
 # --------------------------------------------------------------------------- #
+def _ridge_weights(sigma: np.ndarray, lam: float) -> np.ndarray:
+    """sigma / (sigma^2 + lam^2): x*_lam = V diag(.) U^T b for A = U diag(sigma) V^T (section 5)."""
+    return sigma / (sigma * sigma + lam * lam)
+
+
+def _csr_reference(C, b: np.ndarray, lam: float) -> np.ndarray:
+    """Min-length (lam = 0) or Tikhonov solution of a full-rank sprandn matrix from the
+    normal equations of its short side (well conditioned, so FP64 Cholesky is exact to
+    ~1e-15): tall x = (A^T A + lam^2 I)^-1 A^T b, fat x = A^T (A A^T + lam^2 I)^-1 b."""
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    A = sp.csr_matrix((C.values.astype(np.float64), C.col_idx, C.row_ptr), shape=(C.m, C.n))
+    if C.m >= C.n:
+        K = (A.T @ A).toarray() + lam * lam * np.eye(C.n)
+        return sla.cho_solve(sla.cho_factor(K), A.T @ b)
+    K = (A @ A.T).toarray() + lam * lam * np.eye(C.m)
+    return A.T @ sla.cho_solve(sla.cho_factor(K), b)
+
+
 def run_serving(args):
-    """Mixed-size requests through the server: solves/s and p50/p99 latency."""
+    """A Poisson stream of solve requests through the server (lsrn_submit /
+    lsrn_poll): 80% dense problems drawn as in the batched configuration, 20%
+    sprandn-like CSR (density 1e-3, short side 32-2000, long side 1e5-2e6),
+    lambda in {0, 1e-4, 1e-2}.  A pool of distinct problems is cycled through;
+    every result is checked against its reference (planted factors for dense
+    problems, the short-side normal equations for CSR).  Mixed precision with
+    the preconditioners of in-flight requests batched, against FP64 plain."""
     import torch
     import paper_1109_5981_gb300 as L
     import workloads as W
@@ -316,80 +345,116 @@ def run_serving(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = "cuda"
     rng = np.random.Generator(np.random.PCG64(11))
-    prepared = []
-    for P, tall in W.serving_mix(args.requests, seed=7 + rank, device=dev):
-        if tall:
-            A, b = P.A, P.b
-            bn = b.cpu().numpy()
-            xstar = P.apply_V(P.apply_Ut(bn) / P.sigma)        # planted x*
+    pool_n = max(1, min(args.requests, args.pool))
+    pool = []
+    for r in W.serving_requests(pool_n, seed=7, device=dev):
+        lam = r["lam"]
+        if r["kind"] == "dense":
+            P = r["P"]
+            w = _ridge_weights(P.sigma, lam)
+            if r["tall"]:
+                A, b = P.A, P.b
+                xs = P.apply_V(P.apply_Ut(b.cpu().numpy()) * w)
+            else:
+                A = P.A.T.contiguous()
+                bn = rng.standard_normal(A.shape[0])
+                b = torch.from_numpy(bn).to(dev)
+                xs = P.apply_U(P.apply_Vt(bn) * w)
+            pool.append(dict(A=A, csr=None, b=b, lam=lam, xstar=xs, n=A.shape[1], kind="dense"))
         else:
-            A = P.A.T.contiguous()                               # stored short x long
-            bn = rng.standard_normal(A.shape[0])
-            b = torch.from_numpy(bn).to(dev)
-            xstar = P.apply_U(P.apply_Vt(bn) / P.sigma)
-        prepared.append((A, b, xstar))
-    mode = {"x2": L.LSRN_ITER_F32, "f32": L.LSRN_ITER_F32, "f64": L.LSRN_ITER_F64}[args.iter]
-    opts = L.default_options(seed=99, iter_mode=mode,
-                             sketch_mode=L.LSRN_SKETCH_TC_SLICED if args.sketch == "tc"
-                             else L.LSRN_SKETCH_F64)
+            C = r["csr"]
+            csr = (C.m, C.n, torch.from_numpy(C.row_ptr).to(dev), torch.from_numpy(C.col_idx).to(dev),
+                   torch.from_numpy(C.values).to(dev))
+            pool.append(dict(A=None, csr=csr, C=C, bnp=r["b"], b=torch.from_numpy(r["b"]).to(dev),
+                             lam=lam, xstar=None, n=C.n, kind="csr"))
     solver = 1 if args.solver == "cs" else 0
-    srv = L.lsrn_server_create(120 << 30, max_slots=args.slots)
-    try:
-        for A, b, _ in prepared[:2]:                              # warm-up
-            t = L.lsrn_submit(srv, A, b, opts, solver)
-            while L.lsrn_poll(srv, t, None)[0] == L.LSRN_PENDING:
-                time.sleep(0.001)
-        gaps = (rng.exponential(1.0 / args.rate, len(prepared)) if args.rate > 0
-                else np.zeros(len(prepared)))
-        due = np.cumsum(gaps)
-        xs = [np.zeros(A.shape[1]) for A, _, _ in prepared]
-        t_sub = np.zeros(len(prepared))
-        t_done = np.zeros(len(prepared))
-        tickets = {}
-        statuses = {}
-        nxt = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        while len(statuses) < len(prepared):
-            now = time.perf_counter() - t0
-            while nxt < len(prepared) and due[nxt] <= now:
-                A, b, _ = prepared[nxt]
-                t_sub[nxt] = time.perf_counter() - t0
-                tickets[L.lsrn_submit(srv, A, b, opts, solver)] = nxt
-                nxt += 1
-            progressed = False
-            for tk, k in list(tickets.items()):
-                st, _ = L.lsrn_poll(srv, tk, xs[k])
-                if st != L.LSRN_PENDING:
-                    t_done[k] = time.perf_counter() - t0
-                    statuses[k] = st
-                    del tickets[tk]
-                    progressed = True
-            if not progressed:
-                time.sleep(0.0002)
-        elapsed = float(t_done.max())
-    finally:
-        L.lsrn_server_destroy(srv)
-    lat = (t_done - t_sub) * 1e3
-    errs = np.array([rel_error(x, xs_) for x, (_, _, xs_) in zip(xs, prepared)])
-    ok = np.array([statuses[k] == L.LSRN_OK for k in range(len(prepared))])
-    good = int(np.sum(ok & (errs <= 1e-10)))
+    order = [k % pool_n for k in range(args.requests)]
+
+    def stream(mode: str):
+        mixed = mode == "mixed"
+        srv = L.lsrn_server_create(120 << 30, max_slots=args.slots)
+        try:
+            L.lsrn_server_set_batching(srv, 512 if mixed else 0)
+            opts = [L.default_options(seed=99, lambda_=p["lam"],
+                                      sketch_mode=L.LSRN_SKETCH_TC_SLICED if mixed else L.LSRN_SKETCH_F64,
+                                      iter_mode=L.LSRN_ITER_F32 if mixed else L.LSRN_ITER_F64)
+                    for p in pool]
+
+            def submit(k):
+                p = pool[k]
+                return L.lsrn_submit(srv, p["A"], p["b"], opts[k], solver, csr=p["csr"])
+            for k in range(min(2, pool_n)):                        # warm-up
+                t = submit(k)
+                while L.lsrn_poll(srv, t, None)[0] == L.LSRN_PENDING:
+                    time.sleep(0.001)
+            b0, r0 = L.lsrn_server_stats(srv)
+            gaps = (rng.exponential(1.0 / args.rate, len(order)) if args.rate > 0
+                    else np.zeros(len(order)))
+            due = np.cumsum(gaps)
+            xs = [np.zeros(pool[k]["n"]) for k in order]
+            t_sub = np.zeros(len(order))
+            t_done = np.zeros(len(order))
+            tickets, statuses = {}, {}
+            nxt = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while len(statuses) < len(order):
+                now = time.perf_counter() - t0
+                while nxt < len(order) and due[nxt] <= now:
+                    t_sub[nxt] = time.perf_counter() - t0
+                    tickets[submit(order[nxt])] = nxt
+                    nxt += 1
+                progressed = False
+                for tk, k in list(tickets.items()):
+                    st, _ = L.lsrn_poll(srv, tk, xs[k])
+                    if st != L.LSRN_PENDING:
+                        t_done[k] = time.perf_counter() - t0
+                        statuses[k] = st
+                        del tickets[tk]
+                        progressed = True
+                if not progressed:
+                    time.sleep(0.0002)
+            elapsed = float(t_done.max())
+            b1, r1 = L.lsrn_server_stats(srv)
+        finally:
+            L.lsrn_server_destroy(srv)
+        return dict(xs=xs, lat=(t_done - t_sub) * 1e3, st=statuses, elapsed=elapsed,
+                    batches=b1 - b0, batched=r1 - r0)
+
+    runs = {m: stream(m) for m in ("mixed", "fp64")}
+    for p in pool:                                                   # references, after the timed runs
+        if p["kind"] == "csr":
+            p["xstar"] = _csr_reference(p["C"], p["bnp"], p["lam"])
+
+    def summary(res):
+        errs = np.array([rel_error(x, pool[k]["xstar"]) for x, k in zip(res["xs"], order)])
+        ok = np.array([res["st"][i] == L.LSRN_OK for i in range(len(order))])
+        good = int(np.sum(ok & (errs <= 1e-10)))
+        lat = res["lat"]
+        return {"value": good / res["elapsed"], "solved_within_1e-10": good, "elapsed_s": res["elapsed"],
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "max": float(lat.max())},
+                "rel_err": {"max": float(errs.max()), "median": float(np.median(errs))},
+                "batched_precond_launches": res["batches"], "batched_requests": res["batched"]}
+    mix, f64 = summary(runs["mixed"]), summary(runs["fp64"])
     line = {
-        "metric": "LS solves/s at <=1e-10 rel err (serving mix through lsrn_submit/lsrn_poll)",
-        "value": good / elapsed, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-        "requests": len(prepared), "solved_within_1e-10": good, "elapsed_s": elapsed,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
-        "rel_err": {"max": float(errs.max()), "median": float(np.median(errs))},
-        "dtype": {"x2": "f32 passes (tall), f64 elsewhere", "f32": "f32 passes (tall), f64 elsewhere",
-                  "f64": "f64"}[args.iter],
+        "metric": "LS solves/s at <=1e-10 rel err: mixed batched vs FP64 plain; p50/p99 latency "
+                  "(serving mix through lsrn_submit/lsrn_poll)",
+        "value": mix["value"], "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+        "requests": len(order), "distinct_problems": pool_n,
+        "mixed": mix, "fp64_plain": f64, "mixed_over_fp64_plain": mix["value"] / max(f64["value"], 1e-30),
+        "latency_ms": mix["latency_ms"],
+        "dtype": "mixed: bf16 exact-slice sketch, f32 passes (dense tall), f64 SVD and refinement; "
+                 "CSR: f64 sketch and passes",
         "data": "synthetic (seeded generator, no dataset)",
-        "config": {"workload": f"{len(prepared)} requests: m log-uniform [5e3, 2e5], n log-uniform "
-                               "[32, 512], 70% tall / 30% fat, rank 0.8-1.0 min(m, n), cond 1e2-1e6, "
-                               "noise 1e-4", "arrivals": (f"Poisson {args.rate}/s" if args.rate > 0
-                                                          else "all at t = 0"),
-                   "slots": args.slots, "hbm_budget_gb": 120, "sketch": args.sketch,
-                   "solver": args.solver},
+        "config": {"workload": f"{len(order)} requests cycling over {pool_n} problems: 80% dense "
+                               "(m log-uniform [5e3, 2e5], n log-uniform [32, 512], 70% tall, rank "
+                               "0.8-1.0 min(m, n), cond 1e2-1e6), 20% CSR (density 1e-3, short side "
+                               "[32, 2000], long side [1e5, 2e6]); lambda in {0, 1e-4, 1e-2}",
+                   "arrivals": (f"Poisson {args.rate}/s" if args.rate > 0 else "all at t = 0"),
+                   "slots": args.slots, "hbm_budget_gb": 120, "solver": args.solver,
+                   "batching": "mixed: preconditioners of in-flight requests packed into shared "
+                               "launches; fp64: per request"},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -692,12 +757,93 @@ def run_batch(args):
                                 "seconds": t_mixed1},
         "batched_over_fp64_plain": (ok_b / t_batch) / max(ok64 / t_plain, 1e-30),
         "batched_precond_ms": float(np.median([i["t_precond_ms"] for i in infos])),
+        "per_problem_sums_ms": {k: float(np.sum([i[k] for i in infos]))
+                                for k in ("t_sketch_ms", "t_iter_ms", "t_refine_ms")},
+        "iterations": {"main_median": float(np.median([i["iterations"] for i in infos])),
+                       "refine_median": float(np.median([i["refine_iterations"] for i in infos])),
+                       "refine_steps_median": float(np.median([i["refine_steps"] for i in infos]))},
         "dtype": "mixed: bf16 exact-slice sketch, f32 passes (tall) with f64 refinement, f64 SVD",
         "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": f"{count} problems: m log-uniform [5e3, 2e5], n log-uniform [32, 512], "
                                "70% tall / 30% fat, rank 0.8-1.0 min(m, n), cond 1e2-1e6, noise 1e-4",
                    "solver": solver, "threads": 8},
         "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_c3(args):
+    """The sparse under-determined Tikhonov problem: A 10^4 x 10^6 CSR with 2000
+    uniform-random columns per row, N(0,1) values, b ~ N(0,1), lambda = 1e-3
+    (Algorithm 2 on [A / lambda, I_m], s = 2 * 10^4, G drawn on the fly).  One
+    step = plan + sketch + preconditioner + LSQR + refinement; x is checked
+    after the timed region against the ridge closed form
+    A^T (A A^T + lambda^2 I)^-1 b (sparse product and FP64 Cholesky)."""
+    import torch
+    import paper_1109_5981_gb300 as L
+    import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.load_library()
+    A, b = W.c3_problem(seed=0)
+    lam = 1e-3
+    csr = (A.m, A.n, torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col_idx).cuda(),
+           torch.from_numpy(A.values).cuda())
+    bt = torch.from_numpy(b).cuda()
+    x = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    mode = L.LSRN_PRECOND_QR if args.precond == "qr" else L.LSRN_PRECOND_SVD
+    opt = L.default_options(seed=3, lambda_=lam, precond_mode=mode)
+    solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
+
+    def step():
+        plan = L.lsrn_plan(None, opt, csr=csr)
+        try:
+            _, info = solve_fn(plan, bt, x)
+        finally:
+            plan.close()
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = L.kernel_launches()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    infos = []
+    for k in range(args.steps):
+        infos.append(step())
+        ev[k + 1].record()
+    torch.cuda.synchronize()
+    elapsed = ev[0].elapsed_time(ev[-1])
+    launches = L.kernel_launches() - launches0
+    clk = clocks.stop()
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    As = sp.csr_matrix((A.values, A.col_idx, A.row_ptr), shape=(A.m, A.n))
+    K = (As @ As.T).toarray() + lam * lam * np.eye(A.m)
+    ref = As.T @ sla.cho_solve(sla.cho_factor(K), b)
+    err = rel_error(x.cpu().numpy(), ref)
+    info = infos[-1]
+    mean = lambda k: float(np.mean([i[k] for i in infos]))
+    line = {
+        "metric": "LS solves/s at <=1e-10 rel err (sparse fat 1e4x1e6 CSR, 2000 nnz/row, ridge 1e-3)",
+        "value": args.steps / (elapsed * 1e-3), "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps,
+        "higher_is_better": True, "dtype": "f64",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": "sparse fat 10^4 x 10^6 CSR, 2000 uniform columns per row, N(0,1), "
+                               "b ~ N(0,1), lambda 1e-3, gamma 2 (s = 2e4)",
+                   "precond": {"qr": "N = R^-1 of the sketch's QR (full rank by the ridge)",
+                               "svd": "N = V Sigma^-1 (one-sided Jacobi SVD)"}[args.precond],
+                   "solver": args.solver},
+        "accuracy": {"rel_err_vs_ridge_closed_form": err, "ok": bool(err <= 1e-10)},
+        "phases_ms": {"sketch": mean("t_sketch_ms"), "precond": mean("t_precond_ms"),
+                      "precond_qr": mean("t_qr_ms"), "iter": mean("t_iter_ms"),
+                      "refine": mean("t_refine_ms")},
+        "iterations": info["iterations"], "refine_iterations": info["refine_iterations"],
+        "jacobi_sweeps": info["jacobi_sweeps"], "gpu_launches": int(launches), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -912,6 +1058,8 @@ def main():
         return run_sketch(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "c3":
+        return run_c3(args)
     return run_dense(args)
 
 

@@ -263,6 +263,35 @@ lsrn_status lsrn_solve_lsqr(lsrn_plan_t p, const double* b, double* x, lsrn_info
  * (1 - alpha) sqrt(s) <= sqrt(r) (no valid upper bound). */
 lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* info);
 
+/* ---- matrix-free operator (section 1: LSRN touches A only through products) ----
+ * A (m x n) given by two callbacks that apply it to blocks of k vectors in
+ * device memory, column-major:
+ *   matmat(ctx, k, x, y):  y (m x k, ld m) = A x    (x: n x k, ld n)
+ *   rmatmat(ctx, k, y, x): x (n x k, ld n) = A^T y  (y: m x k, ld m)
+ * each returning 0 on success (nonzero: the call fails with LSRN_ERR_COMM).
+ * The library synchronises its stream before a call and reads the output
+ * after it, so a callback must finish its work before it returns; it runs on
+ * the thread that called into the library.  The sketch is formed from blocks of
+ * G's columns: A~ = G A as (A^T G^T)^T with rmatmat for m >= n, A~ = A G with
+ * matmat for m < n (about 1 GiB of G per block); each iteration of LSQR or CS
+ * costs one matmat and one rmatmat with k = 1.  There is no refinement step
+ * (refine_max is taken as 0: the products are the caller's, in the caller's
+ * arithmetic), so the accuracy is that of the FP64 iteration.  Ridge
+ * (lambda > 0) works as for a stored matrix; iter_mode and sketch_mode are
+ * ignored. */
+typedef int32_t (*lsrn_matmat_fn)(void* ctx, int64_t k, const double* in, double* out);
+typedef struct {
+  int64_t m, n;
+  lsrn_matmat_fn matmat;      /* out = A in */
+  lsrn_matmat_fn rmatmat;     /* out = A^T in */
+  void* ctx;
+} lsrn_operator;
+
+/* Plan for an operator A (see above).  INVALID_ARG for sizes < 1 or missing
+ * callbacks; the rest as lsrn_plan. */
+lsrn_status lsrn_plan_operator(const lsrn_operator* op, const lsrn_options* opt, void* stream,
+                               lsrn_plan_t* out);
+
 /* ---- choice of the oversampling factor gamma (section 4.3's cost model) ----
  * The paper's operation count of a solve, split into the parts that depend on
  * s = ceil(gamma q) (q = min(m, n)): the sketch (s m randn + 2 s m n) and the QR
@@ -313,45 +342,51 @@ lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* 
                              double* const* x, const lsrn_options* opt, int32_t solver,
                              int32_t threads, lsrn_info* info, int32_t* status);
 
-/* ---- row-sharded solve (section 4.4: A partitioned by rows over processes) ----
- * One plan per shard (a GPU, a process or a host thread), each holding a block
- * of consecutive rows of the tall A (m_total >= n).  The shards exchange data
- * only through the caller's allgather callback:
- *   - the sketch: each shard computes G_p A_p with G's columns drawn at the
- *     block's global row indices (row_offset + i), the s x n partial sketches
- *     are gathered once and summed in rank order, so every shard holds the same
- *     A~ = G A and computes the same N (redundantly, no broadcast);
- *   - each fused pass over A: the partial A_p^T u_p (n values) and ||u_p||^2
- *     are gathered and summed in rank order (one exchange of n + 1 values per
- *     iteration, LSQR's scalar packed with the vector; CS uses the same);
- *   - ||b||^2 once per solve, and each refinement step's residual product
- *     A^T r (gathered as double-double and summed in double-double).
- * Every shard thus runs identical scalar recurrences and reaches the same x.
+/* ---- sharded solve (section 4.4: A partitioned over processes) ----
+ * One plan per shard (a GPU, a process or a host thread).  A is split along its
+ * long side: for m >= n (Algorithm 1) each shard holds a block of consecutive
+ * rows (all n columns); for m < n (Algorithm 2) a block of consecutive columns
+ * (all m rows).  The shards exchange data only through the caller's allgather
+ * callback:
+ *   - the sketch: each shard computes its part of the contraction over the long
+ *     side (G_p A_p, or A_p G_p) with G drawn at the block's global long-side
+ *     indices (long_offset + i); the s x q partial sketches are gathered once
+ *     and summed in rank order, so every shard holds the same A~ and computes
+ *     the same N or M (redundantly, no broadcast);
+ *   - each fused pass over A: the partial products over the long side (q values,
+ *     q = min(m, n)) and the pass's sum of squares (one exchange of q + 1 values
+ *     per iteration);
+ *   - m >= n: ||b||^2 once per solve; m < n: the LSQR ||x||^2 once per iteration;
+ *   - each refinement step's residual product in double-double, and for m < n
+ *     the step's relative change of x.
+ * Every shard runs identical scalar recurrences.  For m >= n, b is the shard's
+ * rows of b and x (n values) is the whole solution on every shard; for m < n,
+ * b is the whole b (m values) and x receives the shard's block of the solution
+ * (A_local.n values).
  *   allgather(ctx, send, recv, count): send holds `count` doubles in device
  *     memory; the callback must write world * count doubles to recv (device
  *     memory, rank-major: shard p's values at recv[p * count]) before it
  *     returns, and return 0 (nonzero: the solve stops with LSRN_ERR_COMM).  The
  *     library synchronises its stream before the call and reads recv after it.
  *     The callback runs on the thread that called into the library.
- * Ridge (lambda > 0): the rows lambda I belong to shard 0. */
+ * Ridge (lambda > 0): the rows lambda I (m >= n) or the block I_m (m < n)
+ * belong to shard 0. */
 typedef int32_t (*lsrn_allgather_fn)(void* ctx, const double* send, double* recv, int64_t count);
 typedef struct {
   int32_t rank, world;        /* this shard, number of shards (>= 1) */
-  int64_t row_offset;         /* global index of this shard's first row */
-  int64_t m_total;            /* rows of the whole matrix (m_total >= n) */
+  int32_t by_columns;         /* 0: row blocks of a tall A; 1: column blocks of a fat A */
+  int64_t long_offset;        /* global index of this shard's first row (column) */
+  int64_t long_total;         /* rows (columns) of the whole matrix, >= its short side */
   lsrn_allgather_fn allgather;
   void* ctx;
 } lsrn_shard;
 
-/* Plan for one shard: A_local is the shard's block (rows row_offset ..
- * row_offset + A_local.m - 1 of A, all n columns; dense or CSR, host or device
- * data as for lsrn_plan).  Every shard must pass the same options (seed
+/* Plan for one shard: A_local is the shard's block (host or device data, dense
+ * or CSR, as for lsrn_plan).  Every shard must pass the same options (seed
  * included) and call lsrn_sketch / lsrn_precond / lsrn_solve_* in the same
- * order: each exchange is a collective over the shards.  b given to a solve is
- * the shard's block of b (A_local.m values); x (n values) is the whole solution
- * on every shard.  UNSUPPORTED for m_total < n (Algorithm 2 partitions columns,
- * which this entry point does not build); INVALID_ARG for inconsistent shard
- * fields or a missing callback with world > 1. */
+ * order: each exchange is a collective over the shards.  INVALID_ARG for
+ * inconsistent shard fields, a long side shorter than the short side, or a
+ * missing callback with world > 1. */
 lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* opt,
                               const lsrn_shard* shard, void* stream, lsrn_plan_t* out);
 
@@ -445,6 +480,20 @@ lsrn_status lsrn_submit(lsrn_server_t s, const lsrn_matrix* A, const double* b,
                         const lsrn_options* opt, int32_t solver, uint64_t* ticket);
 lsrn_status lsrn_poll(lsrn_server_t s, uint64_t ticket, double* x_out, lsrn_info* info);
 lsrn_status lsrn_server_destroy(lsrn_server_t s);
+
+/* Continuous batching of the preconditioner phase (north star serving item):
+ * with max_short_side > 0, a request whose short side is at most that (<= 512)
+ * and whose preconditioner is the SVD of an F64 or TC_SLICED sketch is sketched
+ * by its worker and then handed to the server's batcher, which packs every
+ * request waiting at that phase (after a 0.2 ms gathering window) into one
+ * launch of the batched preconditioner (one CTA per request, as in
+ * lsrn_solve_batch) before the workers continue with their iterations.  0 (the
+ * default) turns it off.  Results are those of the batched preconditioner,
+ * which agrees with the per-request path to rounding.  INVALID_ARG outside
+ * [0, 512]. */
+lsrn_status lsrn_server_set_batching(lsrn_server_t s, int32_t max_short_side);
+/* Batched preconditioner launches so far and the requests they packed. */
+lsrn_status lsrn_server_stats(lsrn_server_t s, uint64_t* batches, uint64_t* batched_requests);
 
 #ifdef __cplusplus
 }

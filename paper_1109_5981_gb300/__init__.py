@@ -84,8 +84,18 @@ lsrn_allgather_fn = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_v
 
 class lsrn_shard(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("world", ctypes.c_int32),
-                ("row_offset", ctypes.c_int64), ("m_total", ctypes.c_int64),
-                ("allgather", lsrn_allgather_fn), ("ctx", ctypes.c_void_p)]
+                ("by_columns", ctypes.c_int32), ("long_offset", ctypes.c_int64),
+                ("long_total", ctypes.c_int64), ("allgather", lsrn_allgather_fn),
+                ("ctx", ctypes.c_void_p)]
+
+
+lsrn_matmat_fn = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p)
+
+
+class lsrn_operator(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("matmat", lsrn_matmat_fn),
+                ("rmatmat", lsrn_matmat_fn), ("ctx", ctypes.c_void_p)]
 
 
 class lsrn_gamma_model(ctypes.Structure):
@@ -125,6 +135,8 @@ _SIGS = {
     "lsrn_plan_set_lambda": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     "lsrn_choose_gamma": ([ctypes.POINTER(lsrn_gamma_model), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "lsrn_plan_operator": ([ctypes.POINTER(lsrn_operator), ctypes.POINTER(lsrn_options),
+                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "lsrn_sketch": ([ctypes.c_void_p], ctypes.c_int),
     "lsrn_precond": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "lsrn_solve_lsqr": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -151,6 +163,9 @@ _SIGS = {
     "lsrn_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(lsrn_info)],
                   ctypes.c_int),
     "lsrn_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "lsrn_server_set_batching": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "lsrn_server_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                           ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
 }
 
 
@@ -359,11 +374,12 @@ def torch_allgather(group=None):
 
 
 def lsrn_plan_sharded(A_local, opt: Optional[lsrn_options], rank: int, world: int,
-                      row_offset: int, m_total: int, allgather, stream: int = 0,
-                      csr: Optional[tuple] = None) -> Plan:
-    """lsrn_plan_sharded(): one shard (rows row_offset .. of the tall A).
-    allgather(send_ptr, recv_ptr, count) fills recv (world * count doubles,
-    rank-major) from every shard's send; exceptions become LSRN_ERR_COMM."""
+                      long_offset: int, long_total: int, allgather, stream: int = 0,
+                      csr: Optional[tuple] = None, by_columns: bool = False) -> Plan:
+    """lsrn_plan_sharded(): one shard -- rows long_offset .. of a tall A, or with
+    by_columns columns long_offset .. of a fat A.  allgather(send_ptr, recv_ptr,
+    count) fills recv (world * count doubles, rank-major) from every shard's
+    send; exceptions become LSRN_ERR_COMM."""
     lib = load_library()
     if csr is not None:
         m, n, rp, ci, vals = csr
@@ -382,8 +398,8 @@ def lsrn_plan_sharded(A_local, opt: Optional[lsrn_options], rank: int, world: in
             traceback.print_exc()
             return 1
     cb = lsrn_allgather_fn(_cb)
-    sh = lsrn_shard(rank=rank, world=world, row_offset=row_offset, m_total=m_total,
-                    allgather=cb, ctx=None)
+    sh = lsrn_shard(rank=rank, world=world, by_columns=1 if by_columns else 0,
+                    long_offset=long_offset, long_total=long_total, allgather=cb, ctx=None)
     keep += [cb, sh]
     h = ctypes.c_void_p()
     o = opt if opt is not None else default_options()
@@ -446,6 +462,36 @@ def gamma_costs_from_info(info: dict) -> dict:
     return {"c_sketch": info["t_sketch_ms"] / s, "c_qr": info["t_qr_ms"] / s,
             "c_svd": max(0.0, info["t_precond_ms"] - info["t_qr_ms"]),
             "c_iter": (info["t_iter_ms"] + info["t_refine_ms"]) / its}
+
+
+def lsrn_plan_operator(m: int, n: int, matmat, rmatmat, opt: Optional[lsrn_options] = None,
+                       stream: int = 0) -> Plan:
+    """lsrn_plan_operator(): A given by products.  matmat(k, x, y) must write
+    y = A x (x: n x k, y: m x k, column-major) and rmatmat(k, y, x) x = A^T y;
+    both receive torch views of the library's device buffers (float64, CUDA,
+    shape (k, rows) -- the column-major block seen row by row) and must finish
+    before returning.  Exceptions become LSRN_ERR_COMM."""
+    def wrap(fn, rows_in, rows_out):
+        def cb(ctx, k, inp, out):
+            try:
+                x = device_view(int(inp), int(k) * rows_in).view(int(k), rows_in)
+                y = device_view(int(out), int(k) * rows_out).view(int(k), rows_out)
+                fn(x, y)
+                import torch
+                torch.cuda.synchronize()
+                return 0
+            except Exception:
+                import traceback
+                traceback.print_exc()
+                return 1
+        return lsrn_matmat_fn(cb)
+    cm, cr = wrap(matmat, n, m), wrap(rmatmat, m, n)
+    op = lsrn_operator(m=m, n=n, matmat=cm, rmatmat=cr, ctx=None)
+    h = ctypes.c_void_p()
+    o = opt if opt is not None else default_options()
+    _check(load_library().lsrn_plan_operator(ctypes.byref(op), ctypes.byref(o), ctypes.c_void_p(stream),
+                                             ctypes.byref(h)), "lsrn_plan_operator")
+    return Plan(h.value, (cm, cr, op, matmat, rmatmat), m, n)
 
 
 def lsrn_plan_set_lambda(plan: Plan, lam: float) -> None:
@@ -598,3 +644,15 @@ def lsrn_poll(server: Server, ticket: int, x_out):
 
 def lsrn_server_destroy(server: Server) -> None:
     server.close()
+
+
+def lsrn_server_set_batching(server: Server, max_short_side: int) -> None:
+    _check(load_library().lsrn_server_set_batching(server.handle, max_short_side),
+           "lsrn_server_set_batching")
+
+
+def lsrn_server_stats(server: Server) -> tuple:
+    b, r = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().lsrn_server_stats(server.handle, ctypes.byref(b), ctypes.byref(r)),
+           "lsrn_server_stats")
+    return b.value, r.value

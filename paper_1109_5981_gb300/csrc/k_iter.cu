@@ -1754,4 +1754,73 @@ lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, 
   return LSRN_OK;
 }
 
+namespace {
+
+// Row updates of an operator pass: mult[i] = row_coef(d[i]) (the same row modes
+// as the fused pass), block partials of the sum of squares into part.
+__global__ void op_rows_kernel(RowArgs a, const double* __restrict__ coef, const double* __restrict__ d,
+                               int64_t rows, double* __restrict__ mult, double* __restrict__ part,
+                               const int* __restrict__ done) {
+  __shared__ double sh[8];
+  double ss = 0.0;
+  if (done == nullptr || !*done) {
+    Coef k{0.0, 0.0};
+    if (coef) {
+      k.c0 = coef[0];
+      k.c1 = coef[1];
+    }
+    const bool r0 = mode_reads_st0(a.mode), r1 = a.mode == RM_FAT_CS;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double s0 = r0 ? a.st0[i] : 0.0, s1 = r1 ? a.st1[i] : 0.0;
+      mult[i] = row_coef(a, k, i, d ? d[i] : 0.0, s0, s1, true, ss);
+    }
+  }
+  ss = group_sum<32>(ss);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void op_sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += part[i];
+    *out = t;
+  }
+}
+
+}  // namespace
+
+lsrn_status op_row_pass(Plan* p, const double* vin, const RowArgs& a, double* pvec, double* pscal,
+                        const int* done) {
+  if (done != nullptr) {   // after convergence nothing is applied
+    int d = 0;
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&d, done, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (d != 0) return LSRN_OK;
+  }
+  // X = A (m >= n) or A^T (m < n): d = X vin, then pvec = X^T mult
+  const lsrn_matmat_fn fwd = p->tall ? p->op.matmat : p->op.rmatmat;
+  const lsrn_matmat_fn bwd = p->tall ? p->op.rmatmat : p->op.matmat;
+  const bool need_dot = a.mode != RM_ACC_STATE;
+  if (need_dot) {
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (fwd(p->op.ctx, 1, vin, p->opd) != 0) return LSRN_ERR_COMM;
+  }
+  const int64_t rows = p->xrows;
+  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
+  launch(op_rows_kernel, parts, 256, 0, p->stream, a, a.coef, need_dot ? (const double*)p->opd : nullptr,
+         rows, p->opt_mult, pscal + 2, (const int*)nullptr);
+  launch(op_sum_kernel, 1, 32, 0, p->stream, (const double*)(pscal + 2), parts, pscal);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  if (bwd(p->op.ctx, 1, p->opt_mult, pvec) != 0) return LSRN_ERR_COMM;
+  return LSRN_OK;
+}
+
 }  // namespace lsrn

@@ -376,18 +376,28 @@ __global__ void diffnorm_kernel(const double* __restrict__ a, const double* __re
 
 // ---- helpers used by the host drivers --------------------------------------
 // ||a - b|| / ||b|| (synchronises)
-static lsrn_status rel_change(Plan* p, const double* a, const double* b, int64_t n, double* out) {
+// ||a - b|| / ||b||; with long_side set, a and b are a shard's block of a
+// vector over the long side and the sums run over all shards.
+static lsrn_status rel_change(Plan* p, const double* a, const double* b, int64_t n, double* out,
+                              bool long_side = false) {
   const int parts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 64);
   launch(diffnorm_kernel, dim3(parts), dim3(256), 0, p->stream, a, b, n, p->pscal);
   double host[128];
   LSRN_CUDA_TRY(cudaMemcpyAsync(host, p->pscal, 2 * parts * sizeof(double), cudaMemcpyDeviceToHost,
                                 p->stream));
   LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  double d2 = 0.0, b2 = 0.0;
+  double d[2] = {0.0, 0.0};
   for (int i = 0; i < parts; ++i) {
-    d2 += host[2 * i];
-    b2 += host[2 * i + 1];
+    d[0] += host[2 * i];
+    d[1] += host[2 * i + 1];
   }
+  if (long_side && p->sharded) {
+    LSRN_CUDA_TRY(cudaMemcpyAsync(p->pscal, d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
+    LSRN_TRY(shard_sum(p, p->pscal, 2));
+    LSRN_CUDA_TRY(cudaMemcpyAsync(d, p->pscal, sizeof(d), cudaMemcpyDeviceToHost, p->stream));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  }
+  const double d2 = d[0], b2 = d[1];
   *out = b2 > 0.0 ? std::sqrt(d2 / b2) : (d2 > 0.0 ? 1.0 : 0.0);
   return LSRN_OK;
 }
@@ -410,6 +420,12 @@ static lsrn_status fill(Plan* p, double* v, int64_t n, double val) {
 static lsrn_status fused_pass_local(Plan* p, const double* vin, const RowArgs& a, double* out,
                                     const int* done) {
   if (p->csr) return csr_fused_pass(p, vin, a, out, p->tcsr, p->scal + SC_SS, done);
+  if (p->is_op) {
+    LSRN_TRY(op_row_pass(p, vin, a, p->pvec, p->pscal, done));
+    LSRN_TRY(launch_extra_rows(p, vin, a, p->pvec, p->pscal, done));
+    const int nslots = p->nblk + (p->extra_rows > 0 ? 1 : 0);
+    return launch_reduce(p->pvec, nslots, p->xcols, out, p->pscal, p->scal + SC_SS, done, p->stream);
+  }
   if (p->time_passes) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -447,6 +463,18 @@ static lsrn_status fused_pass(Plan* p, const double* vin, const RowArgs& a, doub
   return LSRN_OK;
 }
 
+// shard_sum, skipped once the device `done` flag is set (the same on every shard)
+static lsrn_status shard_sum_unless_done(Plan* p, double* buf, int64_t count, const int* done) {
+  if (!p->sharded) return LSRN_OK;
+  if (done != nullptr) {
+    int d = 0;
+    LSRN_CUDA_TRY(cudaMemcpyAsync(&d, done, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (d != 0) return LSRN_OK;
+  }
+  return shard_sum(p, buf, count);
+}
+
 // ||v||^2 of a vector over the long side (b): summed over the shards.
 static lsrn_status sumsq_long(Plan* p, const double* v, int64_t n, double* out) {
   LSRN_TRY(sumsq(p, v, n, out));
@@ -457,19 +485,50 @@ static const double* c100(Plan* p) { return p->scal + SC_ONE; }   // (1, 0, 0)
 
 // Run `body` for each iteration until the device done flag is set or `cap`
 // steps have been issued; the flag is read back every `batch` steps.
+// Small problems (at most kGraphIterElems entries of X) replay the batch of
+// `batch` steps from a CUDA graph captured once: the same kernels with the same
+// device-resident arguments every batch, one launch instead of ~5 per step
+// (launch throughput, not the GPU, bounds such problems).  Their passes are then
+// not timed one by one.  Sharded and operator plans call back to the host
+// inside a step and are never captured.
+constexpr int64_t kGraphIterElems = (int64_t)1 << 25;
+
+static bool capture_iterations(const Plan* p) {
+  return !p->sharded && !p->is_op && p->xrows * p->xcols <= kGraphIterElems;
+}
+
 template <class F>
 static lsrn_status iterate(Plan* p, int cap, F body) {
   const int batch = 8;
   int issued = 0;
   int done = 0;
+  cudaGraphExec_t g = nullptr;
+  unsigned long long nodes = 0;
+  if (capture_iterations(p) && cap >= batch) {
+    p->time_passes = false;
+    lsrn_status cst = LSRN_OK;
+    g = capture_graph(p->stream, [&]() {
+      for (int i = 0; i < batch && cst == LSRN_OK; ++i) cst = body();
+    }, &nodes);
+    if (cst != LSRN_OK && g != nullptr) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  }
   while (issued < cap && !done) {
     const int nb = std::min(batch, cap - issued);
-    for (int i = 0; i < nb; ++i) LSRN_TRY(body());
+    if (g != nullptr && nb == batch) {
+      LSRN_CUDA_TRY(cudaGraphLaunch(g, p->stream));
+      g_kernel_launches.fetch_add(nodes, std::memory_order_relaxed);
+    } else {
+      for (int i = 0; i < nb; ++i) LSRN_TRY(body());
+    }
     issued += nb;
     LSRN_CUDA_TRY(cudaMemcpyAsync(&done, p->iscal + IC_DONE, sizeof(int), cudaMemcpyDeviceToHost,
                                   p->stream));
     LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
   }
+  if (g != nullptr) cudaGraphExecDestroy(g);
   return LSRN_OK;
 }
 
@@ -609,7 +668,15 @@ lsrn_status run_lsqr(Plan* p, int* iters, int* istop) {
       LSRN_TRY(fused_pass(p, p->vq2, a, p->vq, done));
       launch(lsqr_fat_scalar_kernel, 1, 32, 0, p->stream, p->scal, p->iscal);
       launch(lsqr_fat_vec_kernel, nparts, 256, 0, p->stream, p->scal, p->iscal, x, wv, vhat, ns, p->pscal);
-      launch(lsqr_fat_test_kernel, 1, 32, 0, p->stream, p->scal, p->iscal, p->pscal, nparts, tol, tol);
+      if (p->sharded) {   // ||x||^2 over all shards' blocks of x
+        launch(sum_parts_kernel, 1, 32, 0, p->stream, (const double*)p->pscal, nparts,
+               p->pscal + nparts);
+        LSRN_TRY(shard_sum_unless_done(p, p->pscal + nparts, 1, done));
+        launch(lsqr_fat_test_kernel, 1, 32, 0, p->stream, p->scal, p->iscal,
+               (const double*)(p->pscal + nparts), 1, tol, tol);
+      } else {
+        launch(lsqr_fat_test_kernel, 1, 32, 0, p->stream, p->scal, p->iscal, p->pscal, nparts, tol, tol);
+      }
       LSRN_CUDA_TRY(cudaGetLastError());
       return LSRN_OK;
     }));
@@ -688,7 +755,7 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
   // Double-float passes perturb A by ~2^-46 relative, so with a nonzero
   // residual a step contracts by ~kappa^2 2^-46 |r| / (|A||x|): two steps at least.
   if (p->X2h != nullptr && nsteps > 0) nsteps = std::max(nsteps, 2);
-  if (nsteps <= 0 || p->rank == 0) return LSRN_OK;
+  if (nsteps <= 0 || p->rank == 0 || p->is_op) return LSRN_OK;   // operator plans: no refinement
   p->pass_f32 = p->X32 != nullptr;
   double prev_change = 1.0;
   const int64_t r = p->rank, q = p->q;
@@ -697,8 +764,10 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
   int steps = 0;
   LSRN_TRY(upload_coefs(p, cheb_table(sL, sU, p->opt.refine_tol, &steps)));
   const int nslots = p->nblk + (p->extra_rows ? 1 : 0);
-  for (int it = 0; it < nsteps; ++it) {
-    double change = 0.0;
+  // The device work of one step (everything but the host read of the change),
+  // the same kernels with the same arguments every step: small problems replay
+  // it from a CUDA graph, captured again only when the pass precision switches.
+  auto step_kernels = [&]() -> lsrn_status {
     if (p->tall) {
       double* y = p->vr[2];
       double* h = p->vr[3];
@@ -723,18 +792,16 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
         LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, h, h, nullptr, blk + 5, nullptr, p->stream));
       }
       launch(axpy_kernel, grid_for(r), 256, 0, p->stream, y, z, r, 1.0);
-      // relative change of x = N y made by this step
+      // x = N y after the step, compared with x before it
       LSRN_TRY(launch_gemv_dd(p->Nm, q, r, y, p->tmpq, p->stream));
-      LSRN_TRY(rel_change(p, x, p->tmpq, q, &change));
-      LSRN_CUDA_TRY(cudaGetLastError());
     } else {
       double* rho = p->vr[5];
       double* v = p->st0;
       double* x = p->st1;
       LSRN_TRY(launch_dd_pass(p, x, nullptr, nullptr, p->pvec, p->pvec2, nullptr));
       LSRN_TRY(launch_reduce_dd(p->pvec, p->pvec2, nslots, q, p->vq, p->vq2, p->stream));
+      LSRN_TRY(shard_sum_dd(p, p->vq, p->vq2, q));
       launch(resid_dd_kernel, grid_for(q), 256, 0, p->stream, p->bdev, p->vq, p->vq2, q, p->tmpq);
-      LSRN_CUDA_TRY(cudaGetLastError());
       LSRN_TRY(launch_gemv(p->NT, r, q, p->tmpq, rho, nullptr, nullptr, c100(p), nullptr, p->stream));
       LSRN_TRY(fill(p, v, p->nstate, 0.0));
       LSRN_CUDA_TRY(cudaMemcpyAsync(p->xfull, x, p->nstate * sizeof(double),
@@ -746,14 +813,42 @@ lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken) {
         LSRN_TRY(fused_pass(p, p->vq2, a, p->vq, nullptr));
         LSRN_TRY(launch_gemv(p->NT, r, q, p->vq, rho, rho, nullptr, blk + 5, nullptr, p->stream));
       }
-      LSRN_TRY(rel_change(p, p->xfull, x, p->nstate, &change));
     }
+    LSRN_CUDA_TRY(cudaGetLastError());
+    return LSRN_OK;
+  };
+  const bool use_graph = capture_iterations(p) && nsteps > 1;
+  cudaGraphExec_t g = nullptr;
+  bool g_f32 = false;
+  unsigned long long nodes = 0;
+  for (int it = 0; it < nsteps; ++it) {
+    double change = 0.0;
+    if (use_graph && (g == nullptr || g_f32 != p->pass_f32)) {
+      if (g != nullptr) cudaGraphExecDestroy(g);
+      p->time_passes = false;
+      lsrn_status cst = LSRN_OK;
+      g = capture_graph(p->stream, [&]() { cst = step_kernels(); }, &nodes);
+      if (cst != LSRN_OK && g != nullptr) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+      g_f32 = p->pass_f32;
+    }
+    if (g != nullptr) {
+      LSRN_CUDA_TRY(cudaGraphLaunch(g, p->stream));
+      g_kernel_launches.fetch_add(nodes, std::memory_order_relaxed);
+    } else {
+      LSRN_TRY(step_kernels());
+    }
+    if (p->tall) LSRN_TRY(rel_change(p, p->xfull, p->tmpq, q, &change));
+    else LSRN_TRY(rel_change(p, p->xfull, p->st1, p->nstate, &change, true));
     *inner += steps;
     *taken += 1;
     if (change <= 1e-12) break;
     if (p->pass_f32 && change > prev_change / 20.0) p->pass_f32 = false;
     prev_change = change;
   }
+  if (g != nullptr) cudaGraphExecDestroy(g);
   p->pass_f32 = false;
   return LSRN_OK;
 }

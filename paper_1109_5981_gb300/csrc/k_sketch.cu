@@ -269,6 +269,33 @@ lsrn_status launch_sketch_add_gamma(double* C, int64_t ldc, int64_t S, int64_t Q
   return LSRN_OK;
 }
 
+// G[c * L + l] = Gamma[l, k0 + c] for l < L, c < kb (zero past column S)
+__global__ void gamma_cols_kernel(uint64_t seed, uint32_t tag, int64_t L, int64_t k0, int64_t kb,
+                                  int64_t S, double* __restrict__ G) {
+  const int64_t ng = (kb + 3) / 4;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ng * L) return;
+  const int64_t l = idx % L, g = idx / L;
+  const int64_t c0 = 4 * g;                    // k0 is a multiple of 4
+  const float4 z = normal4(seed, tag, (uint64_t)l, (uint64_t)((k0 + c0) >> 2));
+  const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t c = c0 + k;
+    if (c < kb) G[c * L + l] = (k0 + c < S) ? (double)quantize_g(zz[k]) : 0.0;
+  }
+}
+
+lsrn_status launch_gamma_cols(uint64_t seed, uint32_t tag, int64_t L, int64_t k0, int64_t kb,
+                              int64_t S, double* G, cudaStream_t st) {
+  if (k0 % 4 != 0) return LSRN_ERR_INVALID_ARG;
+  const int64_t tot = ((kb + 3) / 4) * L;
+  if (tot == 0) return LSRN_OK;
+  launch(gamma_cols_kernel, (unsigned)((tot + 255) / 256), 256, 0, st, seed, tag, L, k0, kb, S, G);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  return LSRN_OK;
+}
+
 lsrn_status launch_ridge_combine(const double* base, double* C, int64_t ldc, int64_t S, int64_t Q,
                                  double scale, uint64_t seed, uint32_t tag, int64_t lrow0,
                                  double coef, cudaStream_t st) {

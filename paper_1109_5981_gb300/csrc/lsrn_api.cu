@@ -195,7 +195,8 @@ static lsrn_status validate_options(const lsrn_options& o) {
 
 static lsrn_status plan_workspace(Plan* p) {
   const int64_t q = p->q, s = p->s;
-  p->nblk = p->csr ? 1 : pass_blocks(p->xrows, p->xcols);   // sparse passes write whole vectors
+  // sparse and operator passes write whole vectors
+  p->nblk = (p->csr || p->is_op) ? 1 : pass_blocks(p->xrows, p->xcols);
   if (p->nblk <= 0) return LSRN_ERR_UNSUPPORTED;
   LSRN_TRY(dalloc_n(p, &p->Xs, s * q));
   LSRN_TRY(dalloc_n(p, &p->Wj, q * q));
@@ -294,6 +295,8 @@ namespace lsrn {
 void plan_disable_sweep_graphs(lsrn_plan_t p) {
   if (p != nullptr) p->graph_sweeps = false;
 }
+Plan* plan_internal(lsrn_plan_t p) { return p; }
+int64_t plan_short_side(lsrn_plan_t p) { return p ? p->q : 0; }
 }  // namespace lsrn
 
 extern "C" {
@@ -343,16 +346,31 @@ lsrn_status lsrn_default_options(lsrn_options* opt) {
 }
 
 static lsrn_status plan_create(const lsrn_matrix* A, const lsrn_options* opt, void* stream,
-                               const lsrn_shard* sh, lsrn_plan_t* out) {
-  if (out == nullptr || A == nullptr) return LSRN_ERR_INVALID_ARG;
+                               const lsrn_shard* sh, lsrn_plan_t* out,
+                               const lsrn_operator* op = nullptr) {
+  if (out == nullptr || (A == nullptr && op == nullptr)) return LSRN_ERR_INVALID_ARG;
   *out = nullptr;
-  if (A->m < 1 || A->n < 1 || A->values == nullptr) return LSRN_ERR_INVALID_ARG;
+  lsrn_matrix opm{};   // an operator plan's shape, no stored entries
+  if (op != nullptr) {
+    if (op->m < 1 || op->n < 1 || op->matmat == nullptr || op->rmatmat == nullptr)
+      return LSRN_ERR_INVALID_ARG;
+    opm.m = op->m;
+    opm.n = op->n;
+    opm.format = LSRN_DENSE_ROWMAJOR;
+    A = &opm;
+  }
+  if (A->m < 1 || A->n < 1 || (A->values == nullptr && op == nullptr)) return LSRN_ERR_INVALID_ARG;
   if (A->format != LSRN_DENSE_ROWMAJOR && A->format != LSRN_DENSE_COLMAJOR && A->format != LSRN_CSR)
     return LSRN_ERR_INVALID_ARG;
   if (A->dtype != LSRN_F64 && A->dtype != LSRN_F32) return LSRN_ERR_INVALID_ARG;
   lsrn_options o;
   if (opt) o = *opt;
   else lsrn_default_options(&o);
+  if (op != nullptr) {   // products are the caller's: FP64 sweeps, no refinement, no stored-A sketch
+    o.iter_mode = LSRN_ITER_F64;
+    o.sketch_mode = LSRN_SKETCH_F64;
+    o.refine_max = 0;
+  }
   LSRN_TRY(validate_options(o));
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -377,13 +395,13 @@ static lsrn_status plan_create(const lsrn_matrix* A, const lsrn_options* opt, vo
   p->m = A->m;
   p->n = A->n;
   p->tall = A->m >= A->n;
-  if (sh != nullptr) {   // a shard: orientation from the whole matrix; exchanges when world > 1
+  if (sh != nullptr) {   // a shard: orientation from the partition; exchanges when world > 1
     p->sharded = sh->world > 1;
-    p->tall = true;
+    p->tall = sh->by_columns == 0;
     p->shard.rank = sh->rank;
     p->shard.world = sh->world;
-    p->shard.lbase = sh->row_offset;
-    p->shard.long_total = sh->m_total;
+    p->shard.lbase = sh->long_offset;
+    p->shard.long_total = sh->long_total;
     p->shard.fn = sh->allgather;
     p->shard.ctx = sh->ctx;
   }
@@ -401,10 +419,17 @@ static lsrn_status plan_create(const lsrn_matrix* A, const lsrn_options* opt, vo
     p->xscale = p->tall ? 1.0 : 1.0 / o.lambda;
   }
   p->nstate = p->xrows + p->extra_rows;
-  const bool host = !is_device_pointer(A->values);
   lsrn_status st;
-  if (p->csr) st = csr_plan_setup(p, A, host);
-  else st = dense_setup(p, A, host);
+  if (op != nullptr) {
+    p->is_op = true;
+    p->op = *op;
+    st = dalloc_n(p, &p->opd, p->xrows);
+    if (st == LSRN_OK) st = dalloc_n(p, &p->opt_mult, p->xrows);
+  } else {
+    const bool host = !is_device_pointer(A->values);
+    if (p->csr) st = csr_plan_setup(p, A, host);
+    else st = dense_setup(p, A, host);
+  }
   // FP32 passes only for m >= n: there x = N y stays in range(N), which the sketch fixes;
   // for m < n the iterate lives in R^n and FP32 rounding of A would let null(A) in.
   if (st == LSRN_OK && o.iter_mode == LSRN_ITER_F32 && !p->csr && p->tall) {
@@ -445,6 +470,12 @@ lsrn_status lsrn_plan(const lsrn_matrix* A, const lsrn_options* opt, void* strea
   return plan_create(A, opt, stream, nullptr, out);
 }
 
+lsrn_status lsrn_plan_operator(const lsrn_operator* op, const lsrn_options* opt, void* stream,
+                               lsrn_plan_t* out) {
+  if (op == nullptr) return LSRN_ERR_INVALID_ARG;
+  return plan_create(nullptr, opt, stream, nullptr, out, op);
+}
+
 lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* opt,
                               const lsrn_shard* shard, void* stream, lsrn_plan_t* out) {
   if (out == nullptr || A_local == nullptr || shard == nullptr) return LSRN_ERR_INVALID_ARG;
@@ -452,10 +483,13 @@ lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* op
   const lsrn_shard& sh = *shard;
   if (sh.world < 1 || sh.rank < 0 || sh.rank >= sh.world) return LSRN_ERR_INVALID_ARG;
   if (sh.world > 1 && sh.allgather == nullptr) return LSRN_ERR_INVALID_ARG;
-  if (sh.row_offset < 0 || A_local->m < 1 || sh.m_total < sh.row_offset + A_local->m)
-    return LSRN_ERR_INVALID_ARG;
-  if (sh.m_total > (int64_t)0xFFFFFFFFll) return LSRN_ERR_INVALID_ARG;   // G's row counter word
-  if (sh.m_total < A_local->n) return LSRN_ERR_UNSUPPORTED;               // Algorithm 2 is not sharded
+  if (sh.by_columns != 0 && sh.by_columns != 1) return LSRN_ERR_INVALID_ARG;
+  if (A_local->m < 1 || A_local->n < 1) return LSRN_ERR_INVALID_ARG;
+  const int64_t local_long = sh.by_columns ? A_local->n : A_local->m;
+  const int64_t short_side = sh.by_columns ? A_local->m : A_local->n;
+  if (sh.long_offset < 0 || sh.long_total < sh.long_offset + local_long) return LSRN_ERR_INVALID_ARG;
+  if (sh.long_total > (int64_t)0xFFFFFFFFll) return LSRN_ERR_INVALID_ARG;   // G's counter word
+  if (sh.long_total < short_side) return LSRN_ERR_INVALID_ARG;              // not the long side
   return plan_create(A_local, opt, stream, &sh, out);
 }
 
@@ -475,7 +509,26 @@ static lsrn_status sketch_with(Plan* p, int mode) {
   // A ridge plan sketches X unscaled and keeps that part (sk_base), so that a
   // new lambda only recombines it with the rows of G that meet lambda I / I_m.
   const double xs_sk = p->ridge ? 1.0 : p->xscale;
-  if (p->csr) {
+  if (p->is_op) {
+    // A~ rows from blocks of G's columns: m >= n: (A^T Gamma_blk)^T, m < n: (A Gamma_blk)^T;
+    // the callback's column-major output block is a run of rows of Xs
+    mode = LSRN_SKETCH_F64;
+    const int64_t L = p->xrows;
+    int64_t kb = std::max<int64_t>(4, ((int64_t)1 << 27) / std::max<int64_t>(L, 1) / 4 * 4);
+    kb = std::min<int64_t>(kb, (p->s + 3) / 4 * 4);
+    double* G = nullptr;
+    LSRN_CUDA_TRY(lsrn_malloc_async((void**)&G, (size_t)L * kb * sizeof(double), p->stream));
+    const lsrn_matmat_fn fn = p->tall ? p->op.rmatmat : p->op.matmat;
+    lsrn_status st = LSRN_OK;
+    for (int64_t k0 = 0; k0 < p->s && st == LSRN_OK; k0 += kb) {
+      const int64_t nb = std::min(kb, p->s - k0);
+      st = launch_gamma_cols(p->opt.seed, tag, L, k0, nb, p->s, G, p->stream);
+      if (st == LSRN_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LSRN_ERR_CUDA;
+      if (st == LSRN_OK && fn(p->op.ctx, nb, G, p->Xs + k0 * p->q) != 0) st = LSRN_ERR_COMM;
+    }
+    cudaFreeAsync(G, p->stream);
+    LSRN_TRY(st);
+  } else if (p->csr) {
     mode = LSRN_SKETCH_F64;
     LSRN_TRY(launch_sketch_csr(p->rpT, p->ciT, p->cvT, p->xrows, p->q, xs_sk, p->s,
                                p->opt.seed, tag, p->Xs, p->q, p->stream, p->shard.lbase));
@@ -731,6 +784,125 @@ lsrn_status lsrn_solve_cs(lsrn_plan_t p, const double* b, double* x, lsrn_info* 
 
 }  // extern "C"
 
+namespace lsrn {
+
+bool precond_batchable(const Plan* p) {
+  return (p->sketch_used == LSRN_SKETCH_F64 || p->sketch_used == LSRN_SKETCH_TC_SLICED) &&
+         p->opt.sketch_mode != LSRN_SKETCH_AUTO && p->opt.sketch_mode != LSRN_SKETCH_BF16 &&
+         p->opt.precond_mode == LSRN_PRECOND_SVD && batch_precond_applies(p->q) && p->state == 1;
+}
+
+// Preconditioners of sketched plans (precond_batchable) in one persistent
+// launch, largest first.  Waits for each plan's sketch; on return every plan
+// whose st[k] is LSRN_OK is preconditioned (state 2).
+void precond_batch(std::vector<Plan*>& plans, std::vector<lsrn_status>& st) {
+  const int nb = (int)plans.size();
+  if (nb == 0) return;
+  std::vector<int> order((size_t)nb);
+  for (int k = 0; k < nb; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return plans[a]->q > plans[c]->q; });
+  cudaStream_t bs = nullptr;
+  lsrn_status bst = LSRN_OK;
+  if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    bst = LSRN_ERR_CUDA;
+  }
+  std::vector<BatchPrecond> hp;
+  std::vector<int> live;   // positions in `plans` of the problems launched
+  BatchPrecond* dp = nullptr;
+  int* dout_i = nullptr;
+  double* dout_d = nullptr;
+  int* dnext = nullptr;
+  if (bst == LSRN_OK) {
+    for (int k : order) {   // every sketch must be complete, its bounded waits clean
+      Plan* p = plans[k];
+      if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st[k] = LSRN_ERR_CUDA;
+      } else if (check_tc_error(p) != LSRN_OK) {
+        st[k] = LSRN_ERR_TIMEOUT;
+      }
+      if (st[k] == LSRN_OK) live.push_back(k);
+    }
+  }
+  const int nl = (int)live.size();
+  if (bst == LSRN_OK && nl > 0 &&
+      (lsrn_malloc_async((void**)&dp, sizeof(BatchPrecond) * nl, bs) != cudaSuccess ||
+       lsrn_malloc_async((void**)&dout_i, sizeof(int) * 2 * nl, bs) != cudaSuccess ||
+       lsrn_malloc_async((void**)&dout_d, sizeof(double) * 2 * nl, bs) != cudaSuccess ||
+       lsrn_malloc_async((void**)&dnext, sizeof(int), bs) != cudaSuccess)) {
+    cudaGetLastError();
+    bst = LSRN_ERR_OOM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float batch_ms = 0.f;
+  std::vector<int> oi((size_t)2 * std::max(nl, 1));
+  std::vector<double> od((size_t)2 * std::max(nl, 1));
+  if (bst == LSRN_OK && nl > 0) {
+    for (int k = 0; k < nl; ++k) {
+      Plan* p = plans[live[k]];
+      const double rcond = p->opt.rcond >= 0.0 ? p->opt.rcond : (double)std::max(p->s, p->q) * 0x1p-53;
+      hp.push_back(BatchPrecond{p->Xs, p->Wj, p->sig, p->perm, p->Nm, p->NT, p->s, p->q, rcond,
+                                dout_i + 2 * k, dout_d + 2 * k});
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    if (cudaMemcpyAsync(dp, hp.data(), sizeof(BatchPrecond) * nl, cudaMemcpyHostToDevice, bs) !=
+        cudaSuccess)
+      bst = LSRN_ERR_CUDA;
+    cudaEventRecord(e0, bs);
+    if (bst == LSRN_OK) bst = launch_batched_precond(dp, nl, dnext, bs);
+    cudaEventRecord(e1, bs);
+    if (bst == LSRN_OK &&
+        (cudaMemcpyAsync(oi.data(), dout_i, sizeof(int) * 2 * nl, cudaMemcpyDeviceToHost, bs) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(od.data(), dout_d, sizeof(double) * 2 * nl, cudaMemcpyDeviceToHost, bs) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(bs) != cudaSuccess)) {
+      cudaGetLastError();
+      bst = LSRN_ERR_CUDA;
+    }
+    if (bst == LSRN_OK) cudaEventElapsedTime(&batch_ms, e0, e1);
+  }
+  for (int k = 0; k < nl; ++k) {
+    const int i = live[k];
+    if (bst != LSRN_OK) {
+      st[i] = bst;
+      continue;
+    }
+    Plan* p = plans[i];
+    p->rank = oi[2 * k];
+    p->sweeps = oi[2 * k + 1];
+    p->sigma_max = od[2 * k];
+    p->sigma_min = od[2 * k + 1];
+    if (p->sweeps > 40) {
+      st[i] = LSRN_ERR_NOT_CONVERGED;
+      p->state = 0;   // the QR overwrote the sketch
+      continue;
+    }
+    cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
+    p->t_precond_ms = batch_ms;   // the whole batch's launch
+    p->t_qr_ms = 0.f;
+    p->t_jacobi_ms = 0.f;
+    p->state = 2;
+  }
+  if (bst != LSRN_OK)
+    for (int k : order)
+      if (st[k] == LSRN_OK) st[k] = bst;
+  if (dp) cudaFreeAsync(dp, bs);
+  if (dout_i) cudaFreeAsync(dout_i, bs);
+  if (dout_d) cudaFreeAsync(dout_d, bs);
+  if (dnext) cudaFreeAsync(dnext, bs);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (bs) {
+    cudaStreamSynchronize(bs);
+    cudaStreamDestroy(bs);
+  }
+}
+
+}  // namespace lsrn
+
 namespace {
 
 // Run body(i) for i in [0, n) on `threads` host threads, each bound to `dev`.
@@ -810,102 +982,17 @@ lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* 
     if (st[i] == LSRN_OK) st[i] = lsrn_sketch(plans[i]);
   });
   // 2. preconditioners: one launch for the small dense-sketch problems, largest first
-  std::vector<int> batched, single;
-  for (int i = 0; i < count; ++i) {
-    if (st[i] != LSRN_OK) continue;
-    Plan* p = plans[i];
-    const bool ok_mode = p->sketch_used == LSRN_SKETCH_F64 || p->sketch_used == LSRN_SKETCH_TC_SLICED;
-    const bool ok_mode2 = p->opt.sketch_mode != LSRN_SKETCH_AUTO &&
-                          p->opt.sketch_mode != LSRN_SKETCH_BF16 &&
-                          p->opt.precond_mode == LSRN_PRECOND_SVD;
-    if (ok_mode && ok_mode2 && batch_precond_applies(p->q)) batched.push_back(i);
-    else single.push_back(i);
-  }
-  std::sort(batched.begin(), batched.end(),
-            [&](int a, int c) { return plans[a]->q > plans[c]->q; });
-  if (!batched.empty()) {
-    const int nb = (int)batched.size();
-    cudaStream_t bs = nullptr;
-    lsrn_status bst = LSRN_OK;
-    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) bst = LSRN_ERR_CUDA;
-    std::vector<BatchPrecond> hp((size_t)nb);
-    BatchPrecond* dp = nullptr;
-    int* dout_i = nullptr;
-    double* dout_d = nullptr;
-    int* dnext = nullptr;
-    if (bst == LSRN_OK) {
-      // every sketch must be complete (and its bounded waits clean) first
-      for (int i : batched) {
-        Plan* p = plans[i];
-        if (cudaStreamSynchronize(p->stream) != cudaSuccess) st[i] = LSRN_ERR_CUDA;
-        else if (check_tc_error(p) != LSRN_OK) st[i] = LSRN_ERR_TIMEOUT;
+  {
+    std::vector<Plan*> ps;
+    std::vector<int> idx;
+    for (int i = 0; i < count; ++i)
+      if (st[i] == LSRN_OK && precond_batchable(plans[i])) {
+        ps.push_back(plans[i]);
+        idx.push_back(i);
       }
-      if (lsrn_malloc_async((void**)&dp, sizeof(BatchPrecond) * nb, bs) != cudaSuccess ||
-          lsrn_malloc_async((void**)&dout_i, sizeof(int) * 2 * nb, bs) != cudaSuccess ||
-          lsrn_malloc_async((void**)&dout_d, sizeof(double) * 2 * nb, bs) != cudaSuccess ||
-          lsrn_malloc_async((void**)&dnext, sizeof(int), bs) != cudaSuccess) {
-        cudaGetLastError();
-        bst = LSRN_ERR_OOM;
-      }
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float batch_ms = 0.f;
-    if (bst == LSRN_OK) {
-      for (int k = 0; k < nb; ++k) {
-        Plan* p = plans[batched[k]];
-        const double rcond = p->opt.rcond >= 0.0 ? p->opt.rcond : (double)std::max(p->s, p->q) * 0x1p-53;
-        hp[k] = BatchPrecond{p->Xs, p->Wj, p->sig, p->perm, p->Nm, p->NT, p->s, p->q, rcond,
-                             dout_i + 2 * k, dout_d + 2 * k};
-      }
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      if (cudaMemcpyAsync(dp, hp.data(), sizeof(BatchPrecond) * nb, cudaMemcpyHostToDevice, bs) !=
-          cudaSuccess)
-        bst = LSRN_ERR_CUDA;
-      cudaEventRecord(e0, bs);
-      if (bst == LSRN_OK) bst = launch_batched_precond(dp, nb, dnext, bs);
-      cudaEventRecord(e1, bs);
-    }
-    std::vector<int> oi((size_t)2 * nb);
-    std::vector<double> od((size_t)2 * nb);
-    if (bst == LSRN_OK &&
-        (cudaMemcpyAsync(oi.data(), dout_i, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, bs) != cudaSuccess ||
-         cudaMemcpyAsync(od.data(), dout_d, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, bs) != cudaSuccess ||
-         cudaStreamSynchronize(bs) != cudaSuccess))
-      bst = LSRN_ERR_CUDA;
-    if (e0 && e1 && bst == LSRN_OK) cudaEventElapsedTime(&batch_ms, e0, e1);
-    for (int k = 0; k < nb; ++k) {
-      const int i = batched[k];
-      if (st[i] != LSRN_OK) continue;
-      if (bst != LSRN_OK) {
-        st[i] = bst;
-        continue;
-      }
-      Plan* p = plans[i];
-      p->rank = oi[2 * k];
-      p->sweeps = oi[2 * k + 1];
-      p->sigma_max = od[2 * k];
-      p->sigma_min = od[2 * k + 1];
-      if (p->sweeps > 40) {
-        st[i] = LSRN_ERR_NOT_CONVERGED;
-        continue;
-      }
-      cudaEventElapsedTime(&p->t_sketch_ms, p->ev[0], p->ev[1]);
-      p->t_precond_ms = batch_ms;   // the whole batch's launch
-      p->t_qr_ms = 0.f;
-      p->t_jacobi_ms = 0.f;
-      p->state = 2;
-    }
-    if (dp) cudaFreeAsync(dp, bs);
-    if (dout_i) cudaFreeAsync(dout_i, bs);
-    if (dout_d) cudaFreeAsync(dout_d, bs);
-    if (dnext) cudaFreeAsync(dnext, bs);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (bs) {
-      cudaStreamSynchronize(bs);
-      cudaStreamDestroy(bs);
-    }
+    std::vector<lsrn_status> bst(ps.size(), LSRN_OK);
+    precond_batch(ps, bst);
+    for (size_t k = 0; k < idx.size(); ++k) st[idx[k]] = bst[k];
   }
   // 3. the other preconditioners and all iterations, overlapping across problems
   parallel_for(count, nth, dev, [&](int i) {

@@ -175,6 +175,10 @@ struct Plan {
   bool sketch_escalated = false;       // AUTO replaced the BF16 sketch by the exact one
   double bf16_noise = 0.0;             // 2^-8 ||A~||_F / sqrt(q) of a BF16 sketch
   double bound_widen = 0.0;            // relative widening of the Theorem 4.5 bounds
+  bool is_op = false;               // A given as an operator (lsrn_plan_operator)
+  lsrn_operator op{};
+  double* opd = nullptr;            // operator passes: X vin (xrows)
+  double* opt_mult = nullptr;       // operator passes: row multipliers (xrows)
   bool sharded = false;             // a shard of a row-partitioned matrix (lsrn_plan_sharded)
   Shard shard;
 };
@@ -200,6 +204,11 @@ struct BatchPrecond {
   double* dout;   // [sigma_1, sigma_r]
 };
 bool batch_precond_applies(int64_t Q);
+// A sketched plan whose preconditioner the batched launch can compute.
+bool precond_batchable(const Plan* p);
+// Preconditioners of sketched, batchable plans in one launch (largest first);
+// st[k] receives each plan's status, state 2 on success.
+void precond_batch(std::vector<Plan*>& plans, std::vector<lsrn_status>& st);
 // N = R^-1 (q x q) and NT from the upper triangle of the factored sketch Xs; T scratch 64 q doubles
 lsrn_status launch_trinv(const double* Xs, int64_t q, double* N, double* NT, double* T,
                          double* diag, cudaStream_t st);
@@ -276,12 +285,22 @@ constexpr lsrn_status kPrecondEscalate = (lsrn_status)100;   // internal, never 
 lsrn_status run_precond(Plan* p, bool bf16_check = false);
 // Server-owned plans launch the Jacobi rounds directly (see Plan::graph_sweeps).
 void plan_disable_sweep_graphs(lsrn_plan_t p);
+// The plan behind a handle, and its short side q.
+Plan* plan_internal(lsrn_plan_t p);
+int64_t plan_short_side(lsrn_plan_t p);
 
 // fused passes
 lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
                             double* pscal, const int* done);
 lsrn_status launch_extra_rows(const Plan* p, const double* vin, const RowArgs& a, double* pvec,
                               double* pscal, const int* done);
+// The fused pass of an operator plan: d = X vin (callback), row updates as in
+// the fused pass, pvec[0:xcols] = X^T multipliers (callback), pscal[0] = sum of squares.
+lsrn_status op_row_pass(Plan* p, const double* vin, const RowArgs& a, double* pvec, double* pscal,
+                        const int* done);
+// Columns k0 .. k0 + kb of the drawing array, column-major: G[c * L + l] = Gamma[lbase + l, k0 + c]
+lsrn_status launch_gamma_cols(uint64_t seed, uint32_t tag, int64_t L, int64_t k0, int64_t kb,
+                              int64_t S, double* G, cudaStream_t st);
 lsrn_status launch_dd_pass(const Plan* p, const double* vin, const double* bvec, double* rout,
                            double* pvec_hi, double* pvec_lo, const int* done);
 lsrn_status launch_reduce(const double* pvec, int nslots, int64_t C, double* out,

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <atomic>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
@@ -67,6 +69,74 @@ size_t estimate_bytes(const lsrn_matrix& A, const lsrn_options& o) {
   return a_bytes + work + ((size_t)64 << 20);
 }
 
+// Continuous batching of the preconditioner phase: workers that reach it hand
+// their sketched plan over; the batcher packs every plan waiting at that
+// moment (after a short gathering window) into one launch of the batched
+// preconditioner kernel, then releases the workers into their iterations.
+struct PrecondBatcher {
+  struct Item {
+    lsrn::Plan* plan;
+    lsrn_status status;
+    bool done;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Item*> pending;
+  bool stop = false;
+  int device = 0;
+  std::thread th;
+  uint64_t batches = 0, packed = 0;
+
+  void run() {
+    cudaSetDevice(device);
+    for (;;) {
+      std::vector<Item*> batch;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || !pending.empty(); });
+        if (pending.empty()) return;   // stopping with nothing left
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(200));   // let others arrive
+        lk.lock();
+        batch.assign(pending.begin(), pending.end());
+        pending.clear();
+      }
+      std::vector<lsrn::Plan*> ps;
+      for (Item* it : batch) ps.push_back(it->plan);
+      std::vector<lsrn_status> st(ps.size(), LSRN_OK);
+      lsrn::precond_batch(ps, st);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t k = 0; k < batch.size(); ++k) {
+          batch[k]->status = st[k];
+          batch[k]->done = true;
+        }
+        batches += 1;
+        packed += batch.size();
+      }
+      cv.notify_all();
+    }
+  }
+
+  lsrn_status submit(lsrn::Plan* p) {
+    Item it{p, LSRN_OK, false};
+    std::unique_lock<std::mutex> lk(mu);
+    pending.push_back(&it);
+    cv.notify_all();
+    cv.wait(lk, [&] { return it.done; });
+    return it.status;
+  }
+
+  void shutdown() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    if (th.joinable()) th.join();
+  }
+};
+
 }  // namespace
 
 struct lsrn_server_s {
@@ -80,6 +150,8 @@ struct lsrn_server_s {
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, Result> results;
   std::vector<std::thread> workers;
+  PrecondBatcher batcher;
+  std::atomic<int> batch_max_q{0};   // 0: every request preconditions on its own
 
   void worker_loop() {
     cudaSetDevice(device);
@@ -109,6 +181,14 @@ struct lsrn_server_s {
       lsrn_status s = lsrn_plan(&req->A, &req->opt, st, &plan);
       if (s == LSRN_OK) {
         lsrn::plan_disable_sweep_graphs(plan);
+        const int bq = batch_max_q.load();
+        if (bq > 0 && lsrn::plan_short_side(plan) <= bq) {
+          s = lsrn_sketch(plan);
+          if (s == LSRN_OK && lsrn::precond_batchable(lsrn::plan_internal(plan)))
+            s = batcher.submit(lsrn::plan_internal(plan));
+        }
+      }
+      if (s == LSRN_OK) {
         s = req->solver == 1 ? lsrn_solve_cs(plan, req->b.data(), res.x.data(), &res.info)
                              : lsrn_solve_lsqr(plan, req->b.data(), res.x.data(), &res.info);
         lsrn_plan_destroy(plan);
@@ -145,6 +225,8 @@ lsrn_status lsrn_server_create(size_t hbm_budget_bytes, int32_t max_slots, lsrn_
   if (s == nullptr) return LSRN_ERR_OOM;
   cudaGetDevice(&s->device);
   s->budget = hbm_budget_bytes;
+  s->batcher.device = s->device;
+  s->batcher.th = std::thread([s] { s->batcher.run(); });
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s] { s->worker_loop(); });
   *out = s;
   return LSRN_OK;
@@ -222,6 +304,20 @@ lsrn_status lsrn_submit(lsrn_server_t s, const lsrn_matrix* A, const double* b,
   return LSRN_OK;
 }
 
+lsrn_status lsrn_server_set_batching(lsrn_server_t s, int32_t max_short_side) {
+  if (s == nullptr || max_short_side < 0 || max_short_side > 512) return LSRN_ERR_INVALID_ARG;
+  s->batch_max_q.store(max_short_side);
+  return LSRN_OK;
+}
+
+lsrn_status lsrn_server_stats(lsrn_server_t s, uint64_t* batches, uint64_t* batched_requests) {
+  if (s == nullptr) return LSRN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->batcher.mu);
+  if (batches) *batches = s->batcher.batches;
+  if (batched_requests) *batched_requests = s->batcher.packed;
+  return LSRN_OK;
+}
+
 lsrn_status lsrn_poll(lsrn_server_t s, uint64_t ticket, double* x_out, lsrn_info* info) {
   if (s == nullptr) return LSRN_ERR_INVALID_ARG;
   Result res;
@@ -252,6 +348,7 @@ lsrn_status lsrn_server_destroy(lsrn_server_t s) {
   }
   s->cv.notify_all();
   for (auto& t : s->workers) t.join();
+  s->batcher.shutdown();
   for (Request* r : s->queue) {
     if (r->dev_values) cudaFree(r->dev_values);
     if (r->dev_rp) cudaFree(r->dev_rp);

@@ -204,3 +204,39 @@ def test_tc_sketch_result_does_not_depend_on_free_memory():
     finally:
         L.lsrn_server_destroy(srv)
     assert np.array_equal(x_alone, x_crowded)
+
+
+def test_server_batches_the_preconditioners_of_in_flight_requests():
+    """With continuous batching on, requests that reach the preconditioner
+    phase together share one batched launch; results still match the oracle
+    and, to rounding, the same requests solved directly."""
+    reqs = []
+    for k, (m, n) in enumerate([(4000, 60), (3000, 120), (150, 2500), (6000, 200), (2500, 90),
+                                (5000, 300)]):
+        tall = m >= n
+        P = W.dense_householder(max(m, n), min(m, n), rank=min(m, n) - 3, cond=1e4, noise=1e-3,
+                                seed=170 + k)
+        A = P.A if tall else np.ascontiguousarray(P.A.T)
+        b = P.b if tall else np.random.Generator(np.random.PCG64(180 + k)).standard_normal(m)
+        reqs.append((A, b))
+    srv = L.lsrn_server_create(64 * GiB, max_slots=6)
+    try:
+        L.lsrn_server_set_batching(srv, 512)
+        opt = L.default_options(seed=21, sketch_mode=L.LSRN_SKETCH_TC_SLICED)
+        tickets = [L.lsrn_submit(srv, torch.from_numpy(A), torch.from_numpy(b), opt, k % 2)
+                   for k, (A, b) in enumerate(reqs)]
+        xs = []
+        for (A, b), t in zip(reqs, tickets):
+            x = np.zeros(A.shape[1])
+            st, info = _wait(srv, t, x)
+            assert st == L.LSRN_OK, L.status_string(st)
+            xs.append(x)
+        batches, packed = L.lsrn_server_stats(srv)
+    finally:
+        L.lsrn_server_destroy(srv)
+    assert packed == len(reqs) and 1 <= batches < packed      # at least one launch packed several
+    for k, ((A, b), x) in enumerate(zip(reqs, xs)):
+        assert O.rel_err(x, O.minlen_refined(A, b)[0]) <= 1e-10
+        xd, _ = L.solve(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(),
+                        solver="cs" if k % 2 else "lsqr", seed=21, sketch_mode=L.LSRN_SKETCH_TC_SLICED)
+        assert O.rel_err(x, xd.cpu().numpy()) <= 1e-11

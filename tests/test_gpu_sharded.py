@@ -45,7 +45,9 @@ class ThreadGather:
 
 
 def sharded_solve(A_host, b_host, world, solver="lsqr", csr=None, fail_rank=-1, **opts):
-    m = A_host.shape[0] if csr is None else csr.m
+    shape = A_host.shape if csr is None else (csr.m, csr.n)
+    by_cols = shape[0] < shape[1]                 # a fat A is split by columns
+    m = shape[1] if by_cols else shape[0]         # the long side
     gather = ThreadGather(world, fail_rank)
     out = [None] * world
 
@@ -53,7 +55,11 @@ def sharded_solve(A_host, b_host, world, solver="lsqr", csr=None, fail_rank=-1, 
         torch.cuda.set_device(0)
         off, cnt = L.shard_rows(m, world, rank)
         try:
-            if csr is None:
+            if csr is None and by_cols:
+                A = torch.from_numpy(np.ascontiguousarray(A_host[:, off:off + cnt])).cuda()
+                plan = L.lsrn_plan_sharded(A, L.default_options(**opts), rank, world, off, m,
+                                           gather.callback(rank), by_columns=True)
+            elif csr is None:
                 A = torch.from_numpy(np.ascontiguousarray(A_host[off:off + cnt])).cuda()
                 plan = L.lsrn_plan_sharded(A, L.default_options(**opts), rank, world, off, m,
                                            gather.callback(rank))
@@ -65,7 +71,8 @@ def sharded_solve(A_host, b_host, world, solver="lsqr", csr=None, fail_rank=-1, 
                        torch.from_numpy(csr.values[lo:hi].copy()).cuda())
                 plan = L.lsrn_plan_sharded(None, L.default_options(**opts), rank, world, off, m,
                                            gather.callback(rank), csr=blk)
-            b = torch.from_numpy(np.ascontiguousarray(b_host[off:off + cnt])).cuda()
+            bh = b_host if by_cols else b_host[off:off + cnt]     # fat: the whole b
+            b = torch.from_numpy(np.ascontiguousarray(bh)).cuda()
             fn = L.lsrn_solve_lsqr if solver == "lsqr" else L.lsrn_solve_cs
             try:
                 x, info = fn(plan, b)
@@ -90,6 +97,31 @@ def _check_same_on_all_shards(out):
     for o in out[1:]:
         assert np.array_equal(o[1], x0)
     return x0, out[0][2]
+
+
+def _gather_blocks(out):
+    """fat: each shard returns its block of x; all shards ran the same recurrences"""
+    assert all(o[0] == "ok" for o in out), out
+    for o in out[1:]:
+        assert o[2]["iterations"] == out[0][2]["iterations"]
+        assert o[2]["rank"] == out[0][2]["rank"]
+    return np.concatenate([o[1] for o in out]), out[0][2]
+
+
+@pytest.mark.parametrize("world,solver,lam", [(2, "lsqr", 0.0), (3, "cs", 0.0), (2, "lsqr", 0.2),
+                                              (3, "cs", 0.2)])
+def test_sharded_fat_by_columns(world, solver, lam):
+    P = W.dense_householder(2600, 110, rank=100, cond=1e4, noise=0.0, seed=77)
+    A = np.ascontiguousarray(P.A.T)                           # 110 x 2600
+    b = np.random.Generator(np.random.PCG64(78)).standard_normal(110)
+    out = sharded_solve(A, b, world, solver, seed=11, lambda_=lam)
+    x, info = _gather_blocks(out)
+    assert info["tall"] == 0 and info["m"] == 110
+    ref = O.ridge_closed_form(A, b, lam) if lam > 0 else O.minlen_refined(A, b)[0]
+    assert O.rel_err(x, ref) <= 1e-10
+    x1, _ = L.solve(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), solver=solver, seed=11,
+                    lambda_=lam)
+    assert O.rel_err(x, x1.cpu().numpy()) <= 1e-11
 
 
 @pytest.mark.parametrize("world,solver", [(2, "lsqr"), (3, "cs")])
@@ -144,6 +176,7 @@ def test_bad_shard_descriptors_are_refused():
                                          (2, 2, 0, 200, L.LSRN_ERR_INVALID_ARG),
                                          (0, 2, 50, 120, L.LSRN_ERR_INVALID_ARG),
                                          (0, 2, 0, 5, L.LSRN_ERR_INVALID_ARG),
+                                         (0, 2, 0, 101, None),
                                          (0, 1, 0, 100, None)]:
         if status is None:
             L.lsrn_plan_sharded(A, None, rank, world, off, mt, noop).close()
@@ -151,7 +184,8 @@ def test_bad_shard_descriptors_are_refused():
         with pytest.raises(L.LsrnError) as e:
             L.lsrn_plan_sharded(A, None, rank, world, off, mt, noop)
         assert e.value.status == status
-    Af = torch.zeros((10, 100), dtype=torch.float64, device="cuda")   # m_total < n: Algorithm 2
+    Af = torch.zeros((10, 100), dtype=torch.float64, device="cuda")   # rows of a fat A: not the long side
     with pytest.raises(L.LsrnError) as e:
         L.lsrn_plan_sharded(Af, None, 0, 2, 0, 20, noop)
-    assert e.value.status == L.LSRN_ERR_UNSUPPORTED
+    assert e.value.status == L.LSRN_ERR_INVALID_ARG
+    L.lsrn_plan_sharded(Af, None, 0, 2, 0, 300, noop, by_columns=True).close()

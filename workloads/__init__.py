@@ -264,3 +264,46 @@ def serving_mix(count: int, seed: int = 7, device: Optional[str] = None,
         P = dense_householder(m, n, rank, cond, 1e-4, seed * 100_003 + k, device=device)
         out.append((P, tall))
     return out
+
+
+def csr_sprandn(m: int, n: int, density: float, seed: int, dtype=np.float64) -> CsrMatrix:
+    """sprandn-like CSR built in bulk: row i holds Binomial(n, density) columns
+    drawn uniformly (repeats within a row merged), values N(0,1), columns sorted."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    counts = rng.binomial(n, density, size=m)
+    rows = np.repeat(np.arange(m, dtype=np.int64), counts)
+    cols = rng.integers(0, n, size=rows.size, dtype=np.int64)
+    key = np.unique(rows * n + cols)
+    rows, cols = key // n, key % n
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(rows, minlength=m))
+    vals = rng.standard_normal(key.size).astype(dtype)
+    return CsrMatrix(m=m, n=n, row_ptr=row_ptr, col_idx=cols.astype(np.int32), values=vals)
+
+
+def serving_requests(count: int, seed: int = 7, device: Optional[str] = None,
+                     sparse_frac: float = 0.2, lambdas=(0.0, 1e-4, 1e-2)):
+    """The serving mix: a fraction 1 - sparse_frac of dense problems drawn as in
+    serving_mix (batched configuration, condition 1e2-1e6), the rest sparse:
+    sprandn-like CSR with density 1e-3, short side log-uniform [32, 2000], long
+    side log-uniform [1e5, 2e6], half of them tall; lambda drawn uniformly from
+    `lambdas`.  Returns dicts with kind ('dense' / 'csr'), lam, and for dense the
+    problem P and its orientation (fat requests are P.A^T), for CSR the matrix."""
+    rng = np.random.Generator(np.random.PCG64(seed + 77))
+    dense = iter(serving_mix(count, seed=seed, device=device))
+    out = []
+    for k in range(count):
+        lam = float(lambdas[int(rng.integers(0, len(lambdas)))])
+        if rng.random() < sparse_frac:
+            short = int(round(math.exp(rng.uniform(math.log(32), math.log(2000)))))
+            long = int(round(math.exp(rng.uniform(math.log(1e5), math.log(2e6)))))
+            tall = bool(rng.random() < 0.5)
+            m, n = (long, short) if tall else (short, long)
+            C = csr_sprandn(m, n, 1e-3, seed * 1_000_003 + k)
+            b = rng.standard_normal(m)
+            out.append(dict(kind="csr", lam=lam, csr=C, b=b, tall=tall))
+            next(dense)
+        else:
+            P, tall = next(dense)
+            out.append(dict(kind="dense", lam=lam, P=P, tall=tall))
+    return out
