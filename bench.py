@@ -374,7 +374,7 @@ def run_serving(args):
         mixed = mode == "mixed"
         srv = L.lsrn_server_create(120 << 30, max_slots=args.slots)
         try:
-            L.lsrn_server_set_batching(srv, 512 if mixed else 0)
+            L.lsrn_server_set_batching(srv, 128 if mixed else 0)
             opts = [L.default_options(seed=99, lambda_=p["lam"],
                                       sketch_mode=L.LSRN_SKETCH_TC_SLICED if mixed else L.LSRN_SKETCH_F64,
                                       iter_mode=L.LSRN_ITER_F32 if mixed else L.LSRN_ITER_F64)

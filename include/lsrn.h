@@ -327,10 +327,11 @@ lsrn_status lsrn_choose_gamma(const lsrn_gamma_model* model, double* gamma, doub
  * whole batch:
  *   - plans and sketches are issued for all problems from `threads` host threads
  *     (0: 8), each problem on its own stream, so the sketches overlap on the GPU;
- *   - the preconditioners of all problems whose short side is at most 512 and
+ *   - the preconditioners of all problems whose short side is at most 128 and
  *     whose sketch is F64 or TC_SLICED run in ONE persistent launch, one CTA per
  *     problem (Householder QR, one-sided Jacobi, rank, N), largest first; other
- *     problems take the per-problem path;
+ *     problems take the per-problem path (one SM's FP64 rate bounds a problem in
+ *     the shared launch, which beats the per-problem path only for small q);
  *   - the iterations run per problem from the host threads, overlapping.
  * A, b, x: arrays of count descriptors / pointers (host or device data, as for
  * lsrn_plan and lsrn_solve_*).  info, status: optional arrays of count entries
@@ -482,13 +483,13 @@ lsrn_status lsrn_poll(lsrn_server_t s, uint64_t ticket, double* x_out, lsrn_info
 lsrn_status lsrn_server_destroy(lsrn_server_t s);
 
 /* Continuous batching of the preconditioner phase (north star serving item):
- * with max_short_side > 0, a request whose short side is at most that (<= 512)
- * and whose preconditioner is the SVD of an F64 or TC_SLICED sketch is sketched
- * by its worker and then handed to the server's batcher, which packs every
- * request waiting at that phase (after a 0.2 ms gathering window) into one
- * launch of the batched preconditioner (one CTA per request, as in
- * lsrn_solve_batch) before the workers continue with their iterations.  0 (the
- * default) turns it off.  Results are those of the batched preconditioner,
+ * with max_short_side > 0, a request whose short side is at most that (and at
+ * most 128, the batched kernel's limit) and whose preconditioner is the SVD of
+ * an F64 or TC_SLICED sketch is sketched by its worker and then handed to the
+ * server's batchers (four threads), one of which packs every request waiting
+ * at that phase (after a 0.2 ms gathering window) into one launch of the
+ * batched preconditioner (one CTA per request, as in lsrn_solve_batch) before
+ * the workers continue with their iterations.  0 (the default) turns it off.  Results are those of the batched preconditioner,
  * which agrees with the per-request path to rounding.  INVALID_ARG outside
  * [0, 512]. */
 lsrn_status lsrn_server_set_batching(lsrn_server_t s, int32_t max_short_side);

@@ -1,10 +1,9 @@
 // Batched preconditioner: Algorithm 1/2 steps 4-5 for many independent
 // problems in one launch.
 //
-// A batch of small problems (short side q <= 512, the uneven mix of the
-// batched and serving workloads) spends most of its preconditioner time in
-// launches: the per-problem path issues a kernel per Householder column and per
-// Jacobi round.  Here one persistent launch takes problems from a queue
+// A batch of small problems (short side q <= 128) spends most of its
+// preconditioner time in launches: the per-problem path issues a kernel per
+// Householder column and per Jacobi round.  Here one persistent launch takes problems from a queue
 // (largest first) and gives each one CTA, which runs the whole preconditioner
 // with __syncthreads between steps:
 //   1. Householder QR of the sketch Xs (S x Q, row-major), one thread per
@@ -245,7 +244,12 @@ __global__ void __launch_bounds__(kBT, 1) batched_precond_kernel(const BatchPrec
 
 }  // namespace
 
-bool batch_precond_applies(int64_t Q) { return Q >= 1 && Q <= kBMaxQ; }
+// One SM's FP64 rate bounds a problem in the batched launch (QR and Jacobi
+// ~40 q^3 flop at ~8 GFLOP/s); up to q = 128 that matches the per-problem
+// path, whose rounds are launch-bound (~10 ms), so larger problems keep the
+// per-problem path (many CTAs per round).
+constexpr int64_t kBatchMaxQ = 128;
+bool batch_precond_applies(int64_t Q) { return Q >= 1 && Q <= kBatchMaxQ && Q <= kBMaxQ; }
 
 lsrn_status launch_batched_precond(const BatchPrecond* dev_probs, int count, int* dev_next,
                                    cudaStream_t st) {

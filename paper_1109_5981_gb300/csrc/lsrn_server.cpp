@@ -84,7 +84,7 @@ struct PrecondBatcher {
   std::deque<Item*> pending;
   bool stop = false;
   int device = 0;
-  std::thread th;
+  std::vector<std::thread> th;   // several batchers: a long batch does not hold up the next
   uint64_t batches = 0, packed = 0;
 
   void run() {
@@ -133,7 +133,8 @@ struct PrecondBatcher {
       stop = true;
     }
     cv.notify_all();
-    if (th.joinable()) th.join();
+    for (auto& t : th)
+      if (t.joinable()) t.join();
   }
 };
 
@@ -182,7 +183,8 @@ struct lsrn_server_s {
       if (s == LSRN_OK) {
         lsrn::plan_disable_sweep_graphs(plan);
         const int bq = batch_max_q.load();
-        if (bq > 0 && lsrn::plan_short_side(plan) <= bq) {
+        if (bq > 0 && lsrn::plan_short_side(plan) <= bq &&
+            lsrn::batch_precond_applies(lsrn::plan_short_side(plan))) {
           s = lsrn_sketch(plan);
           if (s == LSRN_OK && lsrn::precond_batchable(lsrn::plan_internal(plan)))
             s = batcher.submit(lsrn::plan_internal(plan));
@@ -226,7 +228,7 @@ lsrn_status lsrn_server_create(size_t hbm_budget_bytes, int32_t max_slots, lsrn_
   cudaGetDevice(&s->device);
   s->budget = hbm_budget_bytes;
   s->batcher.device = s->device;
-  s->batcher.th = std::thread([s] { s->batcher.run(); });
+  for (int i = 0; i < 4; ++i) s->batcher.th.emplace_back([s] { s->batcher.run(); });
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s] { s->worker_loop(); });
   *out = s;
   return LSRN_OK;

@@ -3,7 +3,7 @@ with the preconditioners of all small problems in one launch (one CTA per
 problem).  Each result must match the oracle's min-length (or ridge) solution
 at the parity tolerance and the same problem solved alone to ~1e-11; the
 batched SVD's singular values must match the per-problem path's; problems the
-batched kernel does not take (short side > 512, CSR with a TC request, AUTO)
+batched kernel does not take (short side > 128, CSR with a TC request, AUTO)
 go through the per-problem path in the same call."""
 import numpy as np
 import pytest
