@@ -70,6 +70,8 @@ def parse(argv=None):
                          "strong scaling); replica = an independent problem per rank (weak)")
     ap.add_argument("--single-limit", type=int, default=512,
                     help="batch workload: problems solved one at a time for the comparison lines")
+    ap.add_argument("--svd", default="f64", choices=["f64", "df"],
+                    help="dense workload: FP64 Jacobi sweeps, or double-float pre-sweeps first (df)")
     ap.add_argument("--precond", default="qr", choices=["qr", "svd"],
                     help="c3 workload: N = R^-1 (full-rank ridge) or the SVD preconditioner")
     ap.add_argument("--workload", default="dense",
@@ -377,7 +379,7 @@ def run_serving(args):
             L.lsrn_server_set_batching(srv, 128 if mixed else 0)
             opts = [L.default_options(seed=99, lambda_=p["lam"],
                                       sketch_mode=L.LSRN_SKETCH_TC_SLICED if mixed else L.LSRN_SKETCH_F64,
-                                      iter_mode=L.LSRN_ITER_F32 if mixed else L.LSRN_ITER_F64)
+                                      iter_mode=L.LSRN_ITER_AUTO if mixed else L.LSRN_ITER_F64)
                     for p in pool]
 
             def submit(k):
@@ -444,7 +446,7 @@ def run_serving(args):
         "requests": len(order), "distinct_problems": pool_n,
         "mixed": mix, "fp64_plain": f64, "mixed_over_fp64_plain": mix["value"] / max(f64["value"], 1e-30),
         "latency_ms": mix["latency_ms"],
-        "dtype": "mixed: bf16 exact-slice sketch, f32 passes (dense tall), f64 SVD and refinement; "
+        "dtype": "mixed: bf16 exact-slice sketch, passes by size (f64 below 1 GiB of A), f64 SVD and refinement; "
                  "CSR: f64 sketch and passes",
         "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": f"{len(order)} requests cycling over {pool_n} problems: 80% dense "
@@ -567,8 +569,11 @@ def phase_rooflines(info_list, args, peaks: dict, fp64_peak: float, m_local: int
     t_jac = mean("t_jacobi_ms")
     jflops = 11.0 * n ** 3
     ach = jflops / (t_jac * 1e-3) / 1e12 if t_jac > 0 else 0.0
-    out["svd"] = {"kernel": "jacobi_flow_kernel (one-sided Jacobi sweeps)", "ms": t_jac,
-                  "sweeps": info_list[-1]["jacobi_sweeps"], "bound": "alu", "achieved": ach,
+    df = info_list[-1].get("jacobi_sweeps_df", 0)
+    kern = ("jacobi_df_flow_kernel (double-float sweeps, FP32 pipe) + df_times_r_kernel + "
+            "jacobi_flow_kernel (FP64 sweeps)" if df else "jacobi_flow_kernel (one-sided Jacobi sweeps)")
+    out["svd"] = {"kernel": kern, "ms": t_jac,
+                  "sweeps": info_list[-1]["jacobi_sweeps"], "sweeps_df": df, "bound": "alu", "achieved": ach,
                   "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                   "work": f"11 n^3 = {jflops:.3e} flop (the SVD count of section 4.3)",
                   "peak_source": "FP64 FMA rate probed in this run (lsrn_probe_fp64_fma)"}
@@ -687,8 +692,8 @@ def run_batch(args):
     log-uniform in [5e3, 2e5], n log-uniform in [32, 512], 70% tall / 30% fat
     (stored n x m), rank 0.8-1.0 min(m, n), condition 1e2-1e6, noise 1e-4.
     Mixed precision, batched: one lsrn_solve_batch call (exact tensor-core
-    sketch, FP32 passes for tall problems with FP64 refinement, all small
-    preconditioners in one launch).  Compared with the FP64-plain solves (FP64
+    sketch, pass precision by size -- LSRN_ITER_AUTO: FP64 below 1 GiB of A --,
+    all small preconditioners in one launch).  Compared with the FP64-plain solves (FP64
     sketch and passes) and the same mixed solves, one problem at a time."""
     import torch
     import paper_1109_5981_gb300 as L
@@ -709,7 +714,7 @@ def run_batch(args):
             xstars.append(P.apply_U(P.apply_Vt(bn) / P.sigma))
         probs.append((A, b))
     elems = sum(int(A.shape[0]) * int(A.shape[1]) for A, _ in probs)
-    mixed = L.default_options(seed=99, sketch_mode=L.LSRN_SKETCH_TC_SLICED, iter_mode=L.LSRN_ITER_F32)
+    mixed = L.default_options(seed=99, sketch_mode=L.LSRN_SKETCH_TC_SLICED, iter_mode=L.LSRN_ITER_AUTO)
     plain = L.default_options(seed=99, sketch_mode=L.LSRN_SKETCH_F64, iter_mode=L.LSRN_ITER_F64)
     solver = args.solver
 
@@ -762,7 +767,7 @@ def run_batch(args):
         "iterations": {"main_median": float(np.median([i["iterations"] for i in infos])),
                        "refine_median": float(np.median([i["refine_iterations"] for i in infos])),
                        "refine_steps_median": float(np.median([i["refine_steps"] for i in infos]))},
-        "dtype": "mixed: bf16 exact-slice sketch, f32 passes (tall) with f64 refinement, f64 SVD",
+        "dtype": "mixed: bf16 exact-slice sketch, passes by size (f64 below 1 GiB of A), f64 SVD",
         "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": f"{count} problems: m log-uniform [5e3, 2e5], n log-uniform [32, 512], "
                                "70% tall / 30% fat, rank 0.8-1.0 min(m, n), cond 1e2-1e6, noise 1e-4",
@@ -889,7 +894,8 @@ def run_dense(args):
     opts = L.default_options(seed=1234 + (0 if sharded else rank),
                              sketch_mode=sketch_mode_of(L, args.sketch),
                              iter_mode={"f32": L.LSRN_ITER_F32, "x2": L.LSRN_ITER_F32X2}.get(
-                                 args.iter, L.LSRN_ITER_F64))
+                                 args.iter, L.LSRN_ITER_F64),
+                             svd_mode=L.LSRN_SVD_DF if args.svd == "df" else L.LSRN_SVD_F64)
     solve_fn = L.lsrn_solve_lsqr if args.solver == "lsqr" else L.lsrn_solve_cs
 
     def make_plan(Amat, o):
@@ -1029,7 +1035,7 @@ def run_dense(args):
                           "iter": float(np.mean([i["t_iter_ms"] for i in infos])),
                           "refine": float(np.mean([i["t_refine_ms"] for i in infos]))},
             "iterations": info["iterations"], "refine_iterations": info["refine_iterations"],
-            "jacobi_sweeps": info["jacobi_sweeps"],
+            "jacobi_sweeps": info["jacobi_sweeps"], "jacobi_sweeps_df": info["jacobi_sweeps_df"],
             "refine_steps": info["refine_steps"],
             "rank": info["rank"], "s": info["s"],
             "roofline": roofline,

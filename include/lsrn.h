@@ -73,7 +73,7 @@ typedef enum {
                                    range(N) whatever the pass precision.  For m < n the option
                                    is ignored (FP64 passes): there x is iterated in R^n and
                                    FP32 rounding of A would add components in null(A). */
-  LSRN_ITER_F32X2 = 2           /* dense A whose short side q has 512 < q <= 4096 (other
+  LSRN_ITER_F32X2 = 2,          /* dense A whose short side q has 512 < q <= 4096 (other
                                    shapes: FP64 passes): the plan keeps A / 2^e as two FP32
                                    planes hi + lo (48 significant bits, 8 bytes per entry, e
                                    the exponent of max |A_ij|) and every pass runs on the FP32
@@ -85,6 +85,12 @@ typedef enum {
                                    r = b - Ax and A^T r exact to ~2^-65 (three FP32 planes).
                                    Vectors and row coefficients are rescaled by powers of two
                                    inside the pass, so any finite A, b work. */
+  LSRN_ITER_AUTO = 3            /* by size: FP64 passes for CSR A and for dense A of less than
+                                   1 GiB in FP64 (8 m n bytes; such A is read largely from L2
+                                   and the extra refinement passes of the reduced-precision
+                                   modes cost more than the passes save); above that
+                                   LSRN_ITER_F32X2 where it applies, else LSRN_ITER_F32 for
+                                   m >= n, else FP64.  lsrn_info.iter_used reports the choice. */
 } lsrn_iter_mode;
 
 typedef enum {
@@ -114,6 +120,22 @@ typedef enum {
                                    one-sided Jacobi sweeps are not needed.  lsrn_plan_get_precond
                                    then reports |R_ii| (descending) in place of sigma~. */
 } lsrn_precond_mode;
+
+typedef enum {
+  LSRN_SVD_F64 = 0,             /* one-sided Jacobi sweeps in FP64 on R (default) */
+  LSRN_SVD_DF = 1               /* 1024 < n' <= 4096: the early sweeps in double-float arithmetic
+                                   (pairs of FP32, ~2^-46) on a copy of R, with the rotations
+                                   accumulated into P, then Y = P R in FP64 and FP64 sweeps on Y
+                                   until no pair rotates (usually one rotating sweep and one
+                                   check).  sigma~(Y) is sigma~(R) up to the relative factor
+                                   ||P^T P - I|| (~1e-12), and N = W_r Sigma_r^-2 from Y's sweeps
+                                   gives R N = P^-1 J, so Lemma 4.3 holds as for FP64 sweeps.
+                                   Other sizes: FP64 sweeps.  Correct but not faster on GB300 as
+                                   built: a double-float sweep reads and writes the rows of P as
+                                   well as W, and with both held in registers two pairs fit on an
+                                   SM, so it is bound by latency (about 57 ms a sweep against
+                                   41 ms for an FP64 sweep at n' = 2000). */
+} lsrn_svd_mode;
 
 /* The matrix A (m x n).  For LSRN_CSR, columns within a row need not be
  * sorted but must be in [0, n) and row_ptr must be non-decreasing with
@@ -148,6 +170,7 @@ typedef struct {
                           shrinks the change by less than 20x */
   int32_t precond_mode;  /* lsrn_precond_mode (default LSRN_PRECOND_SVD); LSRN_PRECOND_QR
                             needs lambda > 0 (INVALID_ARG otherwise) */
+  int32_t svd_mode;      /* lsrn_svd_mode (default LSRN_SVD_F64) */
 } lsrn_options;
 
 typedef struct {
@@ -171,10 +194,12 @@ typedef struct {
                                      sweep converged return at once and are not counted
                                      (duration below a quarter of the longest pass) */
   float t_qr_ms;                  /* Householder QR of the sketch inside t_precond_ms */
-  int32_t jacobi_sweeps;          /* one-sided Jacobi sweeps of the preconditioner */
+  int32_t jacobi_sweeps;          /* FP64 one-sided Jacobi sweeps of the preconditioner */
   float t_jacobi_ms;              /* the Jacobi sweeps inside t_precond_ms */
   int32_t sketch_used;            /* lsrn_sketch_mode of the sketch the preconditioner used */
   int32_t sketch_escalated;       /* 1: LSRN_SKETCH_AUTO replaced the BF16 sketch by the exact one */
+  int32_t jacobi_sweeps_df;       /* double-float sweeps before the FP64 ones (LSRN_SVD_DF) */
+  int32_t iter_used;              /* lsrn_iter_mode the passes ran in (LSRN_ITER_AUTO resolved) */
 } lsrn_info;
 
 typedef struct lsrn_plan_s* lsrn_plan_t;

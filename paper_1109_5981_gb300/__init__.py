@@ -37,9 +37,10 @@ LSRN_ERR_COMM = -10
 LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
 LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED, LSRN_SKETCH_BF16, LSRN_SKETCH_AUTO = 0, 1, 2, 3
-LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2 = 0, 1, 2
+LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2, LSRN_ITER_AUTO = 0, 1, 2, 3
 LSRN_KNOB_JACOBI_WAIT_NS, LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 0, 1
 LSRN_PRECOND_SVD, LSRN_PRECOND_QR = 0, 1
+LSRN_SVD_F64, LSRN_SVD_DF = 0, 1
 
 
 class lsrn_matrix(ctypes.Structure):
@@ -55,7 +56,8 @@ class lsrn_options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("sketch_mode", ctypes.c_int32), ("iter_mode", ctypes.c_int32),
-                ("precond_mode", ctypes.c_int32)]
+                ("precond_mode", ctypes.c_int32),
+                ("svd_mode", ctypes.c_int32)]
 
 
 class lsrn_info(ctypes.Structure):
@@ -72,7 +74,8 @@ class lsrn_info(ctypes.Structure):
                 ("t_pass_ms", ctypes.c_float), ("n_pass", ctypes.c_int32),
                 ("t_qr_ms", ctypes.c_float), ("jacobi_sweeps", ctypes.c_int32),
                 ("t_jacobi_ms", ctypes.c_float), ("sketch_used", ctypes.c_int32),
-                ("sketch_escalated", ctypes.c_int32)]
+                ("sketch_escalated", ctypes.c_int32),
+                ("jacobi_sweeps_df", ctypes.c_int32), ("iter_used", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -549,7 +549,7 @@ __device__ __forceinline__ void named_arrive(int id, int n) {
 // then warps 0-7 accumulate stage k - 1.  The FP64 row update is thus off the
 // compute warps' critical path.
 template <int SLOTS, int RB>
-__global__ void __launch_bounds__(kX2Threads, 1) row_pass_x2_kernel(
+__global__ void __launch_bounds__(kX2Threads, (RB == 2 && SLOTS <= 4) ? 2 : 1) row_pass_x2_kernel(
     const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t rows, int C, int64_t ldx,
     double xs, const double* __restrict__ vin, RowArgs args, double* __restrict__ pvec,
     double* __restrict__ pscal, const int* __restrict__ done, int* __restrict__ err, int rowbytes,
@@ -1475,10 +1475,14 @@ static int pick_layout(int64_t C, int* tpr, int* slots) {
   return 0;
 }
 
-int pass_blocks(int64_t rows, int64_t C) {
+int pass_blocks(int64_t rows, int64_t C, bool x2) {
   int tpr, slots;
   if (pick_layout(C, &tpr, &slots) != 0) return 0;
-  if (pass_is_staged(C)) return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), rows));
+  if (pass_is_staged(C)) {
+    // double-float passes up to 2048 columns: two CTAs per SM (x2_geometry)
+    const int per_sm = (x2 && C <= 2048) ? 2 : 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * num_sms(), rows));
+  }
   const int64_t gpc = kThreads / tpr;
   const int64_t per = gpc * 2;
   const int64_t want = (rows + per - 1) / per;
@@ -1522,15 +1526,18 @@ static lsrn_status launch_staged(const Plan* p, const T* X, int64_t ldx, const d
   return LSRN_OK;
 }
 
-// Geometry of the double-float pass: RB rows of both planes per stage (RB = 4
-// up to 2048 columns, 2 above), as many stages as fit in 196 KB (at most 8).
+// Geometry of the double-float pass: RB = 2 rows of both planes per stage.  Up
+// to 2048 columns three stages (96 KB), so that two CTAs share an SM: twice the
+// warps to hide the latency of the dependent double-float chains (4-row stages
+// with one CTA per SM streamed at 0.40 of HBM, this at 0.47).  Above 2048
+// columns as many stages as fit in 196 KB (at most 8), one CTA per SM.
 static bool x2_geometry(int64_t C, int64_t ldx2, int* planebytes, int* rb, int* nstages) {
   if (C <= 512 || C > 4096) return false;
   const int64_t pbytes = (C * 4 + 15) / 16 * 16;
   if (pbytes > ldx2 * 4 || (ldx2 * 4) % 16 != 0) return false;
-  const int r = C <= 2048 ? 4 : 2;
+  const int r = 2;
   const int64_t stage = 2 * r * pbytes + 2 * r * 8;
-  const int ns = (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / stage);
+  const int ns = C <= 2048 ? 3 : (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / stage);
   if (ns < 3) return false;
   *planebytes = (int)pbytes;
   *rb = r;
@@ -1564,8 +1571,8 @@ lsrn_status launch_row_pass(const Plan* p, const double* vin, const RowArgs& a, 
   const int C = (int)p->xcols;
   int rowbytes = 0, rb = 0, ns = 0;
   if (p->X2h != nullptr && x2_geometry(C, p->ldx2, &rowbytes, &rb, &ns)) {
-    if (slots == 2 && rb == 4) return launch_x2<2, 4>(p, vin, a, pvec, pscal, done, rowbytes, ns);
-    if (slots == 4 && rb == 4) return launch_x2<4, 4>(p, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 2 && rb == 2) return launch_x2<2, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
+    if (slots == 4 && rb == 2) return launch_x2<4, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
     if (slots == 8 && rb == 2) return launch_x2<8, 2>(p, vin, a, pvec, pscal, done, rowbytes, ns);
   }
   if (p->pass_f32 && staged_geometry(C, p->ldx32, sizeof(float), &rowbytes, &rb, &ns)) {

@@ -889,8 +889,6 @@ lsrn_status run_precond(Plan* p, bool bf16_check) {
   }
   // 2. One-sided Jacobi on the rows of R.
   const int64_t QQ = Q * Q;
-  launch(extract_r_kernel, (unsigned)((QQ + 255) / 256), 256, 0, st, X, Q, p->Wj);
-  LSRN_CUDA_TRY(cudaGetLastError());
   const int P = (int)(Q + (Q & 1));
   const double tol = (double)std::max(S, Q) * 0x1p-53;
   const int warps_per_round = P / 2;
@@ -914,6 +912,21 @@ lsrn_status run_precond(Plan* p, bool bf16_check) {
   const int64_t knob_wait = test_knob(LSRN_KNOB_JACOBI_WAIT_NS);
   const uint64_t wait_ns = knob_wait > 0 ? (uint64_t)knob_wait : kJacWaitNs;
   const int skip_items = test_knob(LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND) != 0 ? P / 2 : 0;
+  // Double-float pre-sweeps (k_jacobi_df.cu) leave Y = P R in Wj, nearly
+  // orthogonal rows; otherwise Wj = R.
+  p->sweeps_df = 0;
+  if (flow && p->opt.svd_mode == LSRN_SVD_DF && jacobi_df_applies(Q)) {
+    int dsw = 0;
+    const lsrn_status ds = jacobi_df_phase(p, knob_wait, skip_items, &dsw);
+    p->sweeps_df = dsw;
+    if (ds != LSRN_OK) {
+      p->sweeps = 0;
+      return ds;
+    }
+  } else {
+    launch(extract_r_kernel, (unsigned)((QQ + 255) / 256), 256, 0, st, X, Q, p->Wj);
+    LSRN_CUDA_TRY(cudaGetLastError());
+  }
   if (flow) {
     LSRN_CUDA_TRY(lsrn_malloc_async((void**)&jws, (Q + 2) * sizeof(int), st));
     int per_sm = 0;

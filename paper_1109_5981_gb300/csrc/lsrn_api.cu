@@ -18,7 +18,7 @@ lsrn_status run_lsqr(Plan* p, int* iters, int* istop);
 lsrn_status run_cs(Plan* p, int* iters, double* sL, double* sU, bool* diverged);
 lsrn_status run_refine(Plan* p, int nsteps, int* inner, int* taken);
 lsrn_status finish_x(Plan* p, double* xout);
-int pass_blocks(int64_t rows, int64_t C);
+int pass_blocks(int64_t rows, int64_t C, bool x2);
 lsrn_status csr_plan_setup(Plan* p, const lsrn_matrix* A, bool host);
 
 static thread_local char g_last_error[512];
@@ -185,18 +185,20 @@ static lsrn_status validate_options(const lsrn_options& o) {
   if (!(o.refine_tol > 0.0) || !(o.refine_tol < 1.0)) return LSRN_ERR_INVALID_ARG;
   if (o.sketch_mode < LSRN_SKETCH_F64 || o.sketch_mode > LSRN_SKETCH_AUTO) return LSRN_ERR_INVALID_ARG;
   if (o.iter_mode != LSRN_ITER_F64 && o.iter_mode != LSRN_ITER_F32 &&
-      o.iter_mode != LSRN_ITER_F32X2)
+      o.iter_mode != LSRN_ITER_F32X2 && o.iter_mode != LSRN_ITER_AUTO)
     return LSRN_ERR_INVALID_ARG;
   if (o.precond_mode != LSRN_PRECOND_SVD && o.precond_mode != LSRN_PRECOND_QR)
     return LSRN_ERR_INVALID_ARG;
   if (o.precond_mode == LSRN_PRECOND_QR && !(o.lambda > 0.0)) return LSRN_ERR_INVALID_ARG;
+  if (o.svd_mode != LSRN_SVD_F64 && o.svd_mode != LSRN_SVD_DF) return LSRN_ERR_INVALID_ARG;
   return LSRN_OK;
 }
 
 static lsrn_status plan_workspace(Plan* p) {
   const int64_t q = p->q, s = p->s;
   // sparse and operator passes write whole vectors
-  p->nblk = (p->csr || p->is_op) ? 1 : pass_blocks(p->xrows, p->xcols);
+  const bool x2 = p->opt.iter_mode == LSRN_ITER_F32X2 && !p->csr && !p->is_op && x2_applies(p->xcols);
+  p->nblk = (p->csr || p->is_op) ? 1 : pass_blocks(p->xrows, p->xcols, x2);
   if (p->nblk <= 0) return LSRN_ERR_UNSUPPORTED;
   LSRN_TRY(dalloc_n(p, &p->Xs, s * q));
   LSRN_TRY(dalloc_n(p, &p->Wj, q * q));
@@ -372,6 +374,7 @@ static lsrn_status plan_create(const lsrn_matrix* A, const lsrn_options* opt, vo
     o.refine_max = 0;
   }
   LSRN_TRY(validate_options(o));
+  o.iter_mode = resolve_iter_mode(o.iter_mode, A->m, A->n, A->format == LSRN_CSR);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -413,10 +416,13 @@ static lsrn_status plan_create(const lsrn_matrix* A, const lsrn_options* opt, vo
   p->q = p->xcols;
   p->s = (int64_t)std::ceil(o.gamma * (double)p->q);
   if (p->s <= p->q) p->s = p->q + 1;
-  if (p->ridge && !(p->sharded && p->shard.rank != 0)) {   // shard 0 holds the rows lambda I
-    p->extra_rows = p->tall ? A->n : A->m;
+  if (p->ridge) {
+    // every shard sketches and iterates the same augmented problem (the same
+    // A~ from the summed sketch, the same scaling of a fat A); only shard 0
+    // holds the appended rows lambda I / I_m in its passes
     p->extra_coef = p->tall ? o.lambda : 1.0;
     p->xscale = p->tall ? 1.0 : 1.0 / o.lambda;
+    if (!(p->sharded && p->shard.rank != 0)) p->extra_rows = p->tall ? A->n : A->m;
   }
   p->nstate = p->xrows + p->extra_rows;
   lsrn_status st;
@@ -695,8 +701,10 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   if (p->state < 2) LSRN_TRY(lsrn_precond(p, nullptr));
   lsrn_info inf;
   memset(&inf, 0, sizeof(inf));
-  inf.m = p->shard.long_total > 0 ? p->shard.long_total : p->m;
-  inf.n = p->n;
+  // a shard reports the whole problem: the long side is the partitioned one
+  const bool long_total = p->shard.long_total > 0;
+  inf.m = long_total && p->tall ? p->shard.long_total : p->m;
+  inf.n = long_total && !p->tall ? p->shard.long_total : p->n;
   inf.s = p->s;
   inf.rank = p->rank;
   inf.tall = p->tall ? 1 : 0;
@@ -706,6 +714,8 @@ static lsrn_status solve_common(lsrn_plan_t p, const double* b, double* x, lsrn_
   inf.t_precond_ms = p->t_precond_ms;
   inf.t_qr_ms = p->t_qr_ms;
   inf.jacobi_sweeps = p->sweeps;
+  inf.jacobi_sweeps_df = p->sweeps_df;
+  inf.iter_used = p->opt.iter_mode;
   inf.t_jacobi_ms = p->t_jacobi_ms;
   inf.sketch_used = p->sketch_used;
   inf.sketch_escalated = p->sketch_escalated ? 1 : 0;
@@ -873,6 +883,7 @@ void precond_batch(std::vector<Plan*>& plans, std::vector<lsrn_status>& st) {
     Plan* p = plans[i];
     p->rank = oi[2 * k];
     p->sweeps = oi[2 * k + 1];
+    p->sweeps_df = 0;
     p->sigma_max = od[2 * k];
     p->sigma_min = od[2 * k + 1];
     if (p->sweeps > 40) {

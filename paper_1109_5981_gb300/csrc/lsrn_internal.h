@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <utility>
 #include <vector>
 
@@ -141,7 +142,8 @@ struct Plan {
   double* NT = nullptr;             // r x q row-major
   int64_t rank = 0;
   double sigma_max = 0.0, sigma_min = 0.0;
-  int sweeps = 0;
+  int sweeps = 0;                   // FP64 Jacobi sweeps
+  int sweeps_df = 0;                // double-float Jacobi sweeps before them
   int state = 0;                    // 0 planned, 1 sketched, 2 preconditioned
   // Replay each Jacobi sweep from a captured CUDA graph.  Off for plans run by
   // the server: there several streams share the GPU and fill one another's
@@ -283,6 +285,10 @@ bool is_device_pointer(const void* ptr);
 // |R_ii| (an upper bound on sigma_min) is below 16 times it.
 constexpr lsrn_status kPrecondEscalate = (lsrn_status)100;   // internal, never returned by the ABI
 lsrn_status run_precond(Plan* p, bool bf16_check = false);
+// Double-float Jacobi pre-sweeps on R (k_jacobi_df.cu): for 1024 < q <= 4096,
+// leaves Y = P R (P the accumulated rotations) in p->Wj for the FP64 sweeps.
+bool jacobi_df_applies(int64_t Q);
+lsrn_status jacobi_df_phase(Plan* p, int64_t wait_ns_knob, int skip_items, int* sweeps_out);
 // Server-owned plans launch the Jacobi rounds directly (see Plan::graph_sweeps).
 void plan_disable_sweep_graphs(lsrn_plan_t p);
 // The plan behind a handle, and its short side q.
@@ -313,6 +319,13 @@ lsrn_status launch_gemv(const double* M, int64_t R, int64_t C, const double* v, 
                         cudaStream_t st);
 // Y (rows x ldy, FP32, zero beyond cols) = X (rows x cols, FP64, ldx)
 bool x2_applies(int64_t C);
+// LSRN_ITER_AUTO to a concrete pass precision (the rule in lsrn.h); other modes unchanged
+inline int32_t resolve_iter_mode(int32_t mode, int64_t m, int64_t n, bool csr) {
+  if (mode != LSRN_ITER_AUTO) return mode;
+  if (csr || 8.0 * (double)m * (double)n < (double)(1ll << 30)) return LSRN_ITER_F64;
+  if (x2_applies(std::min(m, n))) return LSRN_ITER_F32X2;
+  return m >= n ? LSRN_ITER_F32 : LSRN_ITER_F64;
+}
 lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Yh,
                          float* Yl, float* Y3, int64_t ldy, unsigned long long* maxbits, double* xs,
                          cudaStream_t st);

@@ -58,8 +58,9 @@ size_t estimate_bytes(const lsrn_matrix& A, const lsrn_options& o) {
   else
     a_bytes = (size_t)m * n * 8 * 2;   // owned copy + possible re-layout
   size_t work = 8 * ((size_t)s * q + 3 * (size_t)q * q + 6 * (size_t)(rows + extra) + 16 * (size_t)q);
-  if (o.iter_mode == LSRN_ITER_F32 && A.format != LSRN_CSR) work += (size_t)m * n * 4;
-  if (o.iter_mode == LSRN_ITER_F32X2 && A.format != LSRN_CSR) work += (size_t)m * n * 12;   // 3 planes
+  const int32_t iter = lsrn::resolve_iter_mode(o.iter_mode, m, n, A.format == LSRN_CSR);
+  if (iter == LSRN_ITER_F32 && A.format != LSRN_CSR) work += (size_t)m * n * 4;
+  if (iter == LSRN_ITER_F32X2 && A.format != LSRN_CSR) work += (size_t)m * n * 12;   // 3 planes
   if ((o.sketch_mode == LSRN_SKETCH_TC_SLICED || o.sketch_mode == LSRN_SKETCH_AUTO) &&
       A.format != LSRN_CSR)   // the plan's exact sizing
     work += lsrn::sketch_tc_scratch_bytes(lsrn::sketch_tc_plan_segment_rows(rows, q, s - 1), q, s - 1);

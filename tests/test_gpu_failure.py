@@ -24,11 +24,15 @@ torch = pytest.importorskip("torch")
 L = pytest.importorskip("paper_1109_5981_gb300")
 
 
-def test_dataflow_jacobi_wait_runs_out_then_the_plan_recovers():
+@pytest.mark.parametrize("svd_mode", ["df", "f64"])
+def test_dataflow_jacobi_wait_runs_out_then_the_plan_recovers(svd_mode):
+    # df: the double-float pre-sweep kernel is the one that gives up;
+    # f64: the FP64 sweep kernel
     P = W.dense_haar(2600, 1100, 1000, 1e4, 1e-3, seed=5)     # q = 1100: dataflow sweep
     A = torch.from_numpy(P.A).cuda()
     b = torch.from_numpy(P.b).cuda()
-    plan = L.lsrn_plan(A, L.default_options(seed=2))
+    mode = L.LSRN_SVD_DF if svd_mode == "df" else L.LSRN_SVD_F64
+    plan = L.lsrn_plan(A, L.default_options(seed=2, svd_mode=mode))
     try:
         L.lsrn_sketch(plan)
         L.lsrn_set_test_knob(L.LSRN_KNOB_JACOBI_WAIT_NS, 2_000_000)
@@ -47,6 +51,7 @@ def test_dataflow_jacobi_wait_runs_out_then_the_plan_recovers():
     finally:
         plan.close()
     assert info["rank"] == 1000
+    assert (info["jacobi_sweeps_df"] > 0) == (svd_mode == "df")
     xs, _ = O.minlen_refined(P.A, P.b)
     assert O.rel_err(x.cpu().numpy(), xs) <= 1e-10
 
