@@ -146,12 +146,15 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # CPU baseline: the oracle on bounded samples                                  #
 # --------------------------------------------------------------------------- #
-SAMPLE_ROWS = 10_000          # rows of A in the timed sketch sample
-SAMPLE_SVD_N = 240            # columns of the timed Jacobi SVD sample
+SAMPLE_ROWS = 10_000          # rows of A in the timed sketch sample (reference arm, per step)
+SAMPLE_SVD_N = 240            # columns of the timed Jacobi SVD sample (reference arm, per step)
+BASELINE_ROW_FRAC = 0.1       # cpu_baseline (once per run): a tenth of the rows ...
+BASELINE_SVD_N = 1000         # ... and the Jacobi SVD at half the columns (x8 by the n^3 law)
 
 
 def oracle_sampled_solve_seconds(A_host: np.ndarray, b_host: np.ndarray, iters: int,
-                                 refine_passes: int, seed: int = 0) -> dict:
+                                 refine_passes: int, seed: int = 0, rows: int = SAMPLE_ROWS,
+                                 svd_n: int = SAMPLE_SVD_N) -> dict:
     """Time the oracle's LSRN stages on bounded samples of the workload and
     extrapolate to one full solve with the paper's cost model (section 4.3, eq.
     lsrn_flops): the sketch (s*m normals + 2smn) is linear in the rows, the SVD
@@ -165,7 +168,7 @@ def oracle_sampled_solve_seconds(A_host: np.ndarray, b_host: np.ndarray, iters: 
     s = math.ceil(2.0 * n)
     out = {}
     # sketch: G (s x m_s) drawn by the oracle, times A[:m_s]
-    m_s = min(m, SAMPLE_ROWS)
+    m_s = max(1, min(m, rows))
     t = time.perf_counter()
     G = O.sketch_block(seed, 0, 0, m_s, s).T
     At_part = G @ A_host[:m_s]
@@ -173,7 +176,7 @@ def oracle_sampled_solve_seconds(A_host: np.ndarray, b_host: np.ndarray, iters: 
     del G, At_part
     # SVD of a (2 n_s) x n_s matrix with the workload's spectrum shape (log-spaced
     # 1 -> 1e-6 on 90% of the columns) by the oracle's one-sided Jacobi
-    n_s = min(n, SAMPLE_SVD_N)
+    n_s = max(1, min(n, svd_n))
     rng = np.random.Generator(np.random.PCG64(1))
     r_s = max(1, int(0.9 * n_s))
     sig = np.zeros(n_s)
@@ -996,7 +999,9 @@ def run_dense(args):
     if world == 1 and not args.no_cpu_baseline:
         A_np = A.cpu().numpy()
         r = oracle_sampled_solve_seconds(A_np, b.cpu().numpy(), info["iterations"],
-                                         info["refine_iterations"] + 1)
+                                         info["refine_iterations"] + 1,
+                                         rows=int(BASELINE_ROW_FRAC * A_np.shape[0]),
+                                         svd_n=BASELINE_SVD_N)
         cpu = {"value": 1.0 / r["total_s"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": r["sample"], "sample_s": r["sample_s"],
                "stages_s": {k: r[k] for k in ("sketch_s", "svd_s", "iter_s")},

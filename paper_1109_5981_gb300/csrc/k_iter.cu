@@ -758,40 +758,73 @@ __global__ void __launch_bounds__(kX2Threads, (RB == 2 && SLOTS <= 4) ? 2 : 1) r
     if (need_dot) {
       const float* hp = (const float*)(smem + (size_t)st * stage_bytes);
       const float* lp = hp + (size_t)RB * rstride;
+      // all rows' chains first (independent), then one transposed butterfly
+      f32x2 h2[RB], l2[RB];
 #pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        float h = 0.0f, l = 0.0f;
-        if (have && r < nr) {
-          // one packed chain: even columns in one lane, odd columns in the other
-          f32x2 h2 = 0ull, l2 = 0ull;
+      for (int r = 0; r < RB; ++r) h2[r] = l2[r] = 0ull;
 #pragma unroll
-          for (int s = 0; s < SLOTS; ++s) {
-            const int c = 2 * tid + 2 * kThreads * s;
-            if (c < C) {
+      for (int s = 0; s < SLOTS; ++s) {
+        const int c = 2 * tid + 2 * kThreads * s;
+        if (have && c < C) {
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            if (r < nr) {
               const f32x2 a = *reinterpret_cast<const f32x2*>(hp + (size_t)r * rstride + c);
               const f32x2 b = *reinterpret_cast<const f32x2*>(lp + (size_t)r * rstride + c);
-              df_fma2(a, b, vh[s], vhn[s], vl[s], h2, l2);   // vin is 0 past C
+              df_fma2(a, b, vh[s], vhn[s], vl[s], h2[r], l2[r]);   // vin is 0 past C
             }
           }
-          const float2 hh = upk2(h2), ll = upk2(l2);
-          float sum, er;
-          two_sum_f(hh.x, hh.y, sum, er);
-          h = sum;
-          l = ll.x + (ll.y + er);
         }
+      }
+      float h[RB], l[RB];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-          const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+      for (int r = 0; r < RB; ++r) {
+        const float2 hh = upk2(h2[r]), ll = upk2(l2[r]);
+        float sum, er;
+        two_sum_f(hh.x, hh.y, sum, er);
+        h[r] = sum;
+        l[r] = ll.x + (ll.y + er);
+      }
+      // transposed butterfly: at width w each lane keeps half of its rows and adds the
+      // partner's copy of them, until one row per lane group remains
+      const int lane = tid & 31;
+      int nrow = RB, w = 16;
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        if (nrow > 1) {
+          const bool upper = (lane & w) != 0;
+          const int half = nrow / 2;
+#pragma unroll
+          for (int j = 0; j < RB / 2; ++j) {
+            if (j < half) {
+              const float sh = upper ? h[j] : h[j + half];   // rows the partner keeps
+              const float sl = upper ? l[j] : l[j + half];
+              const float kh = upper ? h[j + half] : h[j];   // rows this lane keeps
+              const float kl = upper ? l[j + half] : l[j];
+              const float oh = __shfl_xor_sync(0xffffffffu, sh, w);
+              const float ol = __shfl_xor_sync(0xffffffffu, sl, w);
+              float sum, er;
+              two_sum_f(kh, oh, sum, er);
+              h[j] = sum;
+              l[j] = kl + (ol + er);
+            }
+          }
+          nrow = half;
+        } else {
+          const float oh = __shfl_xor_sync(0xffffffffu, h[0], w);
+          const float ol = __shfl_xor_sync(0xffffffffu, l[0], w);
           float sum, er;
-          two_sum_f(h, oh, sum, er);
-          h = sum;
-          l += ol + er;
+          two_sum_f(h[0], oh, sum, er);
+          h[0] = sum;
+          l[0] = l[0] + (ol + er);
         }
-        if ((tid & 31) == 0) {
-          redh[par][r][tid >> 5] = h;
-          redl[par][r][tid >> 5] = l;
-        }
+        w >>= 1;
+      }
+      // lane groups of 32 / RB lanes hold row r = lane / (32 / RB)
+      if ((lane & (32 / RB - 1)) == 0) {
+        const int r = lane / (32 / RB);
+        redh[par][r][tid >> 5] = h[0];
+        redl[par][r][tid >> 5] = l[0];
       }
     }
     __threadfence_block();

@@ -18,8 +18,9 @@
 // Operands are split into digit planes in global memory one segment of rows at
 // a time (K-major, bf16; the digits of X are cut from its 64-bit fixed-point
 // form with integer shifts), then a 128 x 64 output tile per CTA streams them
-// through a two-stage shared-memory ring into tcgen05.mma (M=128, N=64, K=16,
-// FP32 accumulators in TMEM, 8 x 64 columns).  The planes are stored as
+// through a two-stage shared-memory ring into tcgen05.mma (M=128, K=16, FP32
+// accumulators in TMEM, 8 groups x 64 columns; four MMAs per K-step, N = 256,
+// 256, 256 and 192, each spanning the consecutive groups of four digit tiles).  The planes are stored as
 // pre-swizzled tiles, so each stage is ten contiguous bulk copies
 // (cp.async.bulk with mbarrier transaction counts).
 #include <cuda_bf16.h>
@@ -240,7 +241,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t idesc = instr_desc(TC_M, TC_N);
+  // The digit tiles d_1..d_8 lie back to back (64 rows of 128 bytes each), so
+  // d_1..d_4 and d_5..d_8 are each one K-major 256-row operand: one MMA with
+  // N = 256 covers four groups at once (TMEM column 64 g holds group g).
+  constexpr uint32_t idesc256 = instr_desc(TC_M, 4 * TC_N);
+  constexpr uint32_t idesc192 = instr_desc(TC_M, 3 * TC_N);
 
   // Exact column sums: group sums S_g (integers, |S_g| <= 2^24) of every chunk
   // go into two int64 accumulators per column,
@@ -295,19 +300,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
         const uint64_t d_ah = smem_desc(smem_addr(smem + st * STAGE_BYTES));
         const uint64_t d_al = d_ah + (TILE_A_BYTES >> 4);
         const uint64_t d_b = d_al + (TILE_A_BYTES >> 4);
+        const uint64_t d_b5 = d_b + (uint64_t)(4 * (TILE_B_BYTES >> 4));
 #pragma unroll
         for (int ks = 0; ks < TC_KT / 16; ++ks) {
           const uint32_t acc0 = (k == kt && ks == 0) ? 0u : 1u;
-          // eight MMAs into eight different accumulators, then seven more:
-          // consecutive MMAs never wait on each other's TMEM result
-#pragma unroll
-          for (int g = 0; g < TC_GROUPS; ++g)
-            mma_bf16(tmem + (uint32_t)(g * TC_N), d_ah + 2 * ks,
-                     d_b + (uint64_t)(g * (TILE_B_BYTES >> 4)) + 2 * ks, idesc, acc0);
-#pragma unroll
-          for (int g = 1; g < TC_GROUPS; ++g)
-            mma_bf16(tmem + (uint32_t)(g * TC_N), d_al + 2 * ks,
-                     d_b + (uint64_t)((g - 1) * (TILE_B_BYTES >> 4)) + 2 * ks, idesc, 1u);
+          // h d_{g+1} into groups 0-3 and 4-7 (these start a chunk's sums),
+          // then g_lo d_g into groups 1-4 and 5-7 (g_lo d_8 is dropped)
+          mma_bf16(tmem, d_ah + 2 * ks, d_b + 2 * ks, idesc256, acc0);
+          mma_bf16(tmem + (uint32_t)(4 * TC_N), d_ah + 2 * ks, d_b5 + 2 * ks, idesc256, acc0);
+          mma_bf16(tmem + (uint32_t)TC_N, d_al + 2 * ks, d_b + 2 * ks, idesc256, 1u);
+          mma_bf16(tmem + (uint32_t)(5 * TC_N), d_al + 2 * ks, d_b5 + 2 * ks, idesc192, 1u);
         }
         mma_commit(&empty[st]);
         consumed = k + 1;
