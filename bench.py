@@ -147,7 +147,7 @@ class ClockSampler:
 # CPU baseline: the oracle on bounded samples                                  #
 # --------------------------------------------------------------------------- #
 SAMPLE_ROWS = 10_000          # rows of A in the timed sketch sample (reference arm, per step)
-SAMPLE_SVD_N = 240            # columns of the timed Jacobi SVD sample (reference arm, per step)
+SAMPLE_SVD_N = 480            # columns of the timed Jacobi SVD sample (reference arm, per step)
 BASELINE_ROW_FRAC = 0.1       # cpu_baseline (once per run): a tenth of the rows ...
 BASELINE_SVD_N = 800          # ... and the Jacobi SVD at 2/5 of the columns (x15.6 by the n^3 law)
 
