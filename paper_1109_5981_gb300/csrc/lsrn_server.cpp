@@ -71,9 +71,11 @@ size_t estimate_bytes(const lsrn_matrix& A, const lsrn_options& o) {
 }
 
 // Continuous batching of the preconditioner phase: workers that reach it hand
-// their sketched plan over; the batcher packs every plan waiting at that
-// moment (after a short gathering window) into one launch of the batched
-// preconditioner kernel, then releases the workers into their iterations.
+// their sketched plan over; the batcher packs the plans into one launch of the
+// batched preconditioner kernel, then releases the workers into their
+// iterations.  A worker announces an eligible plan before its sketch
+// (expect), so after the first arrival the batcher waits, up to kGatherMs,
+// until every announced plan has arrived; then it packs all waiting plans.
 struct PrecondBatcher {
   struct Item {
     lsrn::Plan* plan;
@@ -87,6 +89,16 @@ struct PrecondBatcher {
   int device = 0;
   std::vector<std::thread> th;   // several batchers: a long batch does not hold up the next
   uint64_t batches = 0, packed = 0;
+  int expecting = 0;             // announced plans still sketching
+  static constexpr int kGatherMs = 2;
+
+  void expect(int d) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      expecting += d;
+    }
+    cv.notify_all();
+  }
 
   void run() {
     cudaSetDevice(device);
@@ -96,9 +108,9 @@ struct PrecondBatcher {
         std::unique_lock<std::mutex> lk(mu);
         cv.wait(lk, [&] { return stop || !pending.empty(); });
         if (pending.empty()) return;   // stopping with nothing left
-        lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(200));   // let others arrive
-        lk.lock();
+        // gather: the announced plans still sketching, for at most kGatherMs
+        cv.wait_for(lk, std::chrono::milliseconds(kGatherMs), [&] { return stop || expecting <= 0; });
+        if (pending.empty()) continue;   // another batcher took them meanwhile
         batch.assign(pending.begin(), pending.end());
         pending.clear();
       }
@@ -119,9 +131,11 @@ struct PrecondBatcher {
     }
   }
 
+  // The plan must have been announced with expect(+1).
   lsrn_status submit(lsrn::Plan* p) {
     Item it{p, LSRN_OK, false};
     std::unique_lock<std::mutex> lk(mu);
+    --expecting;
     pending.push_back(&it);
     cv.notify_all();
     cv.wait(lk, [&] { return it.done; });
@@ -186,9 +200,12 @@ struct lsrn_server_s {
         const int bq = batch_max_q.load();
         if (bq > 0 && lsrn::plan_short_side(plan) <= bq &&
             lsrn::batch_precond_applies(lsrn::plan_short_side(plan))) {
+          batcher.expect(+1);
           s = lsrn_sketch(plan);
           if (s == LSRN_OK && lsrn::precond_batchable(lsrn::plan_internal(plan)))
             s = batcher.submit(lsrn::plan_internal(plan));
+          else
+            batcher.expect(-1);   // not coming: the batcher stops waiting for it
         }
       }
       if (s == LSRN_OK) {
