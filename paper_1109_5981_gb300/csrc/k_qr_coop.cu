@@ -244,14 +244,12 @@ __global__ void __launch_bounds__(kCqThreads, 1) qr_coop_kernel(CoopQr a) {
   }
 }
 
-// One cooperative grid (this QR or the Jacobi sweeps of k_svd.cu) at a time in
-// this process: plans of a server or a batch run on several streams, and two
-// partly resident grids could each hold SMs that the other's waiting CTAs need.
+// One cooperative grid at a time in this process: plans of a server or a
+// batch run on several streams, and two partly resident grids could each hold
+// SMs that the other's waiting CTAs need.
 std::mutex g_coop_mutex;
 
 }  // namespace
-
-std::mutex& coop_launch_mutex() { return g_coop_mutex; }
 
 // Cooperative QR of X (S x Q row-major, in place).  Returns LSRN_OK with *ran
 // false, and nothing launched, when the device cannot hold the grid (then the
@@ -274,6 +272,11 @@ lsrn_status launch_qr_coop(double* X, int64_t S, int64_t Q, double* tau, cudaStr
   LSRN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, kCqThreads, smem));
   const int grid = CB * kCqRG;
   if (per_sm < 1 || grid > per_sm * nsm) return LSRN_OK;
+  // the sketch is done before the lock is tried; a plan that finds another
+  // plan's grid running takes the per-column kernels instead of waiting
+  LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+  std::unique_lock<std::mutex> lock(g_coop_mutex, std::try_to_lock);   // until the grid has finished
+  if (!lock.owns_lock()) return LSRN_OK;
   double* ws = nullptr;
   const size_t wbytes = ((size_t)kCqRG + (size_t)kCqRG * Q) * sizeof(double) + 4 * sizeof(int);
   LSRN_CUDA_TRY(lsrn_malloc_async((void**)&ws, wbytes, st));
@@ -288,11 +291,8 @@ lsrn_status launch_qr_coop(double* X, int64_t S, int64_t Q, double* tau, cudaStr
   a.err = (int*)(a.bar + 2);
   a.wait_ns = kCqWaitNs;
   lsrn_status rs = LSRN_OK;
-  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(int), st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)   // the sketch is done before the lock is taken
-    rs = LSRN_ERR_CUDA;
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(int), st) != cudaSuccess) rs = LSRN_ERR_CUDA;
   void* args[] = {(void*)&a};
-  std::lock_guard<std::mutex> lock(g_coop_mutex);   // held until the grid has finished
   if (rs == LSRN_OK &&
       cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(grid), dim3(kCqThreads), args, smem,
                                   st) != cudaSuccess)

@@ -677,164 +677,6 @@ __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
   }
 }
 
-// ---- all sweeps in one cooperative launch (q <= 1024) ----
-// At small q a round is a few microseconds of work, and one launch per round
-// (from a graph) costs more than the work.  Here a grid of co-resident CTAs
-// runs every sweep: exact squared norms, then the P - 1 rounds, each CTA taking
-// pairs pr = blockIdx.x (mod grid) of the round, with a grid barrier after the
-// norms and after every round.  The pairs, their order and their arithmetic
-// are those of jacobi_pair_kernel, so the result is the same bit for bit.
-// Rows and norms written by other CTAs are read through L2 (ld.global.cg).
-// ws: [0] barrier count, [1] barrier generation, [2] error flag, [3] sweeps
-// run, [4 + s] rotation flag of sweep s (zero at launch).
-__device__ __forceinline__ unsigned jc_ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void jc_st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid barrier bounded by wait_ns of global time; false once the error flag is up.
-__device__ bool jc_grid_sync(unsigned* ws, unsigned& gen, uint64_t wait_ns, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    int* err = (int*)(ws + 2);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&ws[0], 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&ws[0], 0u);
-      __threadfence();
-      jc_st_release(&ws[1], gen + 1);
-    } else {
-      const uint64_t t0 = globaltimer_ns();
-      for (int it = 0;; ++it) {
-        if (jc_ld_acquire(&ws[1]) != gen) break;
-        if ((it & 15) == 15 && (globaltimer_ns() - t0 > wait_ns || ld_acquire_gpu(err) != 0)) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    *s_ok = ok && ld_acquire_gpu((int*)(ws + 2)) == 0;
-  }
-  __syncthreads();
-  ++gen;
-  return *s_ok != 0;
-}
-
-template <int EPT>
-__global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(double* __restrict__ W, int64_t Q,
-                                                                  int P, double tol,
-                                                                  double* __restrict__ nrm2,
-                                                                  unsigned* __restrict__ ws,
-                                                                  int max_sweeps, uint64_t wait_ns) {
-  __shared__ double sh[kJacThreads / 32];
-  __shared__ double rot[3];
-  __shared__ int s_ok;
-  unsigned gen = 0;
-  int* rotflag = (int*)(ws + 4);
-  int sweeps = 0;
-  for (int sw = 0; sw < max_sweeps; ++sw) {
-    // exact squared norms, a warp per row (the order of row_sqnorms_kernel)
-    {
-      const int lane = threadIdx.x & 31, nw = kJacThreads / 32;
-      for (int64_t r = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); r < Q; r += (int64_t)gridDim.x * nw) {
-        double acc = 0.0;
-        for (int64_t c = lane; c < Q; c += 32) {
-          const double x = __ldcg(W + r * Q + c);
-          acc = fma(x, x, acc);
-        }
-        acc = group_sum<32>(acc);
-        if (lane == 0) nrm2[r] = acc;
-      }
-    }
-    if (!jc_grid_sync(ws, gen, wait_ns, &s_ok)) return;
-    for (int t = 0; t < P - 1; ++t) {
-      for (int pr = blockIdx.x; pr < P / 2; pr += gridDim.x) {
-        int a = pr == 0 ? P - 1 : (t + pr) % (P - 1);
-        int b = pr == 0 ? t : (t - pr + P - 1) % (P - 1);
-        if (a >= Q || b >= Q) continue;   // uniform in the CTA
-        if (a > b) {
-          const int tmp = a;
-          a = b;
-          b = tmp;
-        }
-        double* wa = W + (int64_t)a * Q;
-        double* wb = W + (int64_t)b * Q;
-        const double aa = __ldcg(nrm2 + a), bb = __ldcg(nrm2 + b);
-        double x[EPT], y[EPT];
-        double ab = 0.0;
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-          const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
-          x[e] = c < Q ? __ldcg(wa + c) : 0.0;
-          y[e] = c < Q ? __ldcg(wb + c) : 0.0;
-          ab = fma(x[e], y[e], ab);
-        }
-        ab = jac_block_sum(ab, sh);
-        if (aa == 0.0 || bb == 0.0) continue;   // uniform
-        if (threadIdx.x == 0) {
-          double tt = 0.0, cs = 1.0;
-          if (fabs(ab) > tol * sqrt(aa) * sqrt(bb)) {
-            const double zeta = (bb - aa) / (2.0 * ab);
-            if (fabs(zeta) > 1e150) {
-              tt = 0.5 / zeta;
-            } else {
-              tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            }
-            cs = 1.0 / sqrt(1.0 + tt * tt);
-          }
-          rot[0] = tt;
-          rot[1] = cs;
-          rot[2] = cs * tt;
-        }
-        __syncthreads();
-        const double tt = rot[0], cs = rot[1], sn = rot[2];
-        __syncthreads();   // rot is rewritten by the CTA's next pair
-        if (tt == 0.0) continue;   // uniform
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-          const int64_t c = threadIdx.x + (int64_t)kJacThreads * e;
-          const double xa = cs * x[e] - sn * y[e];
-          const double yb = sn * x[e] + cs * y[e];
-          x[e] = xa;
-          y[e] = yb;
-          if (c < Q) {
-            wa[c] = xa;
-            wb[c] = yb;
-          }
-        }
-        double na = aa - tt * ab, nb = bb + tt * ab;
-        if (na < 0.25 * aa || nb < 0.25 * bb) {   // uniform
-          double sa = 0.0, sb = 0.0;
-#pragma unroll
-          for (int e = 0; e < EPT; ++e) {
-            sa = fma(x[e], x[e], sa);
-            sb = fma(y[e], y[e], sb);
-          }
-          na = jac_block_sum(sa, sh);
-          nb = jac_block_sum(sb, sh);
-        }
-        if (threadIdx.x == 0) {
-          nrm2[a] = na;
-          nrm2[b] = nb;
-          rotflag[sw] = 1;
-        }
-      }
-      if (!jc_grid_sync(ws, gen, wait_ns, &s_ok)) return;
-    }
-    ++sweeps;
-    if (ld_acquire_gpu(rotflag + sw) == 0) break;   // read after the barrier: the same in every CTA
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) ws[3] = (unsigned)sweeps;
-}
-
 __global__ void set_int_kernel(int* __restrict__ p, int v) { *p = v; }
 
 __global__ void row_sqnorms_kernel(const double* __restrict__ W, int64_t Q, double* __restrict__ nrm2) {
@@ -953,56 +795,6 @@ __global__ void __launch_bounds__(1024) min_abs_diag_kernel(const double* __rest
 
 }  // namespace
 
-// All sweeps of the q <= 1024 Jacobi in one cooperative launch (jacobi_coop_kernel).
-// *ran is false, with nothing launched, when the device cannot hold the grid.
-static lsrn_status launch_jacobi_coop(Plan* p, int ept, int P, double tol, double* nrm2, int max_sweeps,
-                                      uint64_t wait_ns, bool* ran, int* sweeps, bool* converged) {
-  *ran = false;
-  cudaStream_t st = p->stream;
-  const int64_t Q = p->q;
-  int dev = 0, coop = 0, per_sm = 0;
-  LSRN_CUDA_TRY(cudaGetDevice(&dev));
-  LSRN_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop || (ept != 4 && ept != 8)) return LSRN_OK;
-  const void* kern = ept == 4 ? (const void*)jacobi_coop_kernel<4> : (const void*)jacobi_coop_kernel<8>;
-  if (ept == 4)
-    LSRN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<4>, kJacThreads, 0));
-  else
-    LSRN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<8>, kJacThreads, 0));
-  const int grid = (int)std::min<int64_t>(P / 2, (int64_t)per_sm * num_sms());
-  if (grid < 1) return LSRN_OK;
-  unsigned* ws = nullptr;
-  const size_t wbytes = (size_t)(4 + max_sweeps + 1) * sizeof(unsigned);
-  LSRN_CUDA_TRY(lsrn_malloc_async((void**)&ws, wbytes, st));
-  lsrn_status rs = LSRN_OK;
-  if (cudaMemsetAsync(ws, 0, wbytes, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
-    rs = LSRN_ERR_CUDA;
-  std::vector<unsigned> h((size_t)(4 + max_sweeps + 1), 0u);
-  if (rs == LSRN_OK) {
-    double* W = p->Wj;
-    int64_t q = Q;
-    void* args[] = {(void*)&W, (void*)&q, (void*)&P, (void*)&tol, (void*)&nrm2, (void*)&ws,
-                    (void*)&max_sweeps, (void*)&wait_ns};
-    std::lock_guard<std::mutex> lock(coop_launch_mutex());   // until the grid has finished
-    if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kJacThreads), args, 0, st) != cudaSuccess) {
-      rs = LSRN_ERR_CUDA;
-    } else {
-      g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-      if (cudaMemcpyAsync(h.data(), ws, wbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        rs = LSRN_ERR_CUDA;
-    }
-  }
-  cudaGetLastError();
-  cudaFreeAsync(ws, st);
-  if (rs != LSRN_OK) return rs;
-  *ran = true;
-  if (h[2] != 0) return LSRN_ERR_TIMEOUT;
-  *sweeps = (int)h[3];
-  *converged = *sweeps >= 1 && *sweeps <= max_sweeps && h[4 + *sweeps - 1] == 0;
-  return LSRN_OK;
-}
-
 lsrn_status run_precond(Plan* p, bool bf16_check) {
   cudaStream_t st = p->stream;
   const int64_t S = p->s, Q = p->q;
@@ -1015,14 +807,15 @@ lsrn_status run_precond(Plan* p, bool bf16_check) {
     LSRN_CUDA_TRY(cudaStreamSynchronize(st));
     p->bf16_noise = 0x1p-8 * std::sqrt(f2 / (double)std::max<int64_t>(Q, 1));
   }
-  // 1. Householder QR.  Up to kQrBlockedMin columns one column at a time: all
-  // columns in one cooperative launch with two grid barriers per column, or
-  // (where the device cannot hold that grid) three launches per column, the
-  // trailing update spread over the whole GPU; beyond kQrBlockedMin in panels
-  // of kQrNb columns, where the O(S q^2) trailing work runs as a blocked
-  // rank-32 update and the serial panel factorizations are a small part.
+  // 1. Householder QR, one column at a time: all columns in one cooperative
+  // launch with two grid barriers per column (k_qr_coop.cu).  Where the device
+  // cannot hold that grid (or the sketch is taller than its shared-memory
+  // limit): up to kQrBlockedMin columns three launches per column, the
+  // trailing update spread over the whole GPU; beyond that in panels of kQrNb
+  // columns, where the O(S q^2) trailing work runs as a blocked rank-32 update
+  // and the serial panel factorizations are a small part.
   bool coop = false;
-  if (Q <= kQrBlockedMin) LSRN_TRY(launch_qr_coop(X, S, Q, p->tau, st, &coop));
+  LSRN_TRY(launch_qr_coop(X, S, Q, p->tau, st, &coop));
   if (coop) {
     // done in one cooperative launch (k_qr_coop.cu)
   } else if (Q <= kQrBlockedMin) {
@@ -1181,14 +974,7 @@ lsrn_status run_precond(Plan* p, bool bf16_check) {
       }
     }
   };
-  bool coop_done = false;
-  if (P > 1 && !flow && (ept == 4 || ept == 8)) {
-    bool conv = false;
-    const uint64_t cwait = knob_wait > 0 ? (uint64_t)knob_wait : 10ull * kJacWaitNs;
-    LSRN_TRY(launch_jacobi_coop(p, ept, P, tol, nrm2, max_sweeps, cwait, &coop_done, &sweeps, &conv));
-    if (coop_done) host_rot = conv ? 0 : 1;
-  }
-  if (P > 1 && !coop_done) {
+  if (P > 1) {
     // The sweep is captured once into a CUDA graph and replayed for every
     // sweep: the same kernels with the same arguments, without the host
     // launch overhead of P - 1 rounds (about 2 us a round).  If the capture

@@ -5,7 +5,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -289,8 +288,6 @@ lsrn_status run_precond(Plan* p, bool bf16_check = false);
 // Householder QR of X (S x Q, row-major, in place) in one cooperative launch
 // (k_qr_coop.cu); *ran is false when the device cannot hold the grid.
 lsrn_status launch_qr_coop(double* X, int64_t S, int64_t Q, double* tau, cudaStream_t st, bool* ran);
-// Held around every cooperative launch of the library, until its grid is done.
-std::mutex& coop_launch_mutex();
 // Double-float Jacobi pre-sweeps on R (k_jacobi_df.cu): for 1024 < q <= 4096,
 // leaves Y = P R (P the accumulated rotations) in p->Wj for the FP64 sweeps.
 bool jacobi_df_applies(int64_t Q);
