@@ -474,13 +474,21 @@ lsrn_status lsrn_sketch_f64_noalloc(const double* A, int64_t m, int64_t n, int64
  *                                     waits on rows that are never published
  *                                     and the sweep's bounded wait runs out:
  *                                     lsrn_precond returns LSRN_ERR_TIMEOUT.
+ *   LSRN_KNOB_QR_ABSENT_CTA           != 0: one CTA of the cooperative QR
+ *                                     leaves before its first grid barrier,
+ *                                     so the others' bounded barrier waits
+ *                                     run out (limited by
+ *                                     LSRN_KNOB_JACOBI_WAIT_NS when that is
+ *                                     set, else ten seconds): lsrn_precond
+ *                                     returns LSRN_ERR_TIMEOUT.
  * A preconditioner that fails leaves the plan needing a new sketch (the QR
  * overwrites the sketch in place); lsrn_solve_* redoes it by itself.
  * INVALID_ARG for an unknown knob or a negative value. */
 typedef enum {
   LSRN_KNOB_JACOBI_WAIT_NS = 0,
   LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 1,
-  LSRN_KNOB_COUNT = 2
+  LSRN_KNOB_QR_ABSENT_CTA = 2,
+  LSRN_KNOB_COUNT = 3
 } lsrn_test_knob;
 lsrn_status lsrn_set_test_knob(int32_t knob, int64_t value);
 

@@ -38,7 +38,7 @@ LSRN_DENSE_ROWMAJOR, LSRN_DENSE_COLMAJOR, LSRN_CSR = 0, 1, 2
 LSRN_F64, LSRN_F32 = 0, 1
 LSRN_SKETCH_F64, LSRN_SKETCH_TC_SLICED, LSRN_SKETCH_BF16, LSRN_SKETCH_AUTO = 0, 1, 2, 3
 LSRN_ITER_F64, LSRN_ITER_F32, LSRN_ITER_F32X2, LSRN_ITER_AUTO = 0, 1, 2, 3
-LSRN_KNOB_JACOBI_WAIT_NS, LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND = 0, 1
+LSRN_KNOB_JACOBI_WAIT_NS, LSRN_KNOB_JACOBI_SKIP_FIRST_ROUND, LSRN_KNOB_QR_ABSENT_CTA = 0, 1, 2
 LSRN_PRECOND_SVD, LSRN_PRECOND_QR = 0, 1
 LSRN_SVD_F64, LSRN_SVD_DF = 0, 1
 

@@ -112,6 +112,7 @@ struct CoopQr {
   unsigned* bar;   // [2], zero at launch
   int* err;
   uint64_t wait_ns;
+  int absent;      // test knob: CTA 0 leaves before the first barrier
 };
 
 __global__ void __launch_bounds__(kCqThreads, 1) qr_coop_kernel(CoopQr a) {
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kCqThreads, 1) qr_coop_kernel(CoopQr a) {
   };
 
   if (Q > 0 && owns_col(0)) norm_partial(0);
+  if (a.absent && blockIdx.x == 0) return;   // the others' first barrier wait runs out
   if (!cq_grid_sync(a.bar, gen, a.err, a.wait_ns, &s_ok)) return;
 
   for (int64_t k = 0; k < Q; ++k) {
@@ -272,11 +274,11 @@ lsrn_status launch_qr_coop(double* X, int64_t S, int64_t Q, double* tau, cudaStr
   LSRN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, kCqThreads, smem));
   const int grid = CB * kCqRG;
   if (per_sm < 1 || grid > per_sm * nsm) return LSRN_OK;
-  // the sketch is done before the lock is tried; a plan that finds another
-  // plan's grid running takes the per-column kernels instead of waiting
+  // the sketch is done before the lock is taken; a plan that finds another
+  // plan's grid running waits for it (taking the per-column kernels instead
+  // would round differently, and a result must not depend on what else runs)
   LSRN_CUDA_TRY(cudaStreamSynchronize(st));
-  std::unique_lock<std::mutex> lock(g_coop_mutex, std::try_to_lock);   // until the grid has finished
-  if (!lock.owns_lock()) return LSRN_OK;
+  std::lock_guard<std::mutex> lock(g_coop_mutex);   // until the grid has finished
   double* ws = nullptr;
   const size_t wbytes = ((size_t)kCqRG + (size_t)kCqRG * Q) * sizeof(double) + 4 * sizeof(int);
   LSRN_CUDA_TRY(lsrn_malloc_async((void**)&ws, wbytes, st));
@@ -289,7 +291,9 @@ lsrn_status launch_qr_coop(double* X, int64_t S, int64_t Q, double* tau, cudaStr
   a.wpart = ws + kCqRG;
   a.bar = (unsigned*)(ws + kCqRG + (size_t)kCqRG * Q);
   a.err = (int*)(a.bar + 2);
-  a.wait_ns = kCqWaitNs;
+  a.absent = test_knob(LSRN_KNOB_QR_ABSENT_CTA) != 0 ? 1 : 0;
+  const int64_t knob_wait = test_knob(LSRN_KNOB_JACOBI_WAIT_NS);
+  a.wait_ns = (a.absent && knob_wait > 0) ? (uint64_t)knob_wait : kCqWaitNs;
   lsrn_status rs = LSRN_OK;
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(int), st) != cudaSuccess) rs = LSRN_ERR_CUDA;
   void* args[] = {(void*)&a};

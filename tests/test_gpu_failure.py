@@ -63,3 +63,31 @@ def test_test_knobs_reject_bad_arguments():
     with pytest.raises(L.LsrnError) as e:
         L.lsrn_set_test_knob(L.LSRN_KNOB_JACOBI_WAIT_NS, -5)
     assert e.value.status == L.LSRN_ERR_INVALID_ARG
+
+
+def test_cooperative_qr_barrier_wait_runs_out_then_the_plan_recovers():
+    # one CTA of the cooperative QR leaves before the first grid barrier; the
+    # others wait 2 ms of global time, raise the flag and return
+    P = W.dense_haar(3000, 400, 380, 1e4, 1e-3, seed=6)
+    A = torch.from_numpy(P.A).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    plan = L.lsrn_plan(A, L.default_options(seed=4))
+    try:
+        L.lsrn_sketch(plan)
+        L.lsrn_set_test_knob(L.LSRN_KNOB_JACOBI_WAIT_NS, 2_000_000)
+        L.lsrn_set_test_knob(L.LSRN_KNOB_QR_ABSENT_CTA, 1)
+        t0 = time.perf_counter()
+        try:
+            with pytest.raises(L.LsrnError) as e:
+                L.lsrn_precond(plan)
+        finally:
+            L.lsrn_set_test_knob(L.LSRN_KNOB_JACOBI_WAIT_NS, 0)
+            L.lsrn_set_test_knob(L.LSRN_KNOB_QR_ABSENT_CTA, 0)
+        assert e.value.status == L.LSRN_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 10.0
+        x, info = L.lsrn_solve_lsqr(plan, b)
+    finally:
+        plan.close()
+    assert info["rank"] == 380
+    xs, _ = O.minlen_refined(P.A, P.b)
+    assert O.rel_err(x.cpu().numpy(), xs) <= 1e-10
