@@ -549,7 +549,7 @@ __device__ __forceinline__ void named_arrive(int id, int n) {
 // then warps 0-7 accumulate stage k - 1.  The FP64 row update is thus off the
 // compute warps' critical path.
 template <int SLOTS, int RB>
-__global__ void __launch_bounds__(kX2Threads, (RB == 2 && SLOTS <= 4) ? 2 : 1) row_pass_x2_kernel(
+__global__ void __launch_bounds__(kX2Threads, (RB == 2 && SLOTS <= 4) ? 3 : 1) row_pass_x2_kernel(
     const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t rows, int C, int64_t ldx,
     double xs, const double* __restrict__ vin, RowArgs args, double* __restrict__ pvec,
     double* __restrict__ pscal, const int* __restrict__ done, int* __restrict__ err, int rowbytes,
@@ -1512,8 +1512,8 @@ int pass_blocks(int64_t rows, int64_t C, bool x2) {
   int tpr, slots;
   if (pick_layout(C, &tpr, &slots) != 0) return 0;
   if (pass_is_staged(C)) {
-    // double-float passes up to 2048 columns: two CTAs per SM (x2_geometry)
-    const int per_sm = (x2 && C <= 2048) ? 2 : 1;
+    // double-float passes up to 2048 columns: three CTAs per SM (x2_geometry)
+    const int per_sm = (x2 && C <= 2048) ? 3 : 1;
     return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * num_sms(), rows));
   }
   const int64_t gpc = kThreads / tpr;
@@ -1560,18 +1560,19 @@ static lsrn_status launch_staged(const Plan* p, const T* X, int64_t ldx, const d
 }
 
 // Geometry of the double-float pass: RB = 2 rows of both planes per stage.  Up
-// to 2048 columns three stages (96 KB), so that two CTAs share an SM: twice the
-// warps to hide the latency of the dependent double-float chains (4-row stages
-// with one CTA per SM streamed at 0.40 of HBM, this at 0.47).  Above 2048
-// columns as many stages as fit in 196 KB (at most 8), one CTA per SM.
+// to 2048 columns two stages (64 KB), so that three CTAs share an SM: three
+// times the warps of one CTA to hide the latency of the dependent double-float
+// chains (4-row stages with one CTA per SM streamed at 0.40 of HBM, two CTAs
+// of three stages at 0.50, three of two at 0.51).  Above 2048 columns as many
+// stages as fit in 196 KB (at most 8), one CTA per SM.
 static bool x2_geometry(int64_t C, int64_t ldx2, int* planebytes, int* rb, int* nstages) {
   if (C <= 512 || C > 4096) return false;
   const int64_t pbytes = (C * 4 + 15) / 16 * 16;
   if (pbytes > ldx2 * 4 || (ldx2 * 4) % 16 != 0) return false;
   const int r = 2;
   const int64_t stage = 2 * r * pbytes + 2 * r * 8;
-  const int ns = C <= 2048 ? 3 : (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / stage);
-  if (ns < 3) return false;
+  const int ns = C <= 2048 ? 2 : (int)std::min<int64_t>(kMaxStages, (196608 - 1024) / stage);
+  if (ns < 2) return false;
   *planebytes = (int)pbytes;
   *rb = r;
   *nstages = ns;
