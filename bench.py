@@ -223,7 +223,7 @@ def kernel_source_hash(src_file: str, name: str) -> str:
 
 KERNEL_SOURCES = {"row_pass_x2_kernel": "k_iter.cu", "dd_pass_x3_kernel": "k_iter.cu",
                   "sketch_tc_kernel": "k_sketch_tc.cu", "jacobi_pair_kernel": "k_svd.cu",
-                  "jacobi_flow_kernel": "k_svd.cu"}
+                  "jacobi_flow_kernel": "k_svd.cu", "qr_coop_kernel": "k_qr_coop.cu"}
 
 
 def traffic_per_unit(kernel: str):
@@ -608,6 +608,8 @@ def traffic_for(phase: str, args, m_local: int):
     if phase == "svd":
         tpu = traffic_per_unit("jacobi_flow_kernel")
         return None if tpu is None else tpu
+    if phase == "qr" and args.n == 2000 and math.ceil(2.0 * args.n) == 4000:
+        return traffic_per_unit("qr_coop_kernel")   # captured for the 4000 x 2000 sketch
     return None
 
 

@@ -4,9 +4,10 @@
 // The column-at-a-time QR issues three kernels per column (reflector, w = v^T C,
 // C -= tau v w^T).  Each of them is small, so at q = 2000 the 6000 launches
 // cost ~65 us a column against ~10 us of FP64 work.  Here one persistent grid
-// of one CTA per SM runs all columns, with two grid-wide barriers per column
-// (the CTAs wait on one another, so the launch is cooperative: all are
-// resident at once).  The same reflectors as the per-column kernels:
+// of one CTA per SM (two from q = 1024 on) runs all columns, with two
+// grid-wide barriers per column (the CTAs wait on one another, so the launch
+// is cooperative: all are resident at once).  The same reflectors as the
+// per-column kernels:
 //   alpha = X[k, k], t = sum_{i > k} X[i, k]^2, beta = -sign(alpha) sqrt(alpha^2 + t),
 //   tau = (beta - alpha) / beta, v_k = 1, v_i = X[i, k] / (alpha - beta) (i > k),
 //   w_c = sum_{i >= k} v_i X[i, c], X[i, c] -= tau v_i w_c for c > k;
@@ -115,7 +116,7 @@ struct CoopQr {
   int absent;      // test knob: CTA 0 leaves before the first barrier
 };
 
-__global__ void __launch_bounds__(kCqThreads, 1) qr_coop_kernel(CoopQr a) {
+__global__ void __launch_bounds__(kCqThreads, 2) qr_coop_kernel(CoopQr a) {
   extern __shared__ double vbuf[];   // v for this CTA's rows (row t: i = rg + 8 t)
   __shared__ double red[kCqThreads / 32];
   __shared__ double part[kCqThreads / 32][kCqChunk];
@@ -264,7 +265,9 @@ lsrn_status launch_qr_coop(double* X, int64_t S, int64_t Q, double* tau, cudaStr
   LSRN_CUDA_TRY(cudaGetDevice(&dev));
   LSRN_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   const int nsm = num_sms();
-  const int CB = nsm / kCqRG;
+  // two CTAs per SM from q = 1024 on (59 vs 66 ms at q = 2000); at smaller q
+  // the wider barrier costs more than the extra warps give
+  const int CB = (Q >= 1024 ? 2 : 1) * nsm / kCqRG;
   const size_t smem = (size_t)((S + kCqRG - 1) / kCqRG) * sizeof(double);
   if (!coop || CB < 1 || smem > (size_t)kCqMaxSmem) return LSRN_OK;
   // one fixed limit: plans on other threads set it too, and a per-call value

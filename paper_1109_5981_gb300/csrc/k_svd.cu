@@ -432,6 +432,22 @@ __device__ __forceinline__ double jac_block_sum(double v, double* sh) {
   return t;
 }
 
+// The same sum, valid in thread 0 only (the other threads do not add up the
+// warp partials: on GB300 every warp-wide FP64 instruction costs 16 cycles of
+// the SM's FP64 pipe).
+__device__ __forceinline__ double jac_block_sum0(double v, double* sh) {
+  v = group_sum<32>(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < kJacThreads / 32; ++q) t += sh[q];
+  }
+  return t;
+}
+
 template <int EPT>
 __global__ void __launch_bounds__(kJacThreads) jacobi_pair_kernel(double* __restrict__ W, int64_t Q,
                                                                   int P, int t, double tol,
@@ -556,6 +572,7 @@ __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
                        int* __restrict__ ws, uint64_t wait_ns) {
   __shared__ double sh[kJacThreads / 32];
   __shared__ double rot[3];
+  __shared__ int s_rec;
   __shared__ int s_item, s_ok;
   int* next = ws;
   int* err = ws + 1;
@@ -620,21 +637,28 @@ __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
       y[e] = c < Q ? __ldcg(wb + c) : 0.0;
       ab = fma(x[e], y[e], ab);
     }
-    ab = jac_block_sum(ab, sh);
+    ab = jac_block_sum0(ab, sh);   // thread 0 only
+    double na = aa, nb = bb;       // thread 0: the new squared norms
     if (threadIdx.x == 0) {
       double tt = 0.0, cs = 1.0;
-      if (aa != 0.0 && bb != 0.0 && fabs(ab) > tol * sqrt(aa) * sqrt(bb)) {
+      // |ab| > tol sqrt(aa bb): one square root where aa bb is a normal number
+      const double pab = aa * bb;
+      const double lim = (pab >= 0x1p-1000 && pab <= 0x1p+1000) ? tol * sqrt(pab) : tol * sqrt(aa) * sqrt(bb);
+      if (aa != 0.0 && bb != 0.0 && fabs(ab) > lim) {
         const double zeta = (bb - aa) / (2.0 * ab);
         if (fabs(zeta) > 1e150) {
           tt = 0.5 / zeta;
         } else {
           tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         }
-        cs = 1.0 / sqrt(1.0 + tt * tt);
+        cs = rsqrt(1.0 + tt * tt);
       }
+      na = aa - tt * ab;
+      nb = bb + tt * ab;
       rot[0] = tt;
       rot[1] = cs;
       rot[2] = cs * tt;
+      s_rec = tt != 0.0 && (na < 0.25 * aa || nb < 0.25 * bb);
     }
     __syncthreads();
     const double tt = rot[0], cs = rot[1], sn = rot[2];
@@ -651,16 +675,19 @@ __global__ void __launch_bounds__(kJacThreads, EPT >= 32 ? 1 : 5)
           wb[c] = yb;
         }
       }
-      double na = aa - tt * ab, nb = bb + tt * ab;
-      if (na < 0.25 * aa || nb < 0.25 * bb) {   // uniform
+      if (s_rec) {   // uniform: cancellation, the rotated rows' norms
         double sa = 0.0, sb = 0.0;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
           sa = fma(x[e], x[e], sa);
           sb = fma(y[e], y[e], sb);
         }
-        na = jac_block_sum(sa, sh);
-        nb = jac_block_sum(sb, sh);
+        const double ra = jac_block_sum0(sa, sh);
+        const double rb = jac_block_sum0(sb, sh);
+        if (threadIdx.x == 0) {
+          na = ra;
+          nb = rb;
+        }
       }
       if (threadIdx.x == 0) {
         nrm2[a] = na;
