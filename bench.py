@@ -226,11 +226,15 @@ KERNEL_SOURCES = {"row_pass_x2_kernel": "k_iter.cu", "dd_pass_x3_kernel": "k_ite
                   "jacobi_flow_kernel": "k_svd.cu", "qr_coop_kernel": "k_qr_coop.cu"}
 
 
+# kernels whose body is a device function shared with another launch: hash the body
+HASHED_BODY = {"sketch_tc_kernel": "sketch_tc_tile"}
+
+
 def traffic_per_unit(kernel: str):
     """Bytes per unit from profiles/roofline_traffic.md if the kernel is unchanged, else None."""
     try:
         rows = open(os.path.join(ROOT, "profiles", "roofline_traffic.md")).read().splitlines()
-        cur = kernel_source_hash(KERNEL_SOURCES[kernel], kernel)
+        cur = kernel_source_hash(KERNEL_SOURCES[kernel], HASHED_BODY.get(kernel, kernel))
     except (OSError, KeyError, ValueError):
         return None
     for line in rows:

@@ -350,8 +350,10 @@ lsrn_status lsrn_choose_gamma(const lsrn_gamma_model* model, double* gamma, doub
  * and solver (0 = LSQR, 1 = CS), each exactly as lsrn_plan + lsrn_solve_* would
  * (Algorithm 1 or 2 per problem, by its own shape), but phase by phase over the
  * whole batch:
- *   - plans and sketches are issued for all problems from `threads` host threads
- *     (0: 8), each problem on its own stream, so the sketches overlap on the GPU;
+ *   - plans are made from `threads` host threads (0: 8); the sketches are those
+ *     of lsrn_sketch_group (the exact tensor-core sketches of small dense
+ *     problems grouped into shared launches, the others each on its own
+ *     stream, overlapping on the GPU);
  *   - the preconditioners of all problems whose short side is at most 128 and
  *     whose sketch is F64 or TC_SLICED run in ONE persistent launch, one CTA per
  *     problem (Householder QR, one-sided Jacobi, rank, N), largest first; other
@@ -367,6 +369,20 @@ lsrn_status lsrn_choose_gamma(const lsrn_gamma_model* model, double* gamma, doub
 lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* const* b,
                              double* const* x, const lsrn_options* opt, int32_t solver,
                              int32_t threads, lsrn_info* info, int32_t* status);
+
+/* Sketches (Algorithm 1/2 steps 2-3) of count plans at once, each with the
+ * result lsrn_sketch would give it, bit for bit.  Dense plans in
+ * LSRN_SKETCH_TC_SLICED mode whose long side fits one segment of the sketch's
+ * scratch (and that are neither ridge, sharded nor matrix-free) are grouped:
+ * their digit planes are prepared one after another on a stream of the call's
+ * own, then the output tiles of all of them run in one tensor-core launch (a
+ * tile table of (problem, row tile, column tile), the longest problems
+ * first), in chunks of at most 8 GiB of planes.  Every other plan is sketched
+ * by lsrn_sketch.  Each plan's stream waits for its sketch.  status: optional
+ * array of count statuses.  Returns LSRN_OK or the first failing status.
+ * INVALID_ARG: count < 0, plans NULL with count > 0, a NULL plan.
+ * Synchronises. */
+lsrn_status lsrn_sketch_group(int32_t count, lsrn_plan_t* plans, int32_t* status);
 
 /* ---- sharded solve (section 4.4: A partitioned over processes) ----
  * One plan per shard (a GPU, a process or a host thread).  A is split along its

@@ -135,6 +135,7 @@ _SIGS = {
     "lsrn_solve_batch": ([ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.POINTER(lsrn_options), ctypes.c_int32, ctypes.c_int32,
                           ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "lsrn_sketch_group": ([ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "lsrn_plan_set_lambda": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     "lsrn_choose_gamma": ([ctypes.POINTER(lsrn_gamma_model), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -443,6 +444,17 @@ def lsrn_solve_batch(problems, opt: Optional[lsrn_options] = None, solver: str =
         out_info.append(d)
     _check(st, "lsrn_solve_batch", (LSRN_OK, LSRN_ERR_NOT_CONVERGED, LSRN_ERR_DIVERGED))
     return xs, out_info, [int(stat[k]) for k in range(n)]
+
+
+def lsrn_sketch_group(plans) -> list:
+    """lsrn_sketch_group(): sketches a list of Plan objects at once; returns their statuses."""
+    lib = load_library()
+    n = len(plans)
+    hs = (ctypes.c_void_p * max(n, 1))(*[p.handle for p in plans])
+    stat = (ctypes.c_int32 * max(n, 1))()
+    st = lib.lsrn_sketch_group(n, ctypes.byref(hs), ctypes.byref(stat))
+    _check(st, "lsrn_sketch_group")
+    return [int(stat[k]) for k in range(n)]
 
 
 def lsrn_choose_gamma(m: int, n: int, rank: int = 0, tol: float = 1e-14, solver: str = "lsqr",

@@ -210,10 +210,12 @@ __device__ __forceinline__ int col_exponent(const int* ecol, int64_t j) {
 // warps share.
 constexpr int TC_STAGE_TX = 2 * TILE_A_BYTES + TC_DIGITS * TILE_B_BYTES;
 
-__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
+// One 128 x 64 output tile (rows i0.., columns j0.. of C) of one problem's
+// digit planes: the body of sketch_tc_kernel and sketch_tc_grouped_kernel.
+__device__ __forceinline__ void sketch_tc_tile(
     const uint16_t* __restrict__ Gt, const uint16_t* __restrict__ Dt, int64_t Sp, int64_t Qp,
     int64_t Lp, int64_t Kext, const int* __restrict__ ecol, double scale, int64_t S, int64_t Q,
-    double* __restrict__ C, int64_t ldc, int* __restrict__ err) {
+    double* __restrict__ C, int64_t ldc, int* __restrict__ err, int64_t i0, int64_t j0) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + 2 * STAGE_BYTES);   // full[2], empty[2], done
@@ -223,8 +225,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
   uint32_t* tmem_slot = (uint32_t*)(bars + 5);
   int* abort_flag = (int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t i0 = (int64_t)blockIdx.x * TC_M;   // row tiles vary fastest
-  const int64_t j0 = (int64_t)blockIdx.y * TC_N;
 
   if (tid == 0) {
     for (int q = 0; q < 5; ++q) mbar_init(&bars[q], 1);
@@ -385,6 +385,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(
+    const uint16_t* __restrict__ Gt, const uint16_t* __restrict__ Dt, int64_t Sp, int64_t Qp,
+    int64_t Lp, int64_t Kext, const int* __restrict__ ecol, double scale, int64_t S, int64_t Q,
+    double* __restrict__ C, int64_t ldc, int* __restrict__ err) {
+  // row tiles vary fastest
+  sketch_tc_tile(Gt, Dt, Sp, Qp, Lp, Kext, ecol, scale, S, Q, C, ldc, err,
+                 (int64_t)blockIdx.x * TC_M, (int64_t)blockIdx.y * TC_N);
+}
+
+// Grouped sketch of several problems in one launch: CTA b runs tile tiles[b]
+// = (problem, row tile, column tile) of the problem descriptors.
+struct TcGroupDesc {
+  const uint16_t* Gt;
+  const uint16_t* Dt;
+  int64_t Sp, Qp, Lp, Kext;
+  const int* ecol;
+  double scale;
+  int64_t S, Q;
+  double* C;
+  int64_t ldc;
+  int* err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(
+    const TcGroupDesc* __restrict__ descs, const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  const TcGroupDesc d = descs[t.x];
+  sketch_tc_tile(d.Gt, d.Dt, d.Sp, d.Qp, d.Lp, d.Kext, d.ecol, d.scale, d.S, d.Q, d.C, d.ldc, d.err,
+                 (int64_t)t.y * TC_M, (int64_t)t.z * TC_N);
 }
 
 // Digit planes of X rows [l0, l0 + Ls): D[p][j][l - l0], transposed through shared memory.
@@ -814,6 +845,73 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
   return LSRN_OK;
 }
 
+
+static size_t tc_round256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t sketch_tc_group_scratch_bytes(const std::vector<TcGroupItem>& items) {
+  size_t b = 0, tiles = 0;
+  for (const TcGroupItem& it : items) {
+    b += tc_round256(sketch_tc_scratch_bytes(it.L, it.Q, it.S));
+    tiles += (size_t)((it.S + TC_M - 1) / TC_M) * (size_t)((it.Q + TC_N - 1) / TC_N);
+  }
+  return b + tc_round256(items.size() * sizeof(TcGroupDesc)) + tc_round256(tiles * sizeof(int4));
+}
+
+lsrn_status launch_sketch_tc_grouped(const std::vector<TcGroupItem>& items, void* scratch,
+                                     size_t scratch_bytes, cudaStream_t st) {
+  if (items.empty()) return LSRN_OK;
+  if (scratch_bytes < sketch_tc_group_scratch_bytes(items)) return LSRN_ERR_INVALID_ARG;
+  LSRN_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_grouped_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  unsigned char* base = (unsigned char*)scratch;
+  std::vector<TcGroupDesc> descs;
+  std::vector<int64_t> klen;
+  for (const TcGroupItem& it : items) {
+    // the single segment of launch_sketch_tc, planes in this problem's slice
+    const int64_t Qp = (it.Q + TC_N - 1) / TC_N * TC_N;
+    const int64_t Sp = (it.S + TC_M - 1) / TC_M * TC_M;
+    const int64_t Lp = (it.L + TC_KT - 1) / TC_KT * TC_KT;
+    uint16_t* Gh = (uint16_t*)base;
+    uint16_t* Gl = Gh + Sp * Lp;
+    uint16_t* D = Gl + Sp * Lp;
+    int* ecol = (int*)(D + (int64_t)TC_DIGITS * Qp * Lp);
+    base += tc_round256(sketch_tc_scratch_bytes(it.L, it.Q, it.S));
+    const int64_t tot = it.S * it.Q;
+    const int64_t rpb = 1024;
+    launch(zero_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, it.C, it.S, it.Q, it.ldc);
+    launch(colexp_init_kernel, dim3((unsigned)((it.Q + 255) / 256)), dim3(256), 0, st, ecol, it.Q);
+    launch(colexp_kernel, dim3((unsigned)((it.Q + 127) / 128), (unsigned)((it.L + rpb - 1) / rpb)),
+           dim3(128), 0, st, it.X, (int64_t)0, it.L, it.Q, it.ldx, rpb, ecol);
+    launch(split_x_kernel, dim3((unsigned)(Qp / 32), (unsigned)(Lp / 32)), dim3(256), 0, st, it.X,
+           (int64_t)0, it.L, it.Q, it.ldx, (const int*)ecol, Qp, Lp, D);
+    launch(gamma_digits_kernel, dim3((unsigned)(Sp / 128), (unsigned)(Lp / 32)), dim3(256), 0, st,
+           it.seed, it.tag, (int64_t)0, it.L, it.S, Sp, Lp, Gh, Gl, it.lbase);
+    descs.push_back(TcGroupDesc{Gh, D, Sp, Qp, Lp, Lp, ecol, it.xscale, it.S, it.Q, it.C, it.ldc, it.err});
+    klen.push_back(Lp);
+  }
+  // tiles of the longest problems first (a tile's time grows with its K extent);
+  // within a problem the row tiles vary fastest, as in the single launch
+  std::vector<int> order(items.size());
+  for (size_t k = 0; k < items.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return klen[a] > klen[b]; });
+  std::vector<int4> tiles;
+  for (int k : order)
+    for (int64_t tj = 0; tj < descs[k].Qp / TC_N; ++tj)
+      for (int64_t ti = 0; ti < descs[k].Sp / TC_M; ++ti) tiles.push_back(make_int4(k, (int)ti, (int)tj, 0));
+  TcGroupDesc* ddesc = (TcGroupDesc*)base;
+  base += tc_round256(descs.size() * sizeof(TcGroupDesc));
+  int4* dtiles = (int4*)base;
+  LSRN_CUDA_TRY(cudaMemcpyAsync(ddesc, descs.data(), descs.size() * sizeof(TcGroupDesc),
+                                cudaMemcpyHostToDevice, st));
+  LSRN_CUDA_TRY(cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice, st));
+  launch(sketch_tc_grouped_kernel, dim3((unsigned)tiles.size()), dim3(TC_THREADS), (size_t)TC_SMEM, st,
+         (const TcGroupDesc*)ddesc, (const int4*)dtiles);
+  LSRN_CUDA_TRY(cudaGetLastError());
+  // the host vectors must outlive the copies from pageable memory
+  LSRN_CUDA_TRY(cudaStreamSynchronize(st));
+  return LSRN_OK;
+}
 
 // ---- BF16 sketch launcher -----------------------------------------------------
 static int64_t bf16_dims_Sp(int64_t S) { return (S + BF_M - 1) / BF_M * BF_M; }

@@ -973,6 +973,95 @@ lsrn_status lsrn_choose_gamma(const lsrn_gamma_model* md, double* gamma, double*
   return LSRN_OK;
 }
 
+lsrn_status lsrn_sketch_group(int32_t count, lsrn_plan_t* plans, int32_t* status) {
+  if (count < 0 || (count > 0 && plans == nullptr)) return LSRN_ERR_INVALID_ARG;
+  for (int k = 0; k < count; ++k)
+    if (plans[k] == nullptr) return LSRN_ERR_INVALID_ARG;
+  std::vector<lsrn_status> st((size_t)count, LSRN_OK);
+  std::vector<int> grp, rest;
+  const bool forced_segments = getenv("LSRN_TC_SEGMENT_ROWS") != nullptr;
+  int dev = -1;
+  for (int k = 0; k < count; ++k) {
+    Plan* p = plans[k];
+    const bool ok = !forced_segments && !p->csr && !p->is_op && !p->sharded && !p->ridge &&
+                    p->opt.sketch_mode == LSRN_SKETCH_TC_SLICED && (dev < 0 || p->device == dev) &&
+                    sketch_tc_plan_segment_rows(p->xrows, p->q, p->s) >= p->xrows;
+    if (ok) {
+      grp.push_back(k);
+      dev = p->device;
+    } else {
+      rest.push_back(k);
+    }
+  }
+  if (!rest.empty()) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    parallel_for((int)rest.size(), std::min<int>(8, (int)rest.size()), cur,
+                 [&](int i) { st[rest[i]] = lsrn_sketch(plans[rest[i]]); });
+  }
+  if (!grp.empty()) {
+    cudaSetDevice(dev);
+    cudaStream_t gs = nullptr;
+    lsrn_status gst = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) == cudaSuccess ? LSRN_OK
+                                                                                            : LSRN_ERR_CUDA;
+    size_t k0 = 0;
+    while (gst == LSRN_OK && k0 < grp.size()) {
+      // a chunk of plans whose digit planes fit 8 GiB (at least one plan)
+      std::vector<TcGroupItem> items;
+      std::vector<Plan*> ps;
+      size_t k1 = k0;
+      for (; k1 < grp.size(); ++k1) {
+        Plan* p = plans[grp[k1]];
+        std::vector<TcGroupItem> trial = items;
+        trial.push_back(TcGroupItem{p->X, p->xrows, p->q, p->ldx, p->xscale, p->s, p->opt.seed, 0u,
+                                    p->shard.lbase, p->Xs, p->q, p->iscal + IC_TCERR});
+        if (!items.empty() && sketch_tc_group_scratch_bytes(trial) > kTcScratchBudget) break;
+        items.swap(trial);
+        ps.push_back(p);
+      }
+      for (Plan* p : ps) {   // the plan's own earlier work (A's layout) comes first
+        cudaEventRecord(p->ev[0], p->stream);
+        cudaStreamWaitEvent(gs, p->ev[0], 0);
+        for (auto& pr : p->gemm_events) {
+          cudaEventDestroy(pr.first);
+          cudaEventDestroy(pr.second);
+        }
+        p->gemm_events.clear();
+        p->sketch_escalated = false;
+        p->bound_widen = 0.0;
+        cudaMemsetAsync(p->iscal + IC_TCERR, 0, sizeof(int), gs);
+      }
+      const size_t bytes = sketch_tc_group_scratch_bytes(items);
+      void* buf = nullptr;
+      if (lsrn_malloc_async(&buf, bytes, gs) != cudaSuccess) {
+        cudaGetLastError();
+        gst = LSRN_ERR_OOM;
+        break;
+      }
+      gst = launch_sketch_tc_grouped(items, buf, bytes, gs);
+      cudaFreeAsync(buf, gs);
+      for (Plan* p : ps) {
+        cudaEventRecord(p->ev[1], gs);
+        cudaStreamWaitEvent(p->stream, p->ev[1], 0);
+        if (gst == LSRN_OK) {
+          p->sketch_used = LSRN_SKETCH_TC_SLICED;
+          p->state = 1;
+        }
+      }
+      for (size_t k = k0; k < k1; ++k) st[grp[k]] = gst;
+      k0 = k1;
+    }
+    for (size_t k = k0; k < grp.size(); ++k) st[grp[k]] = gst;   // after a failure
+    if (gs) cudaStreamDestroy(gs);
+  }
+  lsrn_status first = LSRN_OK;
+  for (int k = 0; k < count; ++k) {
+    if (status) status[k] = st[k];
+    if (first == LSRN_OK && st[k] != LSRN_OK) first = st[k];
+  }
+  return first;
+}
+
 lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* const* b,
                              double* const* x, const lsrn_options* opt, int32_t solver,
                              int32_t threads, lsrn_info* info, int32_t* status) {
@@ -987,11 +1076,21 @@ lsrn_status lsrn_solve_batch(int32_t count, const lsrn_matrix* A, const double* 
   const int nth = std::max(1, std::min<int>(threads > 0 ? threads : 8, count));
   std::vector<lsrn_plan_t> plans((size_t)count, nullptr);
   std::vector<lsrn_status> st((size_t)count, LSRN_OK);
-  // 1. plans and sketches, each problem on its own stream
-  parallel_for(count, nth, dev, [&](int i) {
-    st[i] = lsrn_plan(&A[i], opt, nullptr, &plans[i]);
-    if (st[i] == LSRN_OK) st[i] = lsrn_sketch(plans[i]);
-  });
+  // 1. plans on the host threads, then the sketches: the exact tensor-core
+  // sketches of small dense problems grouped into shared launches
+  parallel_for(count, nth, dev, [&](int i) { st[i] = lsrn_plan(&A[i], opt, nullptr, &plans[i]); });
+  {
+    std::vector<lsrn_plan_t> ok;
+    std::vector<int> idx;
+    for (int i = 0; i < count; ++i)
+      if (st[i] == LSRN_OK) {
+        ok.push_back(plans[i]);
+        idx.push_back(i);
+      }
+    std::vector<int32_t> gst(ok.size(), LSRN_OK);
+    lsrn_sketch_group((int32_t)ok.size(), ok.data(), gst.data());
+    for (size_t k = 0; k < idx.size(); ++k) st[idx[k]] = (lsrn_status)gst[k];
+  }
   // 2. preconditioners: one launch for the small dense-sketch problems, largest first
   {
     std::vector<Plan*> ps;

@@ -250,6 +250,24 @@ lsrn_status launch_sketch_tc(const double* X, int64_t L, int64_t Q, int64_t ldx,
                              cudaStream_t st,
                              std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* gemm_events,
                              int64_t lbase = 0);
+// Grouped exact sketch: several single-segment problems, their digit planes
+// prepared one after another, then all their output tiles in one launch.  Each
+// problem's C is bit for bit what launch_sketch_tc gives for it alone.
+struct TcGroupItem {
+  const double* X;
+  int64_t L, Q, ldx;
+  double xscale;
+  int64_t S;
+  uint64_t seed;
+  uint32_t tag;
+  int64_t lbase;
+  double* C;
+  int64_t ldc;
+  int* err;
+};
+size_t sketch_tc_group_scratch_bytes(const std::vector<TcGroupItem>& items);
+lsrn_status launch_sketch_tc_grouped(const std::vector<TcGroupItem>& items, void* scratch,
+                                     size_t scratch_bytes, cudaStream_t st);
 // Single-pass BF16 sketch (operands rounded to bf16 once, FP32 accumulation in
 // TMEM per 2048 rows, FP64 across chunks and K splits); same contract.
 size_t sketch_bf16_scratch_bytes(int64_t Ls, int64_t Q, int64_t S);

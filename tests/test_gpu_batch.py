@@ -82,3 +82,47 @@ def test_batch_edge_cases():
     b = torch.ones(300, dtype=torch.float64, device="cuda")
     xs, infos, stats = L.lsrn_solve_batch([(A, b)], None)
     assert stats == [L.LSRN_OK] and infos[0]["rank"] == 0 and float(xs[0].abs().max()) == 0.0
+
+
+def test_grouped_tensor_core_sketch_is_bit_identical_to_one_at_a_time():
+    """lsrn_sketch_group puts the exact tensor-core sketches of small dense
+    plans into shared launches; each sketch must be bit for bit the one
+    lsrn_sketch gives alone, and plans it does not group (ridge, CSR, FP64
+    mode) must still come out right.  The grouped sketch is also checked
+    against the oracle's G A (1e-13 of sum |g||a|)."""
+    probs = _problems()
+    opt_tc = dict(seed=41, sketch_mode=L.LSRN_SKETCH_TC_SLICED)
+
+    def make(k, A, extra=None):
+        kw = dict(opt_tc, **(extra or {}))
+        if isinstance(A, tuple):
+            return L.lsrn_plan(None, L.default_options(**kw), csr=A)
+        return L.lsrn_plan(A, L.default_options(**kw))
+
+    extras = [None] * len(probs)
+    extras[1] = dict(lambda_=0.05)                    # ridge: sketched alone
+    extras[2] = dict(sketch_mode=L.LSRN_SKETCH_F64)   # FP64 mode: sketched alone
+    group = [make(k, p[0], extras[k]) for k, p in enumerate(probs)]
+    alone = [make(k, p[0], extras[k]) for k, p in enumerate(probs)]
+    try:
+        sts = L.lsrn_sketch_group(group)
+        assert sts == [L.LSRN_OK] * len(group)
+        for p in alone:
+            L.lsrn_sketch(p)
+        for k, (pg, pa) in enumerate(zip(group, alone)):
+            Sg, Sa = L.lsrn_plan_get_sketch(pg), L.lsrn_plan_get_sketch(pa)
+            assert np.array_equal(Sg, Sa), k
+        # one grouped sketch against the oracle: tall 3000 x 40, Gamma^T A
+        Sg = L.lsrn_plan_get_sketch(group[0])
+        A = probs[0][2]
+        Gm = O.sketch_block(41, 0, 0, A.shape[0], Sg.shape[0])
+        ref = Gm.T @ A
+        bound = 1e-13 * (np.abs(Gm).T @ np.abs(A))
+        assert np.all(np.abs(Sg - ref) <= bound + 1e-300)
+        # and the grouped plans solve like any other
+        x, info = L.lsrn_solve_lsqr(group[3], probs[3][1])
+        xs, _ = O.minlen_refined(probs[3][2], probs[3][3])
+        assert O.rel_err(x.cpu().numpy(), xs) <= 1e-10
+    finally:
+        for p in group + alone:
+            p.close()
