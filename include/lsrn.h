@@ -531,7 +531,7 @@ lsrn_status lsrn_submit(lsrn_server_t s, const lsrn_matrix* A, const double* b,
 lsrn_status lsrn_poll(lsrn_server_t s, uint64_t ticket, double* x_out, lsrn_info* info);
 lsrn_status lsrn_server_destroy(lsrn_server_t s);
 
-/* Continuous batching of the preconditioner phase (north star serving item):
+/* Continuous batching of the preconditioner phase (beyond the paper, for serving):
  * with max_short_side > 0, a request whose short side is at most that (and at
  * most 128, the batched kernel's limit) and whose preconditioner is the SVD of
  * an F64 or TC_SLICED sketch is sketched by its worker and then handed to the
