@@ -440,6 +440,20 @@ lsrn_status lsrn_plan_destroy(lsrn_plan_t p);
  * shape.  STATE before lsrn_sketch.  Synchronises. */
 lsrn_status lsrn_plan_get_sketch(lsrn_plan_t p, double* out, int64_t* rows, int64_t* cols);
 
+/* Copy the three FP32 planes of a dense plan made with LSRN_ITER_F32X2 (the
+ * operand of the double-float passes and of the triple-float residual of the
+ * refinement): hi, lo and x3, each rows x ld row-major (rows = the long side,
+ * ld = the short side rounded up to a multiple of 4, zero beyond it), with
+ * X / scale = hi + lo + x3 exactly, hi = fl32(X / scale), lo = fl32(X / scale
+ * - hi), x3 = fl32(X / scale - hi - lo) in round-to-nearest, and scale the
+ * power of two that puts max |X| in [1, 2) (1 for a zero or non-finite X).
+ * Any of hi, lo, x3, rows, ld, scale may be NULL; hi, lo, x3 are device or
+ * host buffers of rows * ld floats owned by the caller.  UNSUPPORTED if the
+ * plan has no planes (another iteration mode, CSR A, an operator, or a short
+ * side the double-float passes do not take).  Synchronises. */
+lsrn_status lsrn_plan_get_planes(lsrn_plan_t p, float* hi, float* lo, float* x3, int64_t* rows,
+                                 int64_t* ld, double* scale);
+
 /* Copy the preconditioner N (n' x r, row-major; n' = n for m >= n) or M
  * (m x r) to `out` and the r kept singular values of A~ (descending) to
  * `sigma` (either may be NULL).  STATE before lsrn_precond.  Synchronises. */

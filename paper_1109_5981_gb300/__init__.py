@@ -150,6 +150,9 @@ _SIGS = {
     "lsrn_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "lsrn_plan_get_sketch": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "lsrn_plan_get_planes": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "lsrn_plan_get_precond": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "lsrn_generate_sketch_block": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64,
@@ -558,6 +561,19 @@ def lsrn_plan_get_sketch(plan: Plan) -> np.ndarray:
     _check(lib.lsrn_plan_get_sketch(plan.handle, out.ctypes.data, None, None),
            "lsrn_plan_get_sketch")
     return out
+
+
+def lsrn_plan_get_planes(plan: Plan):
+    """Returns (hi, lo, x3 as (rows, ld) float32 arrays, scale)."""
+    lib = load_library()
+    rows, ld, scale = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(lib.lsrn_plan_get_planes(plan.handle, None, None, None, ctypes.byref(rows),
+                                    ctypes.byref(ld), ctypes.byref(scale)),
+           "lsrn_plan_get_planes")
+    planes = [np.empty((rows.value, ld.value), dtype=np.float32) for _ in range(3)]
+    _check(lib.lsrn_plan_get_planes(plan.handle, *[a.ctypes.data for a in planes], None, None,
+                                    None), "lsrn_plan_get_planes")
+    return planes[0], planes[1], planes[2], scale.value
 
 
 def lsrn_plan_get_precond(plan: Plan):

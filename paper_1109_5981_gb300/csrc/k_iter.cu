@@ -1422,54 +1422,179 @@ __global__ void to_f32_kernel(const double* __restrict__ X, int64_t rows, int64_
   const int64_t i = idx / ldy, j = idx % ldy;
   Y[idx] = j < cols ? (float)X[i * ldx + j] : 0.0f;
 }
+// The conversion kernels below walk X row by row: a group of TPR threads (a
+// power of two, 32..256) per row, 256 / TPR rows per block and pass, blocks
+// striding over the rows, so no element index needs a 64-bit division.  VEC = 2
+// moves two neighbouring columns per access (16-byte loads of X, 8-byte stores
+// of the FP32 planes); it needs X 16-byte aligned and cols and ldx even.
+
+// |x| as a key whose unsigned order is the order of the values (non-negative
+// doubles order like their bit patterns); NaN gets key 0, so it is skipped.
+// Integer compares keep the FP64 pipe, a few instructions per clock per SM on
+// this part, out of a pass that is meant to stream at HBM speed.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  const unsigned long long b =
+      (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  return b > 0x7ff0000000000000ull ? 0ull : b;
+}
+
 // Largest |X_ij| as the bit pattern of a non-negative double (ordered like the value).
-__global__ void maxabs_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
-                              unsigned long long* __restrict__ out) {
-  __shared__ double sm[32];
-  double mx = 0.0;
-  const int64_t tot = rows * cols;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const double v = fabs(X[(idx / cols) * ldx + idx % cols]);
-    mx = v > mx ? v : mx;   // NaN entries are skipped
+template <int VEC>
+__global__ void __launch_bounds__(256) maxabs_kernel(const double* __restrict__ X, int64_t rows,
+                                                     int64_t cols, int64_t ldx, int tpr_log2,
+                                                     unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long sm[8];
+  const int tpr = 1 << tpr_log2, rpb = 256 >> tpr_log2;
+  const int t = (int)threadIdx.x & (tpr - 1);
+  const int64_t nv = cols / VEC;
+  unsigned long long mx = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * rpb + (threadIdx.x >> tpr_log2); i < rows;
+       i += (int64_t)gridDim.x * rpb) {
+    const double* x = X + i * ldx;
+#pragma unroll 4
+    for (int64_t p = t; p < nv; p += tpr) {
+      if constexpr (VEC == 2) {
+        const double2 v = reinterpret_cast<const double2*>(x)[p];
+        const unsigned long long a = abs_key(v.x), b = abs_key(v.y);
+        mx = a > mx ? a : mx;
+        mx = b > mx ? b : mx;
+      } else {
+        const unsigned long long a = abs_key(x[p]);
+        mx = a > mx ? a : mx;
+      }
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 1; q < (int)(blockDim.x / 32); ++q) mx = fmax(mx, sm[q]);
-    atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+    for (int q = 1; q < 8; ++q) mx = sm[q] > mx ? sm[q] : mx;
+    atomicMax(out, mx);
   }
 }
 
 // Xh = fl32(X * inv), Xl = fl32(X * inv - Xh), X3 = fl32(X * inv - Xh - Xl) (exact);
-// zero padding for j >= cols.
-__global__ void to_x2_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
-                             double inv, float* __restrict__ Yh, float* __restrict__ Yl,
-                             float* __restrict__ Y3, int64_t ldy) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * ldy) return;
-  const int64_t i = idx / ldy, j = idx % ldy;
-  const double v = j < cols ? X[i * ldx + j] * inv : 0.0;
+// zero padding for cols <= j < ldy.
+struct Split3 {
+  float h, l, e;
+};
+__device__ __forceinline__ Split3 split3(double x, double inv) {
+  const double v = x * inv;
   const float h = __double2float_rn(v);
   const double r = v - (double)h;
   const float l = __double2float_rn(r);
-  Yh[idx] = h;
-  Yl[idx] = l;
-  Y3[idx] = __double2float_rn(r - (double)l);
+  return {h, l, __double2float_rn(r - (double)l)};
+}
+
+// The same split on the integer and FP32 pipes.  v = x 2^k with exponent E;
+// when every bit of v lies at or above 2^-126 (E >= -74, the significand has
+// 53 bits) and E <= 126, h, l and e are normal floats or zeros, and rounding
+// to float is rounding the 53-bit significand M to 24 bits to nearest, ties
+// to even: h = RN24(M) 2^(E-52), r = M - RN24(M) (|r| <= 2^28, an int32),
+// l = RN24(r) 2^(E-52) (the int-to-float conversion rounds the same way), e =
+// (r - RN24(r)) 2^(E-52) (at most 5 bits, exact).  All scalings are by powers
+// of two into the normal range, hence exact.  Other x (zero, subnormal, tiny
+// after scaling, Inf, NaN) and a scale that is not a normal power of two take
+// split3 itself.
+__device__ __forceinline__ Split3 split3_int(double x, double inv, int k, bool pow2) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const int E = ex - 1023 + k;
+  if (!pow2 || ex == 0 || ex == 0x7ff || E < -74 || E > 126) return split3(x, inv);
+  const long long M = (b & 0xfffffffffffffll) | 0x10000000000000ll;
+  long long q = M >> 29;
+  const int rem = (int)(M & 0x1fffffff);
+  q += (rem > (1 << 28) || (rem == (1 << 28) && (q & 1))) ? 1 : 0;
+  int r = (int)(M - (q << 29));
+  const bool neg = b < 0;
+  if (neg) r = -r;
+  const float lf = __int2float_rn(r);
+  const int e = r - __float2int_rz(lf);
+  const float s52 = __int_as_float((E - 52 + 127) << 23);   // 2^(E-52), >= 2^-126
+  const float s23 = __int_as_float((E - 23 + 127) << 23);   // 2^(E-23)
+  const float hf = __int2float_rn((int)q) * s23;
+  return {neg ? -hf : hf, lf * s52, __int2float_rn(e) * s52};
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256, 4) to_x2_kernel(const double* __restrict__ X, int64_t rows,
+                                                    int64_t cols, int64_t ldx, double inv,
+                                                    int k, bool pow2, int tpr_log2,
+                                                    float* __restrict__ Yh, float* __restrict__ Yl,
+                                                    float* __restrict__ Y3, int64_t ldy) {
+  const int tpr = 1 << tpr_log2, rpb = 256 >> tpr_log2;
+  const int t = (int)threadIdx.x & (tpr - 1);
+  const int64_t nv = cols / VEC, nvy = ldy / VEC;
+  for (int64_t i = (int64_t)blockIdx.x * rpb + (threadIdx.x >> tpr_log2); i < rows;
+       i += (int64_t)gridDim.x * rpb) {
+    const double* x = X + i * ldx;
+    const int64_t o = i * ldy;
+#pragma unroll 4
+    for (int64_t p = t; p < nvy; p += tpr) {
+      if constexpr (VEC == 2) {
+        Split3 a{0.f, 0.f, 0.f}, b{0.f, 0.f, 0.f};
+        if (p < nv) {
+          const double2 v = reinterpret_cast<const double2*>(x)[p];
+          a = split3_int(v.x, inv, k, pow2);
+          b = split3_int(v.y, inv, k, pow2);
+        }
+        reinterpret_cast<float2*>(Yh + o)[p] = make_float2(a.h, b.h);
+        reinterpret_cast<float2*>(Yl + o)[p] = make_float2(a.l, b.l);
+        reinterpret_cast<float2*>(Y3 + o)[p] = make_float2(a.e, b.e);
+      } else {
+        Split3 a{0.f, 0.f, 0.f};
+        if (p < nv) a = split3_int(x[p], inv, k, pow2);
+        Yh[o + p] = a.h;
+        Yl[o + p] = a.l;
+        Y3[o + p] = a.e;
+      }
+    }
+  }
+}
+
+// log2 of the threads per row: about four accesses per thread on the longest
+// side of the row, between a warp and a block
+int conv_tpr_log2(int64_t units) {
+  int lg = 5;
+  while (lg < 8 && ((int64_t)1 << lg) * 4 < units) ++lg;
+  return lg;
+}
+
+// One wave of resident blocks, so that every block's share of rows runs at once.
+template <typename K>
+unsigned conv_grid(K kernel, int64_t rows, int64_t rows_per_block) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int64_t want = (rows + rows_per_block - 1) / rows_per_block;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * num_sms()));
 }
 }  // namespace
 
 lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ldx, float* Yh,
                          float* Yl, float* Y3, int64_t ldy, unsigned long long* maxbits, double* xs,
                          cudaStream_t st) {
-  const int64_t tot = rows * ldy;
   *xs = 1.0;
-  if (tot == 0) return LSRN_OK;
+  if (rows == 0 || ldy == 0) return LSRN_OK;
+  // two columns per access when every row of X starts 16-byte aligned and the
+  // rows hold whole pairs (ldy is a multiple of 4, so the FP32 rows do)
+  const bool vec2 = ((uintptr_t)X % 16 == 0) && cols % 2 == 0 && ldx % 2 == 0 && ldy % 2 == 0;
+  const int vec = vec2 ? 2 : 1;
+  const int lg = conv_tpr_log2(ldy / vec);
+  const int64_t rpb = 256 >> lg;
   LSRN_CUDA_TRY(cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st));
-  const int64_t want = (rows * cols + 255) / 256;
-  launch(maxabs_kernel, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * num_sms()))),
-         dim3(256), 0, st, X, rows, cols, ldx, maxbits);
+  if (vec2)
+    launch(maxabs_kernel<2>, dim3(conv_grid(maxabs_kernel<2>, rows, rpb)), dim3(256), 0, st, X,
+           rows, cols, ldx, lg, maxbits);
+  else
+    launch(maxabs_kernel<1>, dim3(conv_grid(maxabs_kernel<1>, rows, rpb)), dim3(256), 0, st, X,
+           rows, cols, ldx, lg, maxbits);
   unsigned long long bits = 0;
   LSRN_CUDA_TRY(cudaMemcpyAsync(&bits, maxbits, sizeof(bits), cudaMemcpyDeviceToHost, st));
   LSRN_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1478,8 +1603,16 @@ lsrn_status launch_to_x2(const double* X, int64_t rows, int64_t cols, int64_t ld
   // power-of-two scale with the largest |X| / xs in [1, 2): no FP32 overflow,
   // and elements below 2^-126 of the largest are the only ones that lose bits
   if (mx > 0.0 && std::isfinite(mx)) *xs = std::ldexp(1.0, std::ilogb(mx));
-  launch(to_x2_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, X, rows, cols, ldx,
-         1.0 / *xs, Yh, Yl, Y3, ldy);
+  const double inv = 1.0 / *xs;
+  int k = 0;
+  const bool pow2 = std::isnormal(inv) && std::frexp(inv, &k) == 0.5;   // inv = 2^(k-1)
+  k -= 1;
+  if (vec2)
+    launch(to_x2_kernel<2>, dim3(conv_grid(to_x2_kernel<2>, rows, rpb)), dim3(256), 0, st, X, rows,
+           cols, ldx, inv, k, pow2, lg, Yh, Yl, Y3, ldy);
+  else
+    launch(to_x2_kernel<1>, dim3(conv_grid(to_x2_kernel<1>, rows, rpb)), dim3(256), 0, st, X, rows,
+           cols, ldx, inv, k, pow2, lg, Yh, Yl, Y3, ldy);
   LSRN_CUDA_TRY(cudaGetLastError());
   return LSRN_OK;
 }

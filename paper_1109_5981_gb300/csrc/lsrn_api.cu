@@ -1145,6 +1145,22 @@ lsrn_status lsrn_plan_get_sketch(lsrn_plan_t p, double* out, int64_t* rows, int6
   return LSRN_OK;
 }
 
+lsrn_status lsrn_plan_get_planes(lsrn_plan_t p, float* hi, float* lo, float* x3, int64_t* rows,
+                                 int64_t* ld, double* scale) {
+  if (p == nullptr) return LSRN_ERR_INVALID_ARG;
+  if (p->X2h == nullptr || p->X2l == nullptr || p->X3 == nullptr) return LSRN_ERR_UNSUPPORTED;
+  if (rows) *rows = p->xrows;
+  if (ld) *ld = p->ldx2;
+  if (scale) *scale = p->x2scale;
+  const size_t bytes = (size_t)(p->xrows * p->ldx2) * sizeof(float);
+  const float* src[3] = {p->X2h, p->X2l, p->X3};
+  float* dst[3] = {hi, lo, x3};
+  for (int k = 0; k < 3; ++k)
+    if (dst[k]) LSRN_CUDA_TRY(cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyDefault, p->stream));
+  LSRN_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return LSRN_OK;
+}
+
 lsrn_status lsrn_plan_get_precond(lsrn_plan_t p, double* out, double* sigma, int64_t* rank) {
   if (p == nullptr) return LSRN_ERR_INVALID_ARG;
   if (p->state < 2) return LSRN_ERR_STATE;
