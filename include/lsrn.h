@@ -436,7 +436,7 @@ lsrn_status lsrn_plan_sharded(const lsrn_matrix* A_local, const lsrn_options* op
 lsrn_status lsrn_plan_destroy(lsrn_plan_t p);
 
 /* Copy the sketch to `out` (host or device, FP64): for m >= n A~ (s x n,
- * row-major); for m < n A~^T (s x m, row-major).  *rows/*cols receive the
+ * row-major); for m < n A~^T (s x m, row-major).  *rows and *cols receive the
  * shape.  STATE before lsrn_sketch.  Synchronises. */
 lsrn_status lsrn_plan_get_sketch(lsrn_plan_t p, double* out, int64_t* rows, int64_t* cols);
 

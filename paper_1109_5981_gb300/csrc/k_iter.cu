@@ -465,16 +465,6 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
-// (h, l) += (ah + al) * (bh + bl), dropping al * bl (below 2^-48 of the product)
-__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& h, float& l) {
-  const float p = ah * bh;
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, fmaf(al, bh, e));
-  float s, er;
-  two_sum_f(h, p, s, er);
-  h = s;
-  l += er + e;
-}
 // Packed pairs: two FP32 lanes in one 64-bit register, operated on by the
 // f32x2 instructions (one issue slot for both lanes, each lane rounded as the
 // scalar IEEE operation).  The pass handles columns in (even, odd) pairs, so
@@ -510,8 +500,11 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
-// (h, l) += (ah + al) * (bh + bl) lane by lane, as df_fma; bhn = -bh (so the
-// negated product comes from one multiply and the TwoSum uses it directly).
+// (h, l) += (ah + al) * (bh + bl) lane by lane, dropping al * bl (below 2^-48
+// of the product): p = fl(ah bh) and its exact error by an FMA, the cross
+// terms into that error, TwoSum(h, p) with the rounding error into l.  bhn =
+// -bh, so the negated product comes from one multiply and the TwoSum uses it
+// directly.
 __device__ __forceinline__ void df_fma2(f32x2 ah, f32x2 al, f32x2 bh, f32x2 bhn, f32x2 bl,
                                         f32x2& h, f32x2& l) {
   const f32x2 np = mul2(ah, bhn);                       // -p, p = ah bh rounded

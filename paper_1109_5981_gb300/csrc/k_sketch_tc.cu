@@ -957,7 +957,6 @@ lsrn_status launch_sketch_bf16(const double* X, int64_t L, int64_t Q, int64_t ld
   double* part = (double*)(((uintptr_t)(ecol + Q) + 255) & ~(uintptr_t)255);
   const int64_t tot = S * Q;
   launch(zero_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, C, S, Q, ldc);
-  const int64_t tiles = (Sp / BF_M) * (Qp / BF_N);
   for (int64_t l0 = 0; l0 < L; l0 += seg_rows) {
     const int64_t l1 = std::min(L, l0 + seg_rows);
     const int64_t nkt = (l1 - l0 + BF_KT - 1) / BF_KT;
