@@ -569,7 +569,8 @@ def phase_rooflines(info_list, args, peaks: dict, fp64_peak: float, m_local: int
     t_qr = mean("t_qr_ms")
     qflops = 2.0 * s * n * n - 2.0 * n ** 3 / 3.0
     ach = qflops / (t_qr * 1e-3) / 1e12 if t_qr > 0 else 0.0
-    out["qr"] = {"kernel": "hh_reflector/hh_w/hh_update (Householder QR of the sketch)", "ms": t_qr,
+    out["qr"] = {"kernel": "qr_coop_kernel (Householder QR of the sketch in one cooperative launch; "
+                           "the per-column hh_* kernels where it does not apply)", "ms": t_qr,
                  "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                  "frac": ach / fp64_peak, "work": f"2 s n^2 - 2 n^3/3 = {qflops:.3e} flop",
                  "peak_source": "FP64 FMA rate probed in this run (lsrn_probe_fp64_fma)"}
