@@ -1,7 +1,9 @@
 // Preconditioner (Algorithm 1 steps 4-5, Algorithm 2 steps 4-5) on the device.
 //
 // Input: the sketch Xs (S x Q, row-major, S > Q): A~ for m >= n, A~^T for m < n.
-// 1. Householder QR of Xs -> R (Q x Q upper triangular); Q is not formed.  One
+// 1. Householder QR of Xs -> R (Q x Q upper triangular); Q is not formed.  All
+//    columns in one cooperative launch (k_qr_coop.cu) wherever the device
+//    holds its grid and the sketch's rows fit its shared memory; otherwise one
 //    column at a time up to 3000 columns, blocked in panels of 32 columns
 //    with the compact WY form beyond.
 // 2. One-sided (Hestenes) Jacobi on Y = R^T: rotate pairs of columns of Y
