@@ -7,7 +7,9 @@
 // lsrn_plan + lsrn_solve_* on it, and park the result until lsrn_poll collects
 // it.  Requests admitted together run concurrently on the device; each plan's
 // arithmetic has a fixed order, so a result does not depend on what ran beside
-// it.
+// it.  Their preconditioners (short side up to 128) are packed by the batcher
+// below into shared launches of the batched preconditioner kernel, which
+// computes each problem as the per-problem kernels do.
 #include <cuda_runtime.h>
 
 #include <algorithm>
