@@ -7,7 +7,6 @@ with the per-unit costs of the dense 10^6 x 2000 benchmark on this GPU the
 optimum falls in the paper's empirical range 1.6 - 2.5 (section 6.2)."""
 import math
 
-import numpy as np
 import pytest
 
 L = pytest.importorskip("paper_1109_5981_gb300")

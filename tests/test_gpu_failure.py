@@ -12,7 +12,6 @@ safe.  Afterwards the same plan must solve correctly (it sketches again: the
 QR overwrote the sketch)."""
 import time
 
-import numpy as np
 import pytest
 
 import oracle as O
