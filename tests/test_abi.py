@@ -75,3 +75,16 @@ def test_server_needs_a_device():
     with pytest.raises(L.LsrnError) as e:
         L.lsrn_server_create(0, 2)
     assert e.value.status == L.LSRN_ERR_INVALID_ARG
+
+
+def test_inspection_calls_reject_a_null_plan():
+    # argument checks come before any device call, so they hold without a GPU
+    import paper_1109_5981_gb300 as L
+    lib = L.load_library()
+    rows, cols = ctypes.c_int64(), ctypes.c_int64()
+    scale = ctypes.c_double()
+    assert lib.lsrn_plan_get_sketch(None, None, ctypes.byref(rows), ctypes.byref(cols)) == \
+        L.LSRN_ERR_INVALID_ARG
+    assert lib.lsrn_plan_get_precond(None, None, None, ctypes.byref(rows)) == L.LSRN_ERR_INVALID_ARG
+    assert lib.lsrn_plan_get_planes(None, None, None, None, ctypes.byref(rows), ctypes.byref(cols),
+                                    ctypes.byref(scale)) == L.LSRN_ERR_INVALID_ARG
